@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the QMC sector-integration hot path on GB300: integrand evaluations per second.
+
+A step is one pass of the whole hot path over the massive one-loop box in the physical region (4 sectors,
+contour deformation lambda = 0.5, s = 5, t = -1.5, m = 1, massless legs): every sector x 16 random shifts x
+every point of the rank-1 lattice of size n = 16777213 (largest prime below 2^24), Korobov transform r = 3,
+FP64 -- 1.07e9 integrand evaluations, reduced per (sector, shift) -- through qmc_eval_partials +
+qmc_reduce_partials (the two launches of qmc_eval_sums).
+
+Output: one JSON line (rank 0).  `value` = evaluations/s of the whole job with the table, shifts and lambda
+already resident on the device; `e2e` = the same metric through qmc_eval_sums_host (host buffers, copies inside
+the timed region); `roofline` = algorithmic FP64 throughput of the evaluation kernel against the FP64 peak
+derived from the SM count, FP64 units and clock; `cpu_baseline` = the oracle (plain C, all host cores) on a
+bounded sample of the same workload; `time_to_1e-3` = qmc_integrate to 1e-3 relative error over 32 seeds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun, one rank per GPU): every rank integrates its own replica with its own shifts (weak
+scaling, no data-path collective); the barrier and max-over-ranks timing use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+LOG2_N = 24
+N_SHIFTS = 16
+LAMBDA = 0.5
+METRIC = "integrand evals/s"
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock per SM (4 flop) x 2070 MHz maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
+# DRAM bytes per launch of the evaluation kernel from ncu (profiles/qmc_eval_kernel_massive_box.md), valid
+# while the device code hashes to KERNEL_HASH; null otherwise
+TRAFFIC_BYTES = None
+KERNEL_HASH = None
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("qmc_device.cuh", "qmc_kern_d3.cu"):
+        with open(os.path.join(ROOT, "paper_1508_02512_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip time-to-accuracy and CPU baseline")
+    return ap.parse_args()
+
+
+def workload_config(n):
+    return {"workload": f"massive one-loop box, physical s=5 t=-1.5 m^2=1, lambda={LAMBDA}, 4 sectors x "
+                        f"{N_SHIFTS} shifts x n={n} rank-1 lattice, Korobov r=3",
+            "integral": W.CONFIG1.name, "sectors": 4, "shifts": N_SHIFTS, "lattice_n": n,
+            "l2": "inputs (a 3 KB table, shifts) live in shared memory; a 256 MiB buffer is written between steps "
+                  "to flush L2"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def korobov_vector(n, a=76):
+    """An admissible generating vector (1, a, a^2, ...) mod n for timing the oracle: the cost of an evaluation
+    does not depend on which vector the lattice uses."""
+    return [pow(a, j, n) for j in range(6)]
+
+
+def cpu_baseline(n_log2=18):
+    """The oracle as it stands (plain C, OpenMP over all host cores) on a bounded sample of the workload."""
+    from oracle import integrate as OI
+    from oracle import lattice as OL
+    cfg = W.CONFIG1
+    prob = OI.make_problem(cfg.topology, {**cfg.point}, 0, 0)
+    n = OL.prime_below(1 << n_log2)
+    z = korobov_vector(n)
+    shifts = W.shifts(12345, N_SHIFTS)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    OI.integrate(prob, n, z, shifts, LAMBDA, 3, nthreads=cores)
+    dt = time.perf_counter() - t0
+    evals = len(prob.sectors) * N_SHIFTS * n
+    return {"value": evals / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"massive box, n={n} (largest prime < 2^{n_log2}), {N_SHIFTS} shifts, 4 sectors = {evals} "
+                      f"evals in {dt:.2f} s"}
+
+
+def main_reference(args):
+    world, rank, local, dist = dist_setup(args)
+    if rank != 0:
+        return
+    from oracle import integrate as OI
+    from oracle import lattice as OL
+    cfg = W.CONFIG1
+    prob = OI.make_problem(cfg.topology, {**cfg.point}, 0, 0)
+    n = OL.prime_below(1 << 16)
+    z = korobov_vector(n)
+    shifts = W.shifts(12345, N_SHIFTS)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        OI.integrate(prob, n, z, shifts, LAMBDA, 3, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        OI.integrate(prob, n, z, shifts, LAMBDA, 3, nthreads=cores)
+    dt = time.perf_counter() - t0
+    evals = len(prob.sectors) * N_SHIFTS * n
+    v = evals * args.steps / dt
+    sample = f"each step: massive box, n={n} (largest prime < 2^16), {N_SHIFTS} shifts, 4 sectors = {evals} evals"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": workload_config(n),
+                      "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main_ours(args):
+    import torch
+
+    from paper_1508_02512_gb300 import _native as N
+    from paper_1508_02512_gb300 import api
+    from paper_1508_02512_gb300 import tables as T
+
+    world, rank, local, dist = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev_name = f"cuda:{local}"
+    cfg = W.CONFIG1
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, 0, 0)
+    di = api.DeviceIntegral(prep, dev_name)
+    lat = dict(api.builtin_lattices())
+    n = max(k for k in lat if k < (1 << LOG2_N))
+    z = lat[n]
+    shifts = W.shifts(cfg.seed + rank, N_SHIFTS)
+    p = api.make_pass(n, z, N_SHIFTS, 3)
+    ns = prep.info.n_sectors
+    stream = torch.cuda.Stream(device=dev_name)
+    sh = torch.tensor(shifts, device=dev_name)
+    lam = torch.full((ns,), LAMBDA, dtype=torch.float64, device=dev_name)
+    sums, fails = di.outputs(p)
+    scr, scr_bytes = di.scratch(p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev_name)
+    L = N.lib()
+    evals_per_step = ns * N_SHIFTS * n
+
+    def step(evs):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), p, sh.data_ptr(), lam.data_ptr(), scr,
+                                        scr_bytes, stream.cuda_stream), "qmc_eval_partials")
+            e1.record(stream)
+            N.check(L.qmc_reduce_partials(prep.packed, di.dpacked.data_ptr(), p, scr, scr_bytes, sums.data_ptr(),
+                                          fails.data_ptr(), stream.cuda_stream), "qmc_reduce_partials")
+            e2.record(stream)
+            evs.append((e0, e1, e2))
+
+    warm = []
+    for _ in range(args.warmup):
+        step(warm)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step(evs)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = t1 - t0
+    if dist:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev_name)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    eval_ms = [a.elapsed_time(b) for a, b, c in evs]
+    pass_ms = [a.elapsed_time(c) for a, b, c in evs]
+    assert int(fails.sum().item()) == 0, "sign check of the deformation failed in the benchmark workload"
+    value = world * evals_per_step * args.steps / elapsed
+    flops_launch = prep.info.flops_per_eval * evals_per_step
+    achieved = flops_launch / (statistics.mean(eval_ms) * 1e-3) / 1e12
+    kh = kernel_hash()
+    traffic = TRAFFIC_BYTES if (TRAFFIC_BYTES is not None and kh == KERNEL_HASH) else None
+
+    # e2e: the same pass through the host-buffer entry point, copies inside the timed region
+    ctx = api.Context(local, 1 << 30, stream)
+    import ctypes
+    packed_pinned = torch.frombuffer(bytearray(prep.packed), dtype=torch.uint8).pin_memory()
+    sh_pinned = torch.tensor(shifts).pin_memory()
+    lam_pinned = torch.full((ns,), LAMBDA, dtype=torch.float64).pin_memory()
+    sums_h = torch.zeros((ns, N_SHIFTS, prep.info.n_slots, 2), dtype=torch.float64).pin_memory()
+    fails_h = torch.zeros((ns, N_SHIFTS), dtype=torch.int64).pin_memory()
+
+    def e2e_step():
+        N.check(L.qmc_eval_sums_host(ctx._c, ctypes.c_void_p(packed_pinned.data_ptr()), p, sh_pinned.data_ptr(),
+                                     lam_pinned.data_ptr(), sums_h.data_ptr(), fails_h.data_ptr()),
+                "qmc_eval_sums_host")
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    te0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    te = time.perf_counter() - te0
+    if dist:
+        t = torch.tensor([te], dtype=torch.float64, device=dev_name)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    h2d = len(prep.packed) + sh_pinned.numel() * 8 + lam_pinned.numel() * 8
+    d2h = sums_h.numel() * 8 + fails_h.numel() * 8
+    ctx.close()
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream)
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(n),
+            "e2e": {"value": world * evals_per_step * args.steps / te, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                         "kernel": "qmc_eval_kernel<3,deform,0>", "flops_per_eval": prep.info.flops_per_eval,
+                         "eval_kernel_ms": statistics.mean(eval_ms), "pass_ms": statistics.mean(pass_ms),
+                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz (recipe FP64 1.25 TFLOP/s)",
+                         "kernel_hash": kh},
+            "clocks": clocks,
+        }
+        if not args.no_extras:
+            out["cpu_baseline"] = cpu_baseline()
+        out.update(extras)
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def time_to_accuracy(api, blob, cfg, device, stream, seeds=32):
+    """qmc_integrate of the massive box to 1e-3 relative error (lattice ladder from 2^10), over 32 seeds."""
+    ctx = api.Context(device, 1 << 30, stream)
+    iid = ctx.load_sectors(blob)
+    ctx.set_kinematics(iid, cfg.kin, 0, 0)
+    ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=999, lam=LAMBDA)  # warm-up
+    ts, ns, ok = [], [], 0
+    for s in range(seeds):
+        t0 = time.perf_counter()
+        r = ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=1000 + s, lam=LAMBDA)
+        ts.append(1e3 * (time.perf_counter() - t0))
+        ns.append(r.n_final)
+        ok += r.status == 0
+    ctx.close()
+    ts.sort()
+    return {"p50_ms": statistics.median(ts), "p99_ms": ts[min(len(ts) - 1, int(math.ceil(0.99 * len(ts))) - 1)],
+            "seeds": seeds, "converged": ok, "median_final_n": int(statistics.median(ns)), "precision": "f64"}
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        main_reference(a)
+    else:
+        main_ours(a)

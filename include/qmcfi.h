@@ -1,0 +1,231 @@
+/*
+ * qmcfi -- quasi-Monte Carlo evaluation of sector-decomposed Feynman integrals on one GB300 GPU (sm_103a).
+ *
+ * Method: Li, Wang, Yan, Zhao, "Efficient Numerical Evaluation of Feynman Integrals",
+ * Chin. Phys. C 40 (2016) 033103.  The library evaluates the eps-expansion coefficients of every sector
+ * integral of Sec. II, Eq. (9) -- with the endpoint subtraction of Eqs. (10)-(12) and, for sectors whose
+ * F polynomial changes sign, the contour deformation of Eq. (14) with its Jacobian -- at the points of a
+ * randomly shifted rank-1 lattice (Sec. III, Eqs. 17-18) after a periodising transform (Eq. 21), and sums
+ * them into per-shift estimates whose spread gives the error (Eqs. 19-20).
+ *
+ * Conventions
+ *   - Every function returns an int status: QMC_OK (0), QMC_PENDING (1), or a negative QMC_ERR_* code;
+ *     qmc_strerror() names it.  No C++ exception crosses this interface.
+ *   - Inputs are borrowed: the library copies what it keeps.  Outputs are caller-owned.  Pointers documented
+ *     as "device" must point to memory of the current CUDA device; all others are host pointers.
+ *   - Functions taking a `stream` (a cudaStream_t passed as void*, NULL = legacy default stream) are
+ *     asynchronous: they enqueue work and return; the caller synchronises before reading device outputs.
+ *   - A sector table is the binary format written by paper_1508_02512_gb300/tables.py (see qmc_prepare).
+ *   - Series slots: for a sector with sigma singular variables, slot n of its per-shift sums holds the
+ *     coefficient of eps^(n - sigma) of the sector integral; slots beyond the sector's order range are zero.
+ */
+#ifndef QMCFI_H
+#define QMCFI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QMC_OK 0
+#define QMC_PENDING 1
+#define QMC_ERR_ARG (-1)          /* bad argument (null pointer, size out of range, ...) */
+#define QMC_ERR_TABLE (-2)        /* malformed or inconsistent sector table */
+#define QMC_ERR_UNSUPPORTED (-3)  /* valid but outside what the kernels implement (dim > 6, exponent > 15, ...) */
+#define QMC_ERR_KINEMATICS (-4)   /* kinematics make a leading coefficient vanish */
+#define QMC_ERR_CUDA (-5)         /* a CUDA runtime call failed */
+#define QMC_ERR_MEMORY (-6)       /* device memory budget or capacity exceeded */
+#define QMC_ERR_DEFORMATION (-7)  /* Im F(z) > 0 persists after the lambda-halving cap */
+#define QMC_ERR_TIMEOUT (-8)      /* max_seconds reached before the requested accuracy */
+#define QMC_ERR_CANCELLED (-9)
+#define QMC_ERR_NOT_FOUND (-10)   /* unknown integral or request id */
+#define QMC_ERR_NO_DEVICE (-11)   /* no usable CUDA device */
+#define QMC_ERR_NOT_CONVERGED (-12) /* lattice ladder exhausted before the requested accuracy */
+
+#define QMC_MAX_DIM 6             /* sector dimension (7 propagators) */
+#define QMC_MAX_SLOTS 5           /* series slots per sector */
+#define QMC_MAX_ORDERS 8          /* Laurent orders of a result */
+
+enum { QMC_PREC_FP64 = 0, QMC_PREC_MIXED = 1 };
+
+/* A rank-1 lattice (Eq. 17): prime size n and generating vector z (a dim-d sector uses z[0..d-1]). */
+typedef struct {
+    int64_t n;
+    uint32_t z[QMC_MAX_DIM];
+} qmc_lattice;
+
+/* Summary of a prepared integral (filled by qmc_prepare). */
+typedef struct {
+    int32_t n_sectors, dim, loops, n_invariants;
+    int32_t order_min, order_max;  /* Laurent orders of the integral the preparation serves */
+    int32_t kmax;                  /* highest eps order needed from each sector integral */
+    int32_t n_slots;               /* series slots per sector in every output (<= QMC_MAX_SLOTS) */
+    int32_t n_deformed, n_negative, max_sigma, max_terms;
+    int32_t pre_low;               /* lowest eps power of Gamma(N_nu - L D/2) / prod Gamma(nu_j) */
+    int32_t n_pre;
+    double pre[QMC_MAX_ORDERS + 4]; /* its coefficients for eps^pre_low, eps^(pre_low+1), ... */
+    int64_t packed_bytes;          /* size of the packed device image */
+    double flops_per_eval;         /* algorithmic FP work per (sector, shift, point), mean over sectors */
+    double transcendentals_per_eval;
+} qmc_info;
+
+/* Per-sector description inside a packed image. */
+typedef struct {
+    int32_t kind;      /* 0: F > 0 on the cube; 1: F < 0 (real, phase exp(i pi eF(eps)) applied on the host);
+                          2: deformed (Eq. 14) */
+    int32_t sigma;     /* number of variables with exponent alpha = -1 (Eqs. 10-12) */
+    int32_t n_slots;   /* slots this sector fills */
+    int32_t n_terms;   /* polynomial terms staged in shared memory (U, F, dF, d2F) */
+    double flops;      /* algorithmic FP work per point */
+} qmc_sector_desc;
+
+/* One pass of the hot path over one integral: every sector x shift x lattice point. */
+typedef struct {
+    qmc_lattice lattice;
+    int32_t n_shifts;          /* m random shifts, 1..4096 */
+    int32_t transform_r;       /* periodising transform order 0..3 (Eq. 21 is r = 1) */
+    int32_t precision;         /* QMC_PREC_FP64 or QMC_PREC_MIXED */
+    int32_t block;             /* threads per block: 0 = default, else 64..512 and a multiple of 32 */
+    int32_t points_per_thread; /* 0 = default, else 1..64 */
+    int32_t grid;              /* blocks of the persistent kernel: 0 = one wave on the device */
+} qmc_pass;
+
+/* Text for a status code (static storage). */
+const char *qmc_strerror(int status);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int qmc_version(void);
+
+/*
+ * qmc_prepare -- host only; no CUDA call.
+ * Parses and validates a sector table (Sec. II, Eq. 9: per sector the exponents A_j + B_j eps and the
+ * polynomials Ut, Ft with coefficients linear in the kinematic invariants), evaluates the coefficients at
+ * `invariants` (n_invariants values in the table's invariant order), classifies every sector by the signs of
+ * Ft's coefficients (kind 0/1/2), derives for deformed sectors the gradient and Hessian polynomials of Ft that
+ * Eq. (14) and its Jacobian need, computes the Gamma prefactor series of Eq. (2), and writes the packed image
+ * that the kernels read (relocatable: offsets only; copy it to device memory as is).
+ *   order_min..order_max: Laurent orders of the integral the image must serve (order_max - order_min < 8).
+ *   packed: output buffer of packed_capacity bytes, or NULL to query info->packed_bytes only.
+ * Errors: QMC_ERR_ARG, QMC_ERR_TABLE, QMC_ERR_UNSUPPORTED, QMC_ERR_KINEMATICS, QMC_ERR_MEMORY (capacity).
+ */
+int qmc_prepare(const void *table, size_t table_bytes, const double *invariants, int32_t n_invariants,
+                int32_t order_min, int32_t order_max, void *packed, size_t packed_capacity, qmc_info *info);
+
+/* Description of sector `sector` (table order) of a packed image (host pointer).  QMC_ERR_ARG if out of range. */
+int qmc_sector_desc_get(const void *packed, int32_t sector, qmc_sector_desc *out);
+
+/* Bytes of device scratch that qmc_eval_sums needs for `pass` on this image (per-item partial sums, fail
+ * counters and work counters).  Returns 0 for invalid arguments. */
+size_t qmc_scratch_bytes(const void *packed, const qmc_pass *pass);
+
+/*
+ * qmc_eval_sums -- the hot path (Sec. III, Eqs. 16-18), asynchronous on `stream`.
+ * For every sector s, shift k and slot n:
+ *   sums[((s * n_shifts) + k) * n_slots + n] = sum_{i < lattice.n} w(x_i) I_s(t(x_i)) coefficient n,
+ *   x_i = {i z / n + Delta_k},  stored as (re, im) double pairs,
+ *   fails[s * n_shifts + k] = number of points of deformed sectors with Im F(z) > 0 (Eq. 14 sign check).
+ * packed_host / packed_dev: the same image in host and device memory.  shifts_dev: n_shifts x 6 doubles in
+ * [0,1).  lambda_dev: one deformation parameter per sector (table order).  scratch_dev: at least
+ * qmc_scratch_bytes() bytes, 256-byte aligned, owned by the caller; contents need no initialisation and are
+ * overwritten.  Sums are deterministic: independent of grid size and scheduling for fixed block and
+ * points_per_thread.  Errors: QMC_ERR_ARG, QMC_ERR_UNSUPPORTED, QMC_ERR_MEMORY (scratch too small), QMC_ERR_CUDA.
+ */
+int qmc_eval_sums(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shifts_dev,
+                  const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, double *sums_dev,
+                  int64_t *fails_dev, void *stream);
+
+/* The two launches of qmc_eval_sums, exposed separately (same arguments and semantics): qmc_eval_partials runs
+ * the evaluation kernel and leaves one partial sum per work item and slot in the scratch buffer;
+ * qmc_reduce_partials sums them per (sector, shift) in a fixed order into sums/fails.  The scratch buffer must
+ * not be reused between the two calls. */
+int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shifts_dev,
+                      const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, void *stream);
+int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const void *scratch_dev,
+                        size_t scratch_bytes, double *sums_dev, int64_t *fails_dev, void *stream);
+
+/*
+ * qmc_eval_points -- per-point values of one sector (for sampled checks), asynchronous on `stream`.
+ * For each j < npts: out[j * n_slots + n] = w(x) I_s(t(x)) coefficient n at x = {idx[j] z / n + Delta},
+ * Delta = shift_dev[0..5], computed by the same device code as qmc_eval_sums.  idx_dev: npts int64 lattice
+ * indices in [0, lattice.n).  out_dev: npts x n_slots (re, im) pairs.  fails_dev: npts int32 flags.
+ */
+int qmc_eval_points(const void *packed_host, const void *packed_dev, int32_t sector, const qmc_pass *pass,
+                    const double *shift_dev, double lambda, const int64_t *idx_dev, int64_t npts, double *out_dev,
+                    int32_t *fails_dev, void *stream);
+
+/* Built-in lattice ladder (largest prime below 2^k, k = 10..26, fast-CBC vectors).  Copies up to `cap`
+ * entries into `out` and returns how many exist. */
+int qmc_builtin_lattices(qmc_lattice *out, int32_t cap);
+
+/* Combine per-shift sector sums of one pass into the Laurent coefficients of the integral (Sec. III,
+ * Eqs. 16-20; host only).  sums: as written by qmc_eval_sums (host copy).  Q: n_shifts x n_orders (re, im)
+ * per-shift estimates, n_orders = order_max - order_min + 1 of the image; mean/err: n_orders (re, im) each;
+ * err holds the standard errors of the real and imaginary parts. */
+int qmc_combine(const void *packed_host, const qmc_pass *pass, const double *sums, double *Q, double *mean,
+                double *err);
+
+/* ------------------------------------------------------------------ integrate to a requested accuracy */
+
+typedef struct qmc_ctx qmc_ctx;
+
+typedef struct {
+    double rel_tol;          /* stop when every order meets err <= rel_tol * max(|value|, 1e-6 * max |value|) */
+    double abs_tol;          /* ... or err <= abs_tol */
+    int32_t precision;       /* QMC_PREC_FP64 / QMC_PREC_MIXED */
+    int32_t n_shifts;        /* m (default 16) */
+    uint64_t seed;           /* shifts: splitmix64 from this state, 6 draws per shift */
+    double lambda;           /* initial deformation parameter (Eq. 14); halved per failing sector */
+    int32_t max_halvings;    /* cap on lambda halvings per sector (default 6) */
+    int32_t transform_r;     /* default 3 */
+    int32_t ladder_start;    /* index into the built-in ladder where the loop starts (0 = 2^10) */
+    int32_t n_lattices;      /* > 0: use `lattices` instead of the built-in ladder */
+    const qmc_lattice *lattices;
+    const double *shifts;    /* optional n_shifts x 6 host array overriding the seed */
+    int64_t max_n;           /* stop the ladder above this lattice size (0 = no limit) */
+    double max_seconds;      /* 0 = no limit */
+    int32_t block, points_per_thread; /* launch shape (0 = default) */
+} qmc_options;
+
+typedef struct {
+    int32_t status;
+    int32_t order_min, n_orders;
+    double value[QMC_MAX_ORDERS][2];  /* Laurent coefficients (re, im), order_min + k */
+    double error[QMC_MAX_ORDERS][2];  /* standard errors of re and im (Eq. 20) */
+    int64_t n_final;                  /* lattice size of the last pass */
+    int64_t evals;                    /* sector x shift x point evaluations, all passes */
+    double seconds;                   /* wall time of qmc_integrate */
+    double kernel_ms;                 /* device time of the evaluation kernels, all passes */
+    int32_t passes, lambda_halvings, fp64_reruns, sign_failures;
+} qmc_result;
+
+/* Context: owns a CUDA stream binding, the device copies of loaded integrals and its scratch.
+ * device: CUDA ordinal; mem_budget: bytes of device memory the context may hold (0 = 1 GiB);
+ * stream: cudaStream_t to launch on (NULL = the legacy default stream). */
+int qmc_create(qmc_ctx **out, int32_t device, size_t mem_budget, void *stream);
+int qmc_destroy(qmc_ctx *ctx);
+
+/* Copies a sector table into the context; returns its id. */
+int qmc_load_sectors(qmc_ctx *ctx, const void *table, size_t table_bytes, int32_t *integral_id);
+
+/* Evaluates the table at a kinematic point for Laurent orders order_min..order_max and uploads the packed
+ * image (qmc_prepare semantics). */
+int qmc_set_kinematics(qmc_ctx *ctx, int32_t integral_id, const double *invariants, int32_t n_invariants,
+                       int32_t order_min, int32_t order_max);
+
+/* One pass with host buffers (blocking): copies the packed image, shifts and per-sector lambda from host memory to
+ * context-owned device buffers, runs qmc_eval_sums on the context's stream and copies sums and fails back to the
+ * host (layouts as in qmc_eval_sums).  Pinned host memory makes the copies asynchronous DMA. */
+int qmc_eval_sums_host(qmc_ctx *ctx, const void *packed_host, const qmc_pass *pass, const double *shifts_host,
+                       const double *lambda_host, double *sums_host, int64_t *fails_host);
+
+/* Blocking: climbs the lattice ladder, running one pass per size (all sectors and shifts), halving lambda of
+ * sectors that fail the sign check, until every order meets the tolerance (or a limit is reached).
+ * Returns the status also stored in out->status. */
+int qmc_integrate(qmc_ctx *ctx, int32_t integral_id, const qmc_options *opt, qmc_result *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCFI_H */

@@ -1,0 +1,196 @@
+"""CPU checks of the product side: the C-ABI library loads and exports every symbol include/qmcfi.h declares; the
+host-only entry points (table validation, packing, prefactor, combination) agree with the oracle; the table
+compiler and the fast CBC reproduce the oracle's decomposition and CBC exactly (integer data, bit for bit)."""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import integrate as OI
+from oracle import lattice as OL
+from oracle import sectors as OS
+from paper_1508_02512_gb300 import _native as N
+from paper_1508_02512_gb300 import api
+from paper_1508_02512_gb300 import lattice as PL
+from paper_1508_02512_gb300 import tables as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LEGS0 = dict(pp1=0.0, pp2=0.0, pp3=0.0, pp4=0.0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1508_02512_gb300 import build
+    build.build()
+    N.lib()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "qmcfi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(qmc_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    names = header_functions()
+    assert len(names) >= 15
+    L = N.lib()
+    for nm in names:
+        assert hasattr(L, nm), nm
+        assert nm in N.PROTOTYPES, f"{nm} has no Python binding"
+    assert set(N.PROTOTYPES) == set(names)
+
+
+def test_strerror_and_version():
+    assert N.strerror(0) == "ok"
+    assert "table" in N.strerror(N.QMC_ERR_TABLE)
+    assert N.lib().qmc_version() >= 100
+
+
+def canon_product(leaves, meta):
+    names = meta["invariants"]
+
+    def pk(P):
+        return tuple(sorted((tuple(int(v) for v in e),
+                             tuple(sorted((names[k - 1] if k else "1", Fraction(float(c[k])))
+                                          for k in range(len(c)) if c[k] != 0)))
+                            for e, c in zip(P.e, P.c)))
+
+    return tuple(sorted((tuple(int(a) for a in s.A), tuple(int(b) for b in s.B), pk(s.U), pk(s.F)) for s in leaves))
+
+
+@pytest.mark.parametrize("cfg", W.CONFIGS, ids=lambda c: c.name)
+def test_table_compiler_matches_oracle_decomposition(cfg):
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    meta, leaves = T.read_table(blob)
+    mine = canon_product(leaves, meta)
+    ref = OS.canonical(OS.decompose(cfg.topology, OS.zero_invariants_of(cfg.topology, cfg.point)))
+    assert mine == ref
+
+
+def test_symanzik_matches_oracle_for_all_topologies():
+    from oracle import feynman as fy
+    for topo in (W.bubble(True), W.triangle_massive(), W.box(True), W.double_box_planar(True),
+                 W.double_box_nonplanar(True)):
+        U, F = T.symanzik(topo)
+        Uo, Fo = fy.symanzik_momentum(topo)
+        names = topo.invariants
+
+        def conv(P):
+            return {tuple(int(v) for v in e): {(names[k - 1] if k else "1"): Fraction(float(c[k]))
+                                               for k in range(len(c)) if c[k] != 0} for e, c in zip(P.e, P.c)}
+
+        assert conv(U) == Uo and conv(F) == Fo
+
+
+@pytest.mark.parametrize("n", [101, 1009, 1021, 2039, 4093])
+def test_fast_cbc_matches_oracle_cbc(n):
+    assert PL.fast_cbc(n) == OL.cbc_plain(n, 6)
+
+
+def test_builtin_lattices():
+    lat = api.builtin_lattices()
+    assert [n for n, _ in lat] == [OL.prime_below(1 << k) for k in range(10, 10 + len(lat))]
+    for n, z in lat[:3]:
+        assert z == OL.cbc_plain(n, 6)
+    # the criterion decreases along the ladder
+    e = [OL.cbc_error2(n, z) for n, z in lat[:6]]
+    assert all(a > b for a, b in zip(e, e[1:]))
+
+
+@pytest.mark.parametrize("cfg", W.CONFIGS, ids=lambda c: c.name)
+def test_prepare_matches_oracle(cfg):
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
+    prob = OI.make_problem(cfg.topology, cfg.point, cfg.order_min, cfg.order_max)
+    assert prep.info.n_sectors == len(prob.sectors)
+    assert prep.info.pre_low == prob.pre_low
+    k = min(prep.info.n_pre, 6)
+    assert np.allclose(list(prep.info.pre)[:k], prob.pre[:k], rtol=1e-14, atol=1e-15)
+    for s, sec in enumerate(prob.sectors):
+        d = prep.sector(s)
+        assert (d.kind, d.sigma) == (sec.kind, sec.sigma)
+    assert prep.info.flops_per_eval > 0
+
+
+def test_prefactor_with_pole_matches_oracle():
+    blob = T.compile_integral(W.bubble(False), ())
+    prep = api.prepare(blob, np.array([-2.0]), -1, 3)
+    prob = OI.make_problem(W.bubble(False), dict(pp1=-2.0), -1, 3)
+    assert prep.info.pre_low == prob.pre_low == -1
+    assert np.allclose(list(prep.info.pre)[:6], prob.pre[:6], rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("cfg", [W.CONFIG0, W.CONFIG1], ids=lambda c: c.name)
+def test_combine_matches_oracle(cfg):
+    """qmc_combine and the oracle's combination agree on the same (synthetic) per-sector sums."""
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
+    prob = OI.make_problem(cfg.topology, cfg.point, cfg.order_min, cfg.order_max)
+    m, n = 6, 1021
+    rng = np.random.default_rng(1)
+    slots = prep.info.n_slots
+    sums = np.zeros((prep.info.n_sectors, m, slots, 2))
+    per = []
+    for s, sec in enumerate(prob.sectors):
+        nout = prob.kmax + sec.sigma + 1
+        v = rng.normal(size=(m, nout)) + 1j * rng.normal(size=(m, nout))
+        per.append(v)
+        sums[s, :, :nout, 0] = v.real
+        sums[s, :, :nout, 1] = v.imag
+    p = api.make_pass(n, [1] * 6, m)
+    Q, mean, err = api.combine(prep, p, sums)
+    Qo = OI.combine(prob, per, n)
+    mo, eo = OI.mean_and_error(Qo)
+    assert np.allclose(Q, Qo, rtol=1e-13, atol=1e-15)
+    assert np.allclose(mean, mo, rtol=1e-13, atol=1e-15)
+    assert np.allclose(np.hypot(err[:, 0], err[:, 1]), eo, rtol=1e-12)
+
+
+def _prep_status(blob, kin, omin=0, omax=0):
+    inv = np.ascontiguousarray(np.asarray(kin, dtype=np.float64))
+    info = N.qmc_info()
+    return N.lib().qmc_prepare(blob, len(blob), inv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(inv), omin,
+                               omax, None, 0, ctypes.byref(info))
+
+
+def test_prepare_rejects_malformed_tables():
+    cfg = W.CONFIG1
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    kin = cfg.kin
+    assert _prep_status(blob, kin) == 0
+    assert _prep_status(b"XXXXXXXX" + blob[8:], kin) == N.QMC_ERR_TABLE          # bad magic
+    assert _prep_status(blob[:-8], kin) == N.QMC_ERR_TABLE                         # truncated
+    assert _prep_status(blob + b"\0" * 8, kin) == N.QMC_ERR_TABLE                  # trailing bytes
+    assert _prep_status(blob, kin[:-1]) == N.QMC_ERR_ARG                           # wrong invariant count
+    assert _prep_status(blob, kin, 0, 9) == N.QMC_ERR_ARG                          # too many orders
+    meta, leaves = T.read_table(blob)
+    bad = [T.SectorRecord(s.A.copy(), s.B.copy(), s.U, s.F, s.D) for s in leaves]
+    bad[0].A[0] = -2                                                               # alpha <= -2
+    assert _prep_status(T.write_table(bad, meta), kin) == N.QMC_ERR_UNSUPPORTED
+    bad[0].A[0] = -1
+    bad[0].B[0] = 0                                                                # unregulated pole
+    assert _prep_status(T.write_table(bad, meta), kin) == N.QMC_ERR_TABLE
+    # kinematics that make the constant term of F vanish: msq = 0 for the massive box
+    k2 = kin.copy()
+    k2[list(cfg.topology.invariants).index("msq")] = 0.0
+    assert _prep_status(blob, k2) == N.QMC_ERR_KINEMATICS
+    nan = kin.copy()
+    nan[0] = np.nan
+    assert _prep_status(blob, nan) == N.QMC_ERR_ARG
+
+
+def test_pass_validation_on_host():
+    cfg = W.CONFIG1
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, 0, 0)
+    good = api.make_pass(1021, [1, 2, 3, 4, 5, 6], 4)
+    assert api.scratch_bytes(prep, good) > 0
+    for bad in (api.make_pass(1, [1] * 6, 4), api.make_pass(1021, [0, 1, 1, 1, 1, 1], 4),
+                api.make_pass(1021, [1] * 6, 0), api.make_pass(1021, [1] * 6, 4, transform_r=7),
+                api.make_pass(1021, [1] * 6, 4, block=48), api.make_pass(1021, [1] * 6, 4, points_per_thread=65)):
+        assert api.scratch_bytes(prep, bad) == 0
