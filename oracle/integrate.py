@@ -98,8 +98,10 @@ def point_series(sec: NumSector, e4, x, lam: float, r: int, kmax: int):
 
 
 def lattice_sums(sec: NumSector, e4, n: int, z, shifts, lam: float, r: int, kmax: int,
-                 nthreads: Optional[int] = None):
-    """Per-shift sums over the n lattice points: (sums[m, nout] complex, l1[m, nout], fails[m])."""
+                 nthreads: Optional[int] = None, with_scale: bool = False):
+    """Per-shift sums over the n lattice points: (sums[m, nout] complex, l1[m, nout], fails[m]); with_scale adds
+    l1c[m, nout], the summed magnitude of the terms that the endpoint subtraction cancels (Sec. II, after
+    Eq. 12: the subtracted remainder suffers from large cancellation) -- the scale of rounding differences."""
     M = kmax + sec.sigma
     nout = M + 1
     args, keep = _sector_args(sec, e4, lam, r, M)
@@ -108,14 +110,18 @@ def lattice_sums(sec: NumSector, e4, n: int, z, shifts, lam: float, r: int, kmax
     m = sh.shape[0]
     sums = np.zeros(2 * m * nout)
     l1 = np.zeros(m * nout)
+    l1c = np.zeros(m * nout)
     fails = np.zeros(m, dtype=np.int64)
     nt = nthreads or os.cpu_count() or 1
     rc = native.lib().oracle_lattice_sums(*args, nout, int(n), _ptr(z, ctypes.c_longlong),
                                           _ptr(sh, ctypes.c_double), m, nt, _ptr(sums, ctypes.c_double),
-                                          _ptr(l1, ctypes.c_double), _ptr(fails, ctypes.c_longlong))
+                                          _ptr(l1, ctypes.c_double), _ptr(l1c, ctypes.c_double),
+                                          _ptr(fails, ctypes.c_longlong))
     if rc != 0:
         raise ValueError("oracle_lattice_sums rejected its arguments")
     s = sums[0::2] + 1j * sums[1::2]
+    if with_scale:
+        return s.reshape(m, nout), l1.reshape(m, nout), fails, l1c.reshape(m, nout)
     return s.reshape(m, nout), l1.reshape(m, nout), fails
 
 

@@ -32,7 +32,7 @@ def lib():
         sector_args = [i, i, P(i), P(i), d, P(i), i, P(d), P(i), i, P(d), P(i), d, i, i]
         _lib.oracle_point.argtypes = sector_args + [P(d), P(d), i]
         _lib.oracle_point.restype = i
-        _lib.oracle_lattice_sums.argtypes = sector_args + [i, ll, P(ll), P(d), i, i, P(d), P(d), P(ll)]
+        _lib.oracle_lattice_sums.argtypes = sector_args + [i, ll, P(ll), P(d), i, i, P(d), P(d), P(d), P(ll)]
         _lib.oracle_lattice_sums.restype = i
         _lib.oracle_cbc_component.argtypes = [ll, P(d), P(ll), ll, i, P(d), P(d)]
         _lib.oracle_cbc_component.restype = i

@@ -215,11 +215,14 @@ typedef struct {
     const double *t, *tm;
     int sing[OR_MAXDIM], sig;
     cplx memo[1 << 6][OR_MAXSER];
+    double amemo[1 << 6][OR_MAXSER]; /* |coefficients| of the same leaves */
     int have[1 << 6];
     int fail;
 } sub_ctx;
 
-static void subtracted(sub_ctx *c, int i, unsigned Y, cplx *res) {
+/* res: the subtracted Laurent series; mag: the same recursion applied to magnitudes (|t^{-1+B eps}| (|a| + |b|)
+   + |b|/|B|), i.e. the size of the terms that cancel in Eq. (11) -- the scale of its rounding errors. */
+static void subtracted(sub_ctx *c, int i, unsigned Y, cplx *res, double *mag) {
     int L = c->sig + c->s->M + 1;
     if (i == c->sig) {
         int slot = 0;
@@ -228,17 +231,25 @@ static void subtracted(sub_ctx *c, int i, unsigned Y, cplx *res) {
         if (!c->have[slot]) {
             cplx g[OR_MAXSER];
             c->fail |= g_series(c->s, c->t, c->tm, Y, g);
-            for (int k = 0; k < L; ++k) c->memo[slot][k] = 0.0;
-            for (int n = 0; n <= c->s->M; ++n) c->memo[slot][c->sig + n] = g[n];
+            for (int k = 0; k < L; ++k) {
+                c->memo[slot][k] = 0.0;
+                c->amemo[slot][k] = 0.0;
+            }
+            for (int n = 0; n <= c->s->M; ++n) {
+                c->memo[slot][c->sig + n] = g[n];
+                c->amemo[slot][c->sig + n] = cabs(g[n]);
+            }
             c->have[slot] = 1;
         }
         memcpy(res, c->memo[slot], sizeof(cplx) * L);
+        memcpy(mag, c->amemo[slot], sizeof(double) * L);
         return;
     }
     int j = c->sing[i];
     cplx a[OR_MAXSER], b[OR_MAXSER], tser[OR_MAXSER];
-    subtracted(c, i + 1, Y, a);
-    subtracted(c, i + 1, Y | (1u << j), b);
+    double am[OR_MAXSER], bm[OR_MAXSER];
+    subtracted(c, i + 1, Y, a, am);
+    subtracted(c, i + 1, Y | (1u << j), b, bm);
     /* t_j^{-1 + B eps} = (1/t_j) exp(B eps log t_j): power series in eps */
     double lt = log(c->t[j]), Bj = c->s->B[j];
     double term = 1.0 / c->t[j];
@@ -252,12 +263,15 @@ static void subtracted(sub_ctx *c, int i, unsigned Y, cplx *res) {
         /* pole term: b / (B eps) moves every order down by one */
         cplx pole = (o + 1 < L) ? b[o + 1] / Bj : 0.0;
         res[o] = acc + pole;
+        double macc = 0.0;
+        for (int n = 0; n <= o; ++n) macc += cabs(tser[n]) * (am[o - n] + bm[o - n]);
+        mag[o] = macc + ((o + 1 < L) ? bm[o + 1] / fabs(Bj) : 0.0);
     }
 }
 
 /* Sector integrand times transform weight at the (already shifted) point x in [0,1)^dim.
    out: 2*(sig+kmax+1) doubles (re, im) for orders -sig .. kmax, where kmax = M - sig.  Returns sign-failure flag. */
-static int point_value(const or_sector *s, const double *x, cplx *out, int nout) {
+static int point_value(const or_sector *s, const double *x, cplx *out, double *mag, int nout) {
     int d = s->dim;
     double t[OR_MAXDIM], tm[OR_MAXDIM], w = 1.0;
     for (int j = 0; j < d; ++j) {
@@ -265,7 +279,10 @@ static int point_value(const or_sector *s, const double *x, cplx *out, int nout)
         tm[j] = phi(s->r, 1.0 - x[j]);
         w *= dphi(s->r, x[j]);
     }
-    for (int k = 0; k < nout; ++k) out[k] = 0.0;
+    for (int k = 0; k < nout; ++k) {
+        out[k] = 0.0;
+        mag[k] = 0.0;
+    }
     if (w == 0.0) return 0;
     for (int j = 0; j < d; ++j)
         if (t[j] == 0.0 || tm[j] == 0.0) return 0;
@@ -277,10 +294,14 @@ static int point_value(const or_sector *s, const double *x, cplx *out, int nout)
     for (int j = 0; j < d; ++j)
         if (s->A[j] == -1) c->sing[c->sig++] = j;
     cplx res[OR_MAXSER];
-    subtracted(c, 0, 0u, res);
+    double rm[OR_MAXSER];
+    subtracted(c, 0, 0u, res, rm);
     int fail = c->fail;
     int L = c->sig + s->M + 1;
-    for (int k = 0; k < nout && k < L; ++k) out[k] = w * res[k];
+    for (int k = 0; k < nout && k < L; ++k) {
+        out[k] = w * res[k];
+        mag[k] = w * rm[k];
+    }
     free(c);
     return fail;
 }
@@ -317,7 +338,8 @@ int oracle_point(int dim, int kind, const int *A, const int *B, double D, const 
     or_sector s;
     fill_sector(&s, dim, kind, A, B, D, e4, nU, cU, xU, nF, cF, xF, lam, r, M);
     cplx v[OR_MAXSER];
-    int f = point_value(&s, x, v, nout);
+    double mg[OR_MAXSER];
+    int f = point_value(&s, x, v, mg, nout);
     for (int k = 0; k < nout; ++k) {
         out[2 * k] = creal(v[k]);
         out[2 * k + 1] = cimag(v[k]);
@@ -326,18 +348,19 @@ int oracle_point(int dim, int kind, const int *A, const int *B, double D, const 
 }
 
 /* Shifted lattice sums: for each shift k, sums[k][o] = sum_{i<n} w * integrand({i z/n + Delta_k}) (Kahan),
-   l1[k][o] = sum_i |value|, fails[k] = number of points with Im Ft(z) > 0.  shifts: m x 6 doubles. */
+   l1[k][o] = sum_i |value|, l1c[k][o] = sum_i (magnitude of the terms the subtraction cancels, see
+   subtracted()), fails[k] = number of points with Im Ft(z) > 0.  shifts: m x 6 doubles. */
 int oracle_lattice_sums(int dim, int kind, const int *A, const int *B, double D, const int *e4, int nU,
                         const double *cU, const int *xU, int nF, const double *cF, const int *xF, double lam, int r,
                         int M, int nout, long long n, const long long *z, const double *shifts, int m, int nthreads,
-                        double *sums, double *l1, long long *fails) {
+                        double *sums, double *l1, double *l1c, long long *fails) {
     if (dim < 1 || dim > OR_MAXDIM || M + dim + 1 > OR_MAXSER || n < 1) return -1;
     or_sector s;
     fill_sector(&s, dim, kind, A, B, D, e4, nU, cU, xU, nF, cF, xF, lam, r, M);
     if (nthreads < 1) nthreads = 1;
     for (int k = 0; k < m; ++k) {
         const double *delta = shifts + 6 * k;
-        double *part = (double *)calloc((size_t)nthreads * nout * 5, sizeof(double));
+        double *part = (double *)calloc((size_t)nthreads * nout * 6, sizeof(double));
         long long *pf = (long long *)calloc((size_t)nthreads, sizeof(long long));
 #pragma omp parallel num_threads(nthreads)
         {
@@ -347,17 +370,18 @@ int oracle_lattice_sums(int dim, int kind, const int *A, const int *B, double D,
             nt = omp_get_num_threads();
 #endif
             long long lo = n * tid / nt, hi = n * (tid + 1) / nt;
-            double *ps = part + (size_t)tid * nout * 5; /* re, im, cre, cim, l1 per order */
+            double *ps = part + (size_t)tid * nout * 6; /* re, im, cre, cim, l1, l1c per order */
             double x[OR_MAXDIM];
             cplx v[OR_MAXSER];
+            double mg[OR_MAXSER];
             for (long long i = lo; i < hi; ++i) {
                 for (int j = 0; j < dim; ++j) {
                     double xi = (double)((i * z[j]) % n) / (double)n + delta[j];
                     x[j] = xi >= 1.0 ? xi - 1.0 : xi;
                 }
-                pf[tid] += point_value(&s, x, v, nout);
+                pf[tid] += point_value(&s, x, v, mg, nout);
                 for (int o = 0; o < nout; ++o) {
-                    double *a = ps + 5 * o;
+                    double *a = ps + 6 * o;
                     double y = creal(v[o]) - a[2];
                     double tt = a[0] + y;
                     a[2] = (tt - a[0]) - y;
@@ -367,13 +391,14 @@ int oracle_lattice_sums(int dim, int kind, const int *A, const int *B, double D,
                     a[3] = (tt - a[1]) - y;
                     a[1] = tt;
                     a[4] += cabs(v[o]);
+                    a[5] += mg[o];
                 }
             }
         }
         for (int o = 0; o < nout; ++o) {
-            double re = 0, im = 0, cre = 0, cim = 0, ab = 0;
+            double re = 0, im = 0, cre = 0, cim = 0, ab = 0, abc = 0;
             for (int tid = 0; tid < nthreads; ++tid) {
-                double *a = part + (size_t)tid * nout * 5 + 5 * o;
+                double *a = part + (size_t)tid * nout * 6 + 6 * o;
                 double y = a[0] - cre, tt = re + y;
                 cre = (tt - re) - y;
                 re = tt;
@@ -382,10 +407,12 @@ int oracle_lattice_sums(int dim, int kind, const int *A, const int *B, double D,
                 cim = (tt - im) - y;
                 im = tt;
                 ab += a[4];
+                abc += a[5];
             }
             sums[2 * (k * nout + o)] = re;
             sums[2 * (k * nout + o) + 1] = im;
             l1[k * nout + o] = ab;
+            l1c[k * nout + o] = abc;
         }
         long long f = 0;
         for (int tid = 0; tid < nthreads; ++tid) f += pf[tid];

@@ -74,13 +74,13 @@ def compare(prep, prob, sums, lams, n, z, shifts, r=3, tol=TOL):
     for s, sec in enumerate(prob.sectors):
         d = prep.sector(s)
         assert d.kind == sec.kind and d.sigma == sec.sigma
-        osum, l1, ofail = OI.lattice_sums(sec, prob.e4, n, z, shifts, lams[s], r, prob.kmax)
+        osum, l1, ofail, l1c = OI.lattice_sums(sec, prob.e4, n, z, shifts, lams[s], r, prob.kmax, with_scale=True)
         nout = osum.shape[1]
         g = sums[s, :, :nout]
         err = np.abs(g - osum)
-        bound = tol * np.maximum(l1, 1e-300)
-        worst = max(worst, float(np.max(err / np.maximum(l1, 1e-300))))
-        assert np.all(err <= bound + 1e-300), (s, err.max(), l1.max())
+        scale = np.maximum(l1c, 1e-300)
+        worst = max(worst, float(np.max(err / scale)))
+        assert np.all(err <= tol * scale + 1e-300), (s, float(np.max(err / scale)))
         # slots beyond the sector's orders stay zero
         assert np.all(sums[s, :, nout:] == 0)
     return worst
