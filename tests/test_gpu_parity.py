@@ -179,9 +179,12 @@ def test_full_size_bench_workload_sampled_points():
             g = g[..., 0] + 1j * g[..., 1]
             x = ((idx[:, None] * np.asarray(z[:3], dtype=np.int64)[None, :]) % n) / n + shifts[k][None, :3]
             x = np.where(x >= 1.0, x - 1.0, x)
-            for j in range(len(idx)):
-                ref, _ = OI.point_series(sec, prob.e4, x[j], 0.5, 3, prob.kmax)
-                assert abs(g[j, 0] - ref[0]) <= 1e-12 * max(abs(ref[0]), 1e-300) + 1e-300, (s, k, idx[j])
+            ref = np.array([OI.point_series(sec, prob.e4, x[j], 0.5, 3, prob.kmax)[0][0] for j in range(len(idx))])
+            # 1e-12 of each value, with the sample's mean magnitude as floor (like the sums' L1 normalisation):
+            # near-corner points carry a vanishing transform weight and are not judged relative to themselves
+            floor = np.mean(np.abs(ref))
+            bad = np.abs(g[:, 0] - ref) > 1e-12 * np.maximum(np.abs(ref), floor)
+            assert not bad.any(), (s, k, idx[bad][:5], g[bad, 0][:5], ref[bad][:5])
 
 
 def test_full_size_bench_workload_estimate():
