@@ -146,6 +146,21 @@ int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const q
                         size_t scratch_bytes, double *sums_dev, int64_t *fails_dev, void *stream);
 
 /*
+ * qmc_eval_sums_noalloc -- qmc_eval_sums without a caller-provided scratch buffer, for callers that cannot
+ * allocate device memory (e.g. an application whose own pool allocator holds all device memory, or a
+ * latency-critical loop that forbids allocation after start-up).  The paper has no counterpart: this is a
+ * deployment convenience.  Same inputs, outputs and results as qmc_eval_sums; the scratch is a fixed 32 MiB
+ * array inside the library that every GPU loading the library holds until exit.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress, with the device current), so make it before any
+ * stream capture.  Calls share the array: calls that overlap on the GPU race; calls in one stream are ordered.
+ * Allocates nothing (no cudaMalloc/cudaFree).  Returns QMC_ERR_MEMORY when the pass needs more scratch than
+ * 32 MiB (qmc_scratch_bytes() > 33554432), QMC_ERR_ARG for invalid passes.
+ */
+int qmc_eval_sums_noalloc(const void *packed_host, const void *packed_dev, const qmc_pass *pass,
+                          const double *shifts_dev, const double *lambda_dev, double *sums_dev, int64_t *fails_dev,
+                          void *stream);
+
+/*
  * qmc_eval_points -- per-point values of one sector (for sampled checks), asynchronous on `stream`.
  * For each j < npts: out[j * n_slots + n] = w(x) I_s(t(x)) coefficient n at x = {idx[j] z / n + Delta},
  * Delta = shift_dev[0..5], computed by the same device code as qmc_eval_sums.  idx_dev: npts int64 lattice

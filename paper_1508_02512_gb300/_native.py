@@ -85,6 +85,8 @@ PROTOTYPES = {
                                   c_void_p]),
     "qmc_reduce_partials": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_size_t, c_void_p, c_void_p,
                                     c_void_p]),
+    "qmc_eval_sums_noalloc": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p]),
     "qmc_eval_points": (c_int, [c_void_p, c_void_p, c_int32, POINTER(qmc_pass), c_void_p, c_double, c_void_p,
                                 c_int64, c_void_p, c_void_p, c_void_p]),
     "qmc_builtin_lattices": (c_int, [POINTER(qmc_lattice), c_int32]),

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmcfi.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_host.cpp"] + [f"qmc_kern_d{d}.cu" for d in range(1, 7)]
+SOURCES = ["qmc_kernels.cu", "qmc_host.cpp", "qmc_noalloc.cu"] + [f"qmc_kern_d{d}.cu" for d in range(1, 7)]
 
 
 def nvcc() -> str:
