@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-accuracy and CPU baseline")
+    ap.add_argument("--profile-pass", action="store_true",
+                    help="run two passes of the same integral at n = 1048573 and exit (small case for ncu)")
     return ap.parse_args()
 
 
@@ -348,9 +350,31 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32):
             "seeds": seeds, "converged": ok, "median_final_n": int(statistics.median(ns)), "precision": "f64"}
 
 
+def profile_pass():
+    """Two passes of the benchmark integral at n = 1048573 (largest prime below 2^20), 16 shifts."""
+    import torch
+    from paper_1508_02512_gb300 import api
+    from paper_1508_02512_gb300 import tables as T
+    cfg = W.CONFIG1
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, 0, 0)
+    dev = api.DeviceIntegral(prep)
+    n = 1048573
+    p = api.make_pass(n, dict(api.builtin_lattices())[n], N_SHIFTS, 3)
+    sh = torch.tensor(W.shifts(cfg.seed, N_SHIFTS), device="cuda")
+    lam = torch.full((prep.info.n_sectors,), LAMBDA, dtype=torch.float64, device="cuda")
+    sums, fails = dev.outputs(p)
+    for _ in range(2):
+        dev.eval_sums(p, sh, lam, sums, fails)
+    torch.cuda.synchronize()
+    print("profile pass ok", int(fails.sum().item()))
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.profile_pass:
+        profile_pass()
+    elif a.impl == "reference":
         main_reference(a)
     else:
         main_ours(a)
