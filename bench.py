@@ -43,6 +43,8 @@ LAMBDA = 0.5
 METRIC = "integrand evals/s"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock per SM (4 flop) x 2070 MHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # DRAM bytes per launch of the evaluation kernel from ncu (profiles/qmc_eval_kernel_massive_box.md), valid
 # while the device code hashes to KERNEL_HASH; null otherwise
 TRAFFIC_BYTES = None
@@ -273,6 +275,52 @@ def main_ours(args):
     kh = kernel_hash()
     traffic = TRAFFIC_BYTES if (TRAFFIC_BYTES is not None and kh == KERNEL_HASH) else None
 
+    # the same pass in mixed precision (FP32 evaluation, FP64 lattice arithmetic and accumulation)
+    pm = api.make_pass(n, z, N_SHIFTS, 3, precision=N.QMC_PREC_MIXED)
+    scr_m, scr_m_bytes = di.scratch(pm)
+    sums_m, fails_m = di.outputs(pm)
+
+    def step_mixed(evs_m):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), pm, sh.data_ptr(), lam.data_ptr(), scr_m,
+                                        scr_m_bytes, stream.cuda_stream), "qmc_eval_partials")
+            e1.record(stream)
+            N.check(L.qmc_reduce_partials(prep.packed, di.dpacked.data_ptr(), pm, scr_m, scr_m_bytes,
+                                          sums_m.data_ptr(), fails_m.data_ptr(), stream.cuda_stream),
+                    "qmc_reduce_partials")
+            e2.record(stream)
+            evs_m.append((e0, e1, e2))
+
+    for _ in range(args.warmup):
+        step_mixed([])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    evs_m = []
+    tm0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_mixed(evs_m)
+    torch.cuda.synchronize()
+    tmix = time.perf_counter() - tm0
+    if dist:
+        t = torch.tensor([tmix], dtype=torch.float64, device=dev_name)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmix = float(t.item())
+    mix_eval_ms = statistics.mean(a.elapsed_time(b) for a, b, c in evs_m)
+    s64 = sums.cpu().numpy()
+    s32 = sums_m.cpu().numpy()
+    mixed_dev = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
+    mixed = {"value": world * evals_per_step * args.steps / tmix, "unit": "evals/s", "dtype": "f32+f64",
+             "ms_per_step": 1e3 * tmix / args.steps, "eval_kernel_ms": mix_eval_ms,
+             "roofline": {"bound": "alu", "achieved": flops_launch / (mix_eval_ms * 1e-3) / 1e12,
+                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": flops_launch / (mix_eval_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                          "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},
+             "max_rel_dev_from_fp64_sums": mixed_dev, "sign_failures": int(fails_m.sum().item())}
+
     # e2e: the same pass through the host-buffer entry point, copies inside the timed region
     ctx = api.Context(local, 1 << 30, stream)
     import ctypes
@@ -303,9 +351,10 @@ def main_ours(args):
     d2h = sums_h.numel() * 8 + fails_h.numel() * 8
     ctx.close()
 
-    extras = {}
+    extras = {"mixed": mixed}
     if not args.no_extras and rank == 0:
         extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream)
+        extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, precision=N.QMC_PREC_MIXED)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -314,7 +363,7 @@ def main_ours(args):
             "config": workload_config(n),
             "e2e": {"value": world * evals_per_step * args.steps / te, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 2 * args.steps,  # per step: qmc_eval_kernel + qmc_finalize_kernel
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                          "kernel": "qmc_eval_kernel<3,deform,0>", "flops_per_eval": prep.info.flops_per_eval,
@@ -331,23 +380,24 @@ def main_ours(args):
         dist.destroy_process_group()
 
 
-def time_to_accuracy(api, blob, cfg, device, stream, seeds=32):
+def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0):
     """qmc_integrate of the massive box to 1e-3 relative error (lattice ladder from 2^10), over 32 seeds."""
     ctx = api.Context(device, 1 << 30, stream)
     iid = ctx.load_sectors(blob)
     ctx.set_kinematics(iid, cfg.kin, 0, 0)
-    ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=999, lam=LAMBDA)  # warm-up
+    ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=999, lam=LAMBDA, precision=precision)  # warm-up
     ts, ns, ok = [], [], 0
     for s in range(seeds):
         t0 = time.perf_counter()
-        r = ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=1000 + s, lam=LAMBDA)
+        r = ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=1000 + s, lam=LAMBDA, precision=precision)
         ts.append(1e3 * (time.perf_counter() - t0))
         ns.append(r.n_final)
         ok += r.status == 0
     ctx.close()
     ts.sort()
     return {"p50_ms": statistics.median(ts), "p99_ms": ts[min(len(ts) - 1, int(math.ceil(0.99 * len(ts))) - 1)],
-            "seeds": seeds, "converged": ok, "median_final_n": int(statistics.median(ns)), "precision": "f64"}
+            "seeds": seeds, "converged": ok, "median_final_n": int(statistics.median(ns)),
+            "precision": "f64" if precision == 0 else "f32+f64"}
 
 
 def profile_pass():

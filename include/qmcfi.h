@@ -90,6 +90,8 @@ typedef struct {
     int32_t block;             /* threads per block: 0 = default, else 64..512 and a multiple of 32 */
     int32_t points_per_thread; /* 0 = default, else 1..64 */
     int32_t grid;              /* blocks of the persistent kernel: 0 = one wave on the device */
+    const int32_t *sector_precision; /* QMC_PREC_MIXED only: device array, one entry per sector (table order),
+                                        1 = evaluate in FP32, anything else = FP64; NULL = every sector FP32 */
 } qmc_pass;
 
 /* Text for a status code (static storage). */
@@ -144,6 +146,17 @@ int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc
                       const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, void *stream);
 int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const void *scratch_dev,
                         size_t scratch_bytes, double *sums_dev, int64_t *fails_dev, void *stream);
+
+/*
+ * qmc_probe_precision -- FP32-versus-FP64 discrepancy per sector (the mixed-precision budget check),
+ * asynchronous on `stream`.  For each sector s, a strided sample of n_sample lattice points i = k * (n / n_sample)
+ * of the shift shift_dev[0..5] is evaluated by both the FP32 and the FP64 device code; per slot it writes
+ *   out[(s * n_slots + slot) * 4 + {0,1,2,3}] = sum |v64|, sum |v32 - v64|, sum (v32 - v64) re, im.
+ * The paper evaluates in one precision; the split into an FP32 path with FP64 re-runs of sectors whose FP32
+ * error exceeds a budget is this library's (Sec. II, after Eq. 12, motivates FP64 where cancellation is large).
+ */
+int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
+                        const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream);
 
 /*
  * qmc_eval_sums_noalloc -- qmc_eval_sums without a caller-provided scratch buffer, for callers that cannot
@@ -201,6 +214,9 @@ typedef struct {
     int64_t max_n;           /* stop the ladder above this lattice size (0 = no limit) */
     double max_seconds;      /* 0 = no limit */
     int32_t block, points_per_thread; /* launch shape (0 = default) */
+    int64_t probe_samples;   /* QMC_PREC_MIXED: points per sector of the FP32/FP64 probe (0 = 4096) */
+    double fp32_budget;      /* QMC_PREC_MIXED: a sector runs in FP64 when its probe's sum|v32-v64| exceeds
+                                fp32_budget * rel_tol * sum|v64| in any order (0 = 0.1) */
 } qmc_options;
 
 typedef struct {

@@ -52,7 +52,8 @@ class qmc_sector_desc(ctypes.Structure):
 
 class qmc_pass(ctypes.Structure):
     _fields_ = [("lattice", qmc_lattice), ("n_shifts", c_int32), ("transform_r", c_int32), ("precision", c_int32),
-                ("block", c_int32), ("points_per_thread", c_int32), ("grid", c_int32)]
+                ("block", c_int32), ("points_per_thread", c_int32), ("grid", c_int32),
+                ("sector_precision", c_void_p)]
 
 
 class qmc_options(ctypes.Structure):
@@ -60,7 +61,7 @@ class qmc_options(ctypes.Structure):
                 ("seed", c_uint64), ("lambda_", c_double), ("max_halvings", c_int32), ("transform_r", c_int32),
                 ("ladder_start", c_int32), ("n_lattices", c_int32), ("lattices", POINTER(qmc_lattice)),
                 ("shifts", POINTER(c_double)), ("max_n", c_int64), ("max_seconds", c_double), ("block", c_int32),
-                ("points_per_thread", c_int32)]
+                ("points_per_thread", c_int32), ("probe_samples", c_int64), ("fp32_budget", c_double)]
 
 
 class qmc_result(ctypes.Structure):
@@ -84,6 +85,8 @@ PROTOTYPES = {
     "qmc_eval_partials": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_size_t,
                                   c_void_p]),
     "qmc_reduce_partials": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_size_t, c_void_p, c_void_p,
+                                    c_void_p]),
+    "qmc_probe_precision": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_int64, c_void_p,
                                     c_void_p]),
     "qmc_eval_sums_noalloc": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),

@@ -240,78 +240,88 @@ int deg_of(const PTerm &t, int d) {
 }
 
 double transform_flops(int r) {
-    /* per dimension: lattice point (2), t and 1-t by Horner, weight, weight product */
+    /* per dimension: lattice point (fma + wrap: 3), the transform polynomial on one side by Horner, 1 - p,
+       1 - x, the weight c_r (x(1-x))^r and its product into w */
     switch (r) {
-        case 0: return 2.0 + 0.0 + 1.0;
-        case 1: return 2.0 + 2 * 4.0 + 3.0 + 1.0;
-        case 2: return 2.0 + 2 * 7.0 + 4.0 + 1.0;
-        default: return 2.0 + 2 * 9.0 + 4.0 + 1.0;
+        case 0: return 3.0 + 0.0 + 1.0 + 1.0 + 0.0 + 1.0;
+        case 1: return 3.0 + 4.0 + 1.0 + 1.0 + 2.0 + 1.0;
+        case 2: return 3.0 + 7.0 + 1.0 + 1.0 + 3.0 + 1.0;
+        default: return 3.0 + 9.0 + 1.0 + 1.0 + 4.0 + 1.0;
     }
 }
 
-/* Algorithmic FP work of one evaluation of a sector (FMA = 2, complex multiply = 6, complex add = 2):
-   transform, per zeroed subset the polynomial evaluations (real: deg+1 per term; complex: 6 per
-   multiplication + 2 per add), the deformation matrix and det(I - i lam A), powers, the V-series and
-   G-series products, the weight and Kahan accumulation.  Logarithms and atan2 are counted separately. */
+/* Algorithmic FP work of one evaluation of a sector: every add or multiply is 1 flop, an FMA 2, a complex
+   multiply 6, a real-times-complex product 2.  Counted from the sector's tables: transform, and per zeroed
+   subset (2^sigma of them) the polynomial terms (real term of degree d >= 1: d+1; complex: 6(d-1)+4;
+   constants: 1), for deformed sectors the matrix A, det(I - i lam A), z and q, integer powers and monomials,
+   the eps-series products; finally weight and accumulation.  Reciprocals count 1; logarithms and atan2 are
+   transcendentals, counted separately. */
 void sector_work(const PackedSector &s, const PTerm *T, int d, int r, int eU0, int eF0, double &flops,
                  double &transc) {
     const int M = s.M;
     double per_subset = 0.0, trans_subset = 0.0;
     auto real_poly = [&](int off, int n) {
         double f = 0.0;
-        for (int a = 0; a < n; ++a) f += deg_of(T[off + a], d) + 1.0;
+        for (int a = 0; a < n; ++a) {
+            const int g = deg_of(T[off + a], d);
+            f += g == 0 ? 1.0 : g + 1.0;
+        }
         return f;
     };
     auto cplx_poly = [&](int off, int n) {
         double f = 0.0;
-        for (int a = 0; a < n; ++a) f += 6.0 * deg_of(T[off + a], d) + 2.0;
+        for (int a = 0; a < n; ++a) {
+            const int g = deg_of(T[off + a], d);
+            f += g == 0 ? 1.0 : 6.0 * (g - 1) + 4.0;
+        }
         return f;
     };
-    int mono = 0;
-    for (int j = 0; j < d; ++j) mono += std::max(0, s.A[j]);
+    int mono = 0, nb = 0, nq = 0, nneg = 0;
+    for (int j = 0; j < d; ++j) {
+        mono += std::max(0, s.A[j]);
+        nb += (s.A[j] != -1 && s.B[j] != 0);
+        nq += std::abs(s.A[j]);
+        nneg += s.A[j] < 0;
+    }
     if (s.kind != 2) {
         per_subset += real_poly(0, s.nU) + real_poly(s.nU, s.nF);
-        per_subset += std::abs(eU0) + std::abs(eF0) + 1 + mono;
+        per_subset += std::abs(eU0) + std::abs(eF0) + 1.0 + mono; /* powers (one reciprocal), D, monomial */
         if (M > 0) {
-            int nb = 0;
-            for (int j = 0; j < d; ++j) nb += (s.A[j] != -1 && s.B[j] != 0);
-            per_subset += 3 + 2 * nb;
-            trans_subset += 2;
+            per_subset += 3.0 + 2.0 * nb; /* U^eU1 F^-eF1, log argument, B_j log t_j */
+            trans_subset += 1;
         }
     } else {
         per_subset += real_poly(s.nU + s.nF, s.nG) + real_poly(s.nU + s.nF + s.nG, s.nH);
-        per_subset += d * (d + 1) / 2 * 2.0 + 2.0 * d;  /* A matrix */
-        if (d == 1) per_subset += 2;
-        else if (d == 2) per_subset += 8;
-        else if (d == 3) per_subset += 30;
+        per_subset += 2.0 * d * d + 3.0 * d; /* A = diag((1-2t) g) + diag(t(1-t)) H */
+        if (d == 1) per_subset += 1;
+        else if (d == 2) per_subset += 7;
+        else if (d == 3) per_subset += 32;
         else {
             double lu = 0.0;
             for (int c = 0; c < d; ++c) {
                 const int rest = d - c - 1;
-                lu += 6 + 10 + rest * (6 + rest * 8.0);
+                lu += 12.0 + rest * (6.0 + 8.0 * rest);
             }
             per_subset += lu;
         }
-        per_subset += 4.0 * d;  /* z and q */
-        per_subset += cplx_poly(0, s.nU) + cplx_poly(s.nU, s.nF);
-        per_subset += 6.0 * (std::abs(eU0) + std::abs(eF0)) + 10 + 2 + mono + 2;
-        int nq = 0, nb = 0;
-        for (int j = 0; j < d; ++j) {
-            nq += std::abs(s.A[j]);
-            nb += (s.B[j] != 0);
-        }
-        per_subset += 6.0 * nq + 10.0 * (nq > 0);
+        per_subset += 3.0 * d; /* z_j and q_j */
+        const bool needU = eU0 != 0 || M > 0;
+        if (needU) per_subset += cplx_poly(0, s.nU);
+        per_subset += cplx_poly(s.nU, s.nF);
+        per_subset += 6.0 * (std::abs(eU0) + std::abs(eF0)) + 6.0 + 2.0 + (mono ? 2.0 + mono : 0.0);
+        per_subset += 6.0 * nq + 6.0 * nneg;
         if (M > 0) {
-            per_subset += 8 + 4.0 * nb;
-            trans_subset += 4 + 2.0 * nb;
+            int nlq = 0;
+            for (int j = 0; j < d; ++j) nlq += s.B[j] != 0;
+            per_subset += 4.0 + 2.0 * nb + 4.0 * nlq;
+            trans_subset += 2 + nlq; /* complex logs of U, F and of the q_j */
         }
     }
     const int nsub = 1 << s.sigma;
-    /* V series: sigma factors times (M+1)(M+2)/2 FMAs; G series and accumulation */
-    double series = s.sigma * ((M + 1) * (M + 2) / 2) * 2.0 + 2.0 * M * s.sigma;
+    double series = s.sigma * ((M + 1) * (M + 2) / 2 * 2.0 + 2.0 * M);
     series += (M + 1) * (M + 2) / 2 * 4.0 + M * 8.0;
-    flops = d * transform_flops(r) + nsub * (per_subset + series) + 2.0 * (M + 1) + 8.0 * (M + 1);
-    transc = nsub * trans_subset + (M > 0 ? (double)(s.sigma) : 0.0);
+    flops = d * transform_flops(r) + nsub * (per_subset + series) + 4.0 * (M + 1);
+    transc = nsub * trans_subset + (M > 0 ? (double)s.sigma : 0.0);
 }
 
 struct Packed {
@@ -498,7 +508,8 @@ int pack_table(const Table &t, const double *inv, int n_inv, int order_min, int 
     h.n_terms_total = (int32_t)n_terms_total;
     h.sectors_off = sizeof(PackedHeader);
     h.terms_off = h.sectors_off + (int64_t)sizeof(PackedSector) * t.n_sectors;
-    h.total_bytes = h.terms_off + (int64_t)sizeof(PackedTerm) * n_terms_total;
+    h.termsf_off = h.terms_off + (int64_t)sizeof(PackedTerm) * n_terms_total;
+    h.total_bytes = h.termsf_off + (int64_t)sizeof(PackedTermF) * n_terms_total;
     h.flops_per_eval = fsum / t.n_sectors;
     h.transc_per_eval = tsum / t.n_sectors;
     h.n_deformed = n_def;
@@ -514,6 +525,11 @@ int pack_table(const Table &t, const double *inv, int n_inv, int order_min, int 
             pt.c = w.terms[k].c;
             std::memcpy(pt.e, w.terms[k].e, 8);
             std::memcpy(out.data() + h.terms_off + (int64_t)sizeof(PackedTerm) * (w.ps.term0 + k), &pt, sizeof(pt));
+            PackedTermF pf;
+            pf.hi = (float)w.terms[k].c;
+            pf.lo = (float)(w.terms[k].c - (double)pf.hi);
+            std::memcpy(pf.e, w.terms[k].e, 8);
+            std::memcpy(out.data() + h.termsf_off + (int64_t)sizeof(PackedTermF) * (w.ps.term0 + k), &pf, sizeof(pf));
         }
     }
     if (info) {
@@ -569,7 +585,7 @@ int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
     if (p->precision != QMC_PREC_FP64 && p->precision != QMC_PREC_MIXED) return QMC_ERR_ARG;
     pl.block = p->block ? p->block : 128;
     if (pl.block < 32 || pl.block > 256 || pl.block % 32) return QMC_ERR_ARG;
-    pl.P = p->points_per_thread ? p->points_per_thread : 8;
+    pl.P = p->points_per_thread ? p->points_per_thread : (p->precision == QMC_PREC_MIXED ? 16 : 8);
     if (pl.P < 1 || pl.P > 64) return QMC_ERR_ARG;
     for (int j = 0; j < h->dim; ++j)
         if (p->lattice.z[j] == 0 || (int64_t)p->lattice.z[j] >= p->lattice.n) return QMC_ERR_ARG;
@@ -586,7 +602,7 @@ int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     pl.partial_bytes = up((size_t)pl.total_items * h->n_slots * 2 * sizeof(double));
     pl.fail_bytes = up((size_t)pl.total_items * sizeof(uint32_t));
-    pl.counter_bytes = up(QMC_N_CLASSES * sizeof(unsigned long long));
+    pl.counter_bytes = up(2 * QMC_N_CLASSES * sizeof(unsigned long long)); /* per class and precision */
     pl.total_bytes = pl.partial_bytes + pl.fail_bytes + pl.counter_bytes;
     return QMC_OK;
 }
@@ -695,7 +711,6 @@ int check_pass(const PackedHeader *h, const void *packed_dev, const qmc_pass *pa
     int rc = make_plan(h, pass, pl);
     if (rc) return rc;
     if (scratch_bytes < pl.total_bytes) return QMC_ERR_MEMORY;
-    if (pass->precision != QMC_PREC_FP64) return QMC_ERR_UNSUPPORTED;
     unsigned char *scr = static_cast<unsigned char *>(scratch_dev);
     sc.partials = reinterpret_cast<double *>(scr);
     sc.pfails = reinterpret_cast<uint32_t *>(scr + pl.partial_bytes);
@@ -719,51 +734,100 @@ int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc
     int rc = check_pass(h, packed_dev, pass, scratch_dev, scratch_bytes, pl, sc);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = cuda_status(cudaMemsetAsync(sc.counters, 0, QMC_N_CLASSES * sizeof(unsigned long long), st));
+    rc = cuda_status(cudaMemsetAsync(sc.counters, 0, 2 * QMC_N_CLASSES * sizeof(unsigned long long), st));
     if (rc) return rc;
     int sms = 0;
     rc = qmc_device_sm_count(&sms);
     if (rc) return rc;
     const size_t smem = sizeof(PackedSector) + (size_t)h->max_terms * sizeof(PackedTerm);
+    /* FP64 pass: one kernel per class.  Mixed pass: the FP32 kernel takes the sectors marked 1 in
+       pass->sector_precision (all when it is null), the FP64 kernel the others; both share the item space. */
+    const bool mixed = pass->precision == QMC_PREC_MIXED;
     for (int c = 0; c < QMC_N_CLASSES; ++c) {
         if (pl.items[c] == 0) continue;
         const int maxm = class_maxm(h, c);
-        EvalArgs a;
+        for (int prec = 0; prec < 2; ++prec) {
+            const int kprec = prec == 0 ? QMC_PREC_FP64 : QMC_PREC_MIXED;
+            if (!mixed && prec == 1) continue;
+            if (mixed && prec == 0 && !pass->sector_precision) continue;
+            EvalArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.packed = static_cast<const unsigned char *>(packed_dev);
+            a.sectors_off = h->sectors_off;
+            a.terms_off = h->terms_off;
+            a.termsf_off = h->termsf_off;
+            a.sector_begin = h->class_begin[c];
+            a.n_sect = h->class_end[c] - h->class_begin[c];
+            a.m = pass->n_shifts;
+            a.r = pass->transform_r;
+            a.P = pl.P;
+            a.n_slots = h->n_slots;
+            a.n = (uint32_t)pass->lattice.n;
+            for (int j = 0; j < QMC_MAX_DIM; ++j) {
+                a.z[j] = j < h->dim ? pass->lattice.z[j] : 0;
+                a.zstep[j] = (uint32_t)(((uint64_t)pl.block * a.z[j]) % (uint64_t)pass->lattice.n);
+            }
+            a.invn = 1.0 / (double)pass->lattice.n;
+            a.chunks = pl.chunks;
+            a.total_items = pl.items[c];
+            a.shifts = shifts_dev;
+            a.lambda = lambda_dev;
+            a.partials = sc.partials + pl.item_off[c] * h->n_slots * 2;
+            a.part_fails = sc.pfails + pl.item_off[c];
+            a.counter = sc.counters + 2 * c + prec;
+            a.eU0 = h->eU0;
+            a.eU1 = h->eU1;
+            a.eF0 = h->eF0;
+            a.eF1 = h->eF1;
+            a.smem_bytes = (int)smem;
+            a.sector_prec = mixed ? pass->sector_precision : nullptr;
+            a.want_prec = prec;
+            int per_sm = 0;
+            rc = qmc_eval_blocks_per_sm(h->dim, c == 1, maxm, kprec, pl.block, (int)smem, &per_sm);
+            if (rc) return rc;
+            if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
+            int64_t grid = pass->grid > 0 ? pass->grid : (int64_t)sms * per_sm;
+            if (grid > pl.items[c]) grid = pl.items[c];
+            rc = qmc_launch_eval(h->dim, c == 1, maxm, kprec, a, (int)grid, pl.block, stream);
+            if (rc) return rc;
+        }
+    }
+    return QMC_OK;
+}
+
+int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
+                        const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream) {
+    const PackedHeader *h = header_of(packed_host);
+    if (!h || !packed_dev || !pass || !shift_dev || !lambda_dev || !out_dev || n_sample < 1) return QMC_ERR_ARG;
+    Plan pl;
+    int rc = make_plan(h, pass, pl);
+    if (rc) return rc;
+    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+        const int ns = h->class_end[c] - h->class_begin[c];
+        if (ns <= 0) continue;
+        ProbeArgs a;
         std::memset(&a, 0, sizeof(a));
         a.packed = static_cast<const unsigned char *>(packed_dev);
         a.sectors_off = h->sectors_off;
         a.terms_off = h->terms_off;
+        a.termsf_off = h->termsf_off;
         a.sector_begin = h->class_begin[c];
-        a.n_sect = h->class_end[c] - h->class_begin[c];
-        a.m = pass->n_shifts;
+        a.n_sect = ns;
         a.r = pass->transform_r;
-        a.P = pl.P;
         a.n_slots = h->n_slots;
         a.n = (uint32_t)pass->lattice.n;
-        for (int j = 0; j < QMC_MAX_DIM; ++j) {
-            a.z[j] = j < h->dim ? pass->lattice.z[j] : 0;
-            a.zstep[j] = (uint32_t)(((uint64_t)pl.block * a.z[j]) % (uint64_t)pass->lattice.n);
-        }
+        for (int j = 0; j < QMC_MAX_DIM; ++j) a.z[j] = j < h->dim ? pass->lattice.z[j] : 0;
         a.invn = 1.0 / (double)pass->lattice.n;
-        a.chunks = pl.chunks;
-        a.total_items = pl.items[c];
-        a.shifts = shifts_dev;
+        a.shift = shift_dev;
         a.lambda = lambda_dev;
-        a.partials = sc.partials + pl.item_off[c] * h->n_slots * 2;
-        a.part_fails = sc.pfails + pl.item_off[c];
-        a.counter = sc.counters + c;
+        a.n_sample = n_sample;
+        a.out = out_dev;
         a.eU0 = h->eU0;
         a.eU1 = h->eU1;
         a.eF0 = h->eF0;
         a.eF1 = h->eF1;
-        a.smem_bytes = (int)smem;
-        int per_sm = 0;
-        rc = qmc_eval_blocks_per_sm(h->dim, c == 1, maxm, pass->precision, pl.block, (int)smem, &per_sm);
-        if (rc) return rc;
-        if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
-        int64_t grid = pass->grid > 0 ? pass->grid : (int64_t)sms * per_sm;
-        if (grid > pl.items[c]) grid = pl.items[c];
-        rc = qmc_launch_eval(h->dim, c == 1, maxm, pass->precision, a, (int)grid, pl.block, stream);
+        a.smem_bytes = (int)(sizeof(PackedSector) + 2 * (size_t)h->max_terms * sizeof(PackedTerm));
+        rc = qmc_launch_probe(h->dim, c == 1, class_maxm(h, c), a, stream);
         if (rc) return rc;
     }
     return QMC_OK;
@@ -958,7 +1022,7 @@ struct qmc_ctx {
     cudaStream_t stream = nullptr;
     std::map<int32_t, Integral> integrals;
     int32_t next_id = 1;
-    DevBuf scratch, sums, fails, shifts, lambda, hpacked;
+    DevBuf scratch, sums, fails, shifts, lambda, hpacked, prec, probe;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::mutex mu;
 };
@@ -1025,6 +1089,8 @@ int qmc_destroy(qmc_ctx *c) {
     dev_release(c, c->shifts);
     dev_release(c, c->lambda);
     dev_release(c, c->hpacked);
+    dev_release(c, c->prec);
+    dev_release(c, c->probe);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
     delete c;
@@ -1119,6 +1185,14 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
     if (rc) return res->status = rc;
     std::vector<double> sums((size_t)ns * m * h->n_slots * 2), Q((size_t)m * nord * 2), mean(nord * 2), err(nord * 2);
     std::vector<int64_t> fails((size_t)ns * m);
+    const bool mixed = opt->precision == QMC_PREC_MIXED;
+    std::vector<int32_t> prec(ns, 1);
+    bool probe_due = mixed;
+    if (mixed) {
+        rc = dev_reserve(c, c->prec, ns * sizeof(int32_t));
+        if (!rc) rc = dev_reserve(c, c->probe, (size_t)ns * h->n_slots * 4 * sizeof(double));
+        if (rc) return res->status = rc;
+    }
     int status = QMC_ERR_NOT_CONVERGED;
     float kernel_ms_total = 0.f;
     for (const qmc_lattice &L : ladder) {
@@ -1131,6 +1205,7 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
         pass.precision = opt->precision;
         pass.block = opt->block;
         pass.points_per_thread = opt->points_per_thread;
+        pass.sector_precision = mixed ? (const int32_t *)c->prec.p : nullptr;
         const size_t need = qmc_scratch_bytes(I.packed.data(), &pass);
         if (!need) return res->status = QMC_ERR_ARG;
         rc = dev_reserve(c, c->scratch, need);
@@ -1138,6 +1213,33 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
         for (;;) {
             rc = cuda_status(cudaMemcpyAsync(c->lambda.p, lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
                                              c->stream));
+            if (!rc && probe_due) {
+                /* FP32 budget: sectors whose FP32 values on the probe sample deviate from FP64 by more than
+                   fp32_budget * rel_tol (L1, any order) are evaluated in FP64 */
+                const int64_t nsamp = opt->probe_samples > 0 ? opt->probe_samples : 4096;
+                const double budget = (opt->fp32_budget > 0 ? opt->fp32_budget : 0.1) * opt->rel_tol;
+                std::vector<double> pr((size_t)ns * h->n_slots * 4);
+                rc = qmc_probe_precision(I.packed.data(), I.dpacked.p, &pass, (const double *)c->shifts.p,
+                                         (const double *)c->lambda.p, nsamp, (double *)c->probe.p, c->stream);
+                if (!rc)
+                    rc = cuda_status(cudaMemcpyAsync(pr.data(), c->probe.p, pr.size() * sizeof(double),
+                                                     cudaMemcpyDeviceToHost, c->stream));
+                if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+                if (rc) return res->status = rc;
+                res->fp64_reruns = 0;
+                for (int s2 = 0; s2 < ns; ++s2) {
+                    bool bad = false;
+                    for (int o = 0; o < h->n_slots; ++o) {
+                        const double *v = &pr[((size_t)s2 * h->n_slots + o) * 4];
+                        if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
+                    }
+                    prec[s2] = bad ? 0 : 1;
+                    res->fp64_reruns += bad;
+                }
+                rc = cuda_status(cudaMemcpyAsync(c->prec.p, prec.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                                 c->stream));
+                probe_due = false;
+            }
             if (!rc) rc = cuda_status(cudaEventRecord(c->ev0, c->stream));
             if (!rc)
                 rc = qmc_eval_sums(I.packed.data(), I.dpacked.p, &pass, (const double *)c->shifts.p,
@@ -1175,6 +1277,7 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
                 }
             }
             if (!again) break;
+            probe_due = mixed;
         }
         qmc_combine(I.packed.data(), &pass, sums.data(), Q.data(), mean.data(), err.data());
         res->n_final = L.n;

@@ -7,6 +7,9 @@
  *   PackedTerm[n_terms_total]         per sector: Ut terms, Ft terms, dFt/dt_j terms (j = 0..dim-1),
  *                                     d2Ft/dt_j dt_k terms (j <= k, row-major upper triangle)
  *
+ *   PackedTermF[n_terms_total]        the same terms for the FP32 path: the coefficient as a float pair
+ *                                     hi + lo (hi = fl32(c), lo = fl32(c - hi)) and the same exponents
+ *
  * A term is one monomial c * prod_j t_j^{e_j}: 8 bytes of coefficient (already evaluated at the kinematic
  * point) and 8 exponent bytes, 16 bytes in all, so that a block stages a sector into shared memory with
  * 16-byte vector copies and every thread of a warp reads the same term (a shared-memory broadcast).
@@ -34,7 +37,7 @@ struct PackedHeader {
     int64_t sectors_off, terms_off, total_bytes;
     double flops_per_eval, transc_per_eval;
     int32_t n_deformed, n_negative, max_sigma, reserved;
-    int32_t pad[2];
+    int64_t termsf_off;
 };
 
 struct PackedSector {
@@ -60,7 +63,13 @@ struct PackedTerm {
     uint8_t e[8];
 };
 
+struct PackedTermF {
+    float hi, lo;
+    uint8_t e[8];
+};
+
 static_assert(sizeof(PackedTerm) == 16, "term must be 16 bytes");
+static_assert(sizeof(PackedTermF) == 16, "FP32 term must be 16 bytes");
 static_assert(sizeof(PackedSector) % 16 == 0, "sector record must be 16-byte aligned");
 static_assert(sizeof(PackedHeader) % 16 == 0, "header must be 16-byte aligned");
 
@@ -85,6 +94,26 @@ struct EvalArgs {
     double *partials;             /* total_items x n_slots x 2 */
     uint32_t *part_fails;         /* total_items */
     unsigned long long *counter;  /* work counter (zeroed before launch) */
+    int32_t eU0, eU1, eF0, eF1;
+    int32_t smem_bytes;
+    int64_t termsf_off;
+    const int32_t *sector_prec;   /* per sector (table order): 0 FP64, 1 FP32; null = all of want_prec */
+    int32_t want_prec;            /* items of sectors with another precision are skipped */
+};
+
+/* Precision probe: a strided sample of each sector's lattice points for one shift, in FP32 and FP64. */
+struct ProbeArgs {
+    const unsigned char *packed;
+    int64_t sectors_off, terms_off, termsf_off;
+    int32_t sector_begin, n_sect;
+    int32_t r, n_slots;
+    uint32_t n;
+    uint32_t z[QMC_MAX_DIM];
+    double invn;
+    const double *shift;          /* 6 doubles */
+    const double *lambda;         /* per sector, table order */
+    int64_t n_sample;             /* sample points per sector */
+    double *out;                  /* n_sectors(table order) x n_slots x 4: sum|v64|, sum|v32-v64|, sum(v32-v64) re, im */
     int32_t eU0, eU1, eF0, eF1;
     int32_t smem_bytes;
 };
@@ -125,3 +154,4 @@ int qmc_launch_finalize(const FinalizeArgs &a, void *stream);
 int qmc_launch_points(int dim, int deform, int maxm, int precision, const PointArgs &a, void *stream);
 int qmc_device_sm_count(int *sms);
 int qmc_eval_blocks_per_sm(int dim, int deform, int maxm, int precision, int block, int smem_bytes, int *out);
+int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *stream);

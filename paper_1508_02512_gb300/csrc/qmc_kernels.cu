@@ -4,23 +4,29 @@
  */
 #include "qmc_device.cuh"
 
-int qmc_launch_eval_d1(int deform, int maxm, const EvalArgs &a, int grid, int block, cudaStream_t st);
-int qmc_occupancy_d1(int deform, int maxm, int block, int smem, int *out);
+int qmc_launch_eval_d1(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st);
+int qmc_occupancy_d1(int deform, int maxm, int precision, int block, int smem, int *out);
+int qmc_launch_probe_d1(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d1(int deform, int maxm, const PointArgs &a, cudaStream_t st);
-int qmc_launch_eval_d2(int deform, int maxm, const EvalArgs &a, int grid, int block, cudaStream_t st);
-int qmc_occupancy_d2(int deform, int maxm, int block, int smem, int *out);
+int qmc_launch_eval_d2(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st);
+int qmc_occupancy_d2(int deform, int maxm, int precision, int block, int smem, int *out);
+int qmc_launch_probe_d2(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d2(int deform, int maxm, const PointArgs &a, cudaStream_t st);
-int qmc_launch_eval_d3(int deform, int maxm, const EvalArgs &a, int grid, int block, cudaStream_t st);
-int qmc_occupancy_d3(int deform, int maxm, int block, int smem, int *out);
+int qmc_launch_eval_d3(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st);
+int qmc_occupancy_d3(int deform, int maxm, int precision, int block, int smem, int *out);
+int qmc_launch_probe_d3(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d3(int deform, int maxm, const PointArgs &a, cudaStream_t st);
-int qmc_launch_eval_d4(int deform, int maxm, const EvalArgs &a, int grid, int block, cudaStream_t st);
-int qmc_occupancy_d4(int deform, int maxm, int block, int smem, int *out);
+int qmc_launch_eval_d4(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st);
+int qmc_occupancy_d4(int deform, int maxm, int precision, int block, int smem, int *out);
+int qmc_launch_probe_d4(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d4(int deform, int maxm, const PointArgs &a, cudaStream_t st);
-int qmc_launch_eval_d5(int deform, int maxm, const EvalArgs &a, int grid, int block, cudaStream_t st);
-int qmc_occupancy_d5(int deform, int maxm, int block, int smem, int *out);
+int qmc_launch_eval_d5(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st);
+int qmc_occupancy_d5(int deform, int maxm, int precision, int block, int smem, int *out);
+int qmc_launch_probe_d5(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d5(int deform, int maxm, const PointArgs &a, cudaStream_t st);
-int qmc_launch_eval_d6(int deform, int maxm, const EvalArgs &a, int grid, int block, cudaStream_t st);
-int qmc_occupancy_d6(int deform, int maxm, int block, int smem, int *out);
+int qmc_launch_eval_d6(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st);
+int qmc_occupancy_d6(int deform, int maxm, int precision, int block, int smem, int *out);
+int qmc_launch_probe_d6(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d6(int deform, int maxm, const PointArgs &a, cudaStream_t st);
 
 /* ------------------------------------------------------------------ K4: deterministic per-(sector, shift) sums */
@@ -58,28 +64,41 @@ __global__ void __launch_bounds__(128) qmc_finalize_kernel(FinalizeArgs a) {
 
 int qmc_launch_eval(int dim, int deform, int maxm, int precision, const EvalArgs &a, int grid, int block,
                     void *stream) {
-    if (precision != QMC_PREC_FP64) return QMC_ERR_UNSUPPORTED;
+    if (precision != QMC_PREC_FP64 && precision != QMC_PREC_MIXED) return QMC_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     switch (dim) {
-        case 1: return qmc_launch_eval_d1(deform, maxm, a, grid, block, st);
-        case 2: return qmc_launch_eval_d2(deform, maxm, a, grid, block, st);
-        case 3: return qmc_launch_eval_d3(deform, maxm, a, grid, block, st);
-        case 4: return qmc_launch_eval_d4(deform, maxm, a, grid, block, st);
-        case 5: return qmc_launch_eval_d5(deform, maxm, a, grid, block, st);
-        case 6: return qmc_launch_eval_d6(deform, maxm, a, grid, block, st);
+        case 1: return qmc_launch_eval_d1(deform, maxm, precision, a, grid, block, st);
+        case 2: return qmc_launch_eval_d2(deform, maxm, precision, a, grid, block, st);
+        case 3: return qmc_launch_eval_d3(deform, maxm, precision, a, grid, block, st);
+        case 4: return qmc_launch_eval_d4(deform, maxm, precision, a, grid, block, st);
+        case 5: return qmc_launch_eval_d5(deform, maxm, precision, a, grid, block, st);
+        case 6: return qmc_launch_eval_d6(deform, maxm, precision, a, grid, block, st);
         default: return QMC_ERR_UNSUPPORTED;
     }
 }
 
 int qmc_eval_blocks_per_sm(int dim, int deform, int maxm, int precision, int block, int smem_bytes, int *out) {
-    if (precision != QMC_PREC_FP64) return QMC_ERR_UNSUPPORTED;
+    if (precision != QMC_PREC_FP64 && precision != QMC_PREC_MIXED) return QMC_ERR_UNSUPPORTED;
     switch (dim) {
-        case 1: return qmc_occupancy_d1(deform, maxm, block, smem_bytes, out);
-        case 2: return qmc_occupancy_d2(deform, maxm, block, smem_bytes, out);
-        case 3: return qmc_occupancy_d3(deform, maxm, block, smem_bytes, out);
-        case 4: return qmc_occupancy_d4(deform, maxm, block, smem_bytes, out);
-        case 5: return qmc_occupancy_d5(deform, maxm, block, smem_bytes, out);
-        case 6: return qmc_occupancy_d6(deform, maxm, block, smem_bytes, out);
+        case 1: return qmc_occupancy_d1(deform, maxm, precision, block, smem_bytes, out);
+        case 2: return qmc_occupancy_d2(deform, maxm, precision, block, smem_bytes, out);
+        case 3: return qmc_occupancy_d3(deform, maxm, precision, block, smem_bytes, out);
+        case 4: return qmc_occupancy_d4(deform, maxm, precision, block, smem_bytes, out);
+        case 5: return qmc_occupancy_d5(deform, maxm, precision, block, smem_bytes, out);
+        case 6: return qmc_occupancy_d6(deform, maxm, precision, block, smem_bytes, out);
+        default: return QMC_ERR_UNSUPPORTED;
+    }
+}
+
+int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dim) {
+        case 1: return qmc_launch_probe_d1(deform, maxm, a, st);
+        case 2: return qmc_launch_probe_d2(deform, maxm, a, st);
+        case 3: return qmc_launch_probe_d3(deform, maxm, a, st);
+        case 4: return qmc_launch_probe_d4(deform, maxm, a, st);
+        case 5: return qmc_launch_probe_d5(deform, maxm, a, st);
+        case 6: return qmc_launch_probe_d6(deform, maxm, a, st);
         default: return QMC_ERR_UNSUPPORTED;
     }
 }
