@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-accuracy and CPU baseline")
     ap.add_argument("--profile-pass", action="store_true",
                     help="run two passes of the same integral at n = 1048573 and exit (small case for ncu)")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
     return ap.parse_args()
 
 
@@ -400,9 +401,10 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0):
             "precision": "f64" if precision == 0 else "f32+f64"}
 
 
-def profile_pass():
+def profile_pass(precision="fp64"):
     """Two passes of the benchmark integral at n = 1048573 (largest prime below 2^20), 16 shifts."""
     import torch
+    from paper_1508_02512_gb300 import _native as N
     from paper_1508_02512_gb300 import api
     from paper_1508_02512_gb300 import tables as T
     cfg = W.CONFIG1
@@ -410,7 +412,8 @@ def profile_pass():
     prep = api.prepare(blob, cfg.kin, 0, 0)
     dev = api.DeviceIntegral(prep)
     n = 1048573
-    p = api.make_pass(n, dict(api.builtin_lattices())[n], N_SHIFTS, 3)
+    p = api.make_pass(n, dict(api.builtin_lattices())[n], N_SHIFTS, 3,
+                      precision=N.QMC_PREC_MIXED if precision == "mixed" else N.QMC_PREC_FP64)
     sh = torch.tensor(W.shifts(cfg.seed, N_SHIFTS), device="cuda")
     lam = torch.full((prep.info.n_sectors,), LAMBDA, dtype=torch.float64, device="cuda")
     sums, fails = dev.outputs(p)
@@ -423,7 +426,7 @@ def profile_pass():
 if __name__ == "__main__":
     a = parse()
     if a.profile_pass:
-        profile_pass()
+        profile_pass(a.precision)
     elif a.impl == "reference":
         main_reference(a)
     else:

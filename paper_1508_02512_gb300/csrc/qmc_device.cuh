@@ -592,14 +592,25 @@ DEV void transform_f(int r, float x, float y, float &t, float &tm, float &w) {
 
 DEV uint64_t term_exps_f(const PackedTermF &T) { return *reinterpret_cast<const uint64_t *>(T.e); }
 
+/* Term tables of the FP32 path are read through an accessor: from shared memory (per-thread loads) or from
+   the kernel's parameter space (constant bank: warp-uniform loads, so exponent decoding and loop control run
+   once per warp on the uniform datapath instead of once per thread). */
+struct SmemTabF {
+    const PackedTermF *T;
+    DEV float hi(int i) const { return T[i].hi; }
+    DEV float lo(int i) const { return T[i].lo; }
+    DEV uint64_t ex(int i) const { return term_exps_f(T[i]); }
+};
+
 /* coefficient as hi + lo float pair: two FMAs per term keep the coefficient exact to ~2^-48 */
-template <int S>
-DEV float poly_rf(const PackedTermF *__restrict__ T, int n, const float *t) {
+template <int S, class Tab>
+DEV float poly_rf(const Tab &T, int base, int n, const float *t) {
     float acc = 0.f;
-    for (int a = 0; a < n; ++a) {
-        const uint64_t ew = term_exps_f(T[a]);
+    for (int a = base; a < base + n; ++a) {
+        const uint64_t ew = T.ex(a);
+        const float hi = T.hi(a), lo = T.lo(a);
         if (ew == 0) {
-            acc += T[a].hi + T[a].lo;
+            acc += hi + lo;
             continue;
         }
         float m = 1.f;
@@ -616,18 +627,19 @@ DEV float poly_rf(const PackedTermF *__restrict__ T, int n, const float *t) {
                 for (int k = 0; k < e; ++k) m *= t[j];
             }
         }
-        acc = fmaf(T[a].hi, m, fmaf(T[a].lo, m, acc));
+        acc = fmaf(hi, m, fmaf(lo, m, acc));
     }
     return acc;
 }
 
-template <int S>
-DEV cf poly_cf(const PackedTermF *__restrict__ T, int n, const cf *z) {
+template <int S, class Tab>
+DEV cf poly_cf(const Tab &T, int base, int n, const cf *z) {
     cf acc = mkf(0.f, 0.f);
-    for (int a = 0; a < n; ++a) {
-        const uint64_t ew = term_exps_f(T[a]);
+    for (int a = base; a < base + n; ++a) {
+        const uint64_t ew = T.ex(a);
+        const float hi = T.hi(a), lo = T.lo(a);
         if (ew == 0) {
-            acc.x += T[a].hi + T[a].lo;
+            acc.x += hi + lo;
             continue;
         }
         cf m = mkf(1.f, 0.f);
@@ -644,8 +656,8 @@ DEV cf poly_cf(const PackedTermF *__restrict__ T, int n, const cf *z) {
                 for (int k = 0; k < e; ++k) m = cmulf(m, z[j]);
             }
         }
-        acc.x = fmaf(T[a].hi, m.x, fmaf(T[a].lo, m.x, acc.x));
-        acc.y = fmaf(T[a].hi, m.y, fmaf(T[a].lo, m.y, acc.y));
+        acc.x = fmaf(hi, m.x, fmaf(lo, m.x, acc.x));
+        acc.y = fmaf(hi, m.y, fmaf(lo, m.y, acc.y));
     }
     return acc;
 }
@@ -717,15 +729,14 @@ DEV cf det_deform_f(const float (&A)[S][S], float lam) {
    Im F(z) exceeds that noise */
 #define QMC_F32_SIGN_NOISE 4e-6f
 
-template <int S, bool DEF, int MAXM>
-DEV void eval_G_f(const PackedSector &s, const PackedTermF *__restrict__ T, const float *tt, const float *ttm,
-                  const float *Lt, float lam, int M, const Exps &ex, cf &G0, cf &X, uint32_t &fails) {
-    const PackedTermF *TU = T;
-    const PackedTermF *TF = T + s.nU;
-    const float D = (float)s.D;
+template <int S, bool DEF, int MAXM, class Hdr, class Tab>
+DEV void eval_G_f(const Hdr &s, const Tab &T, int tbase, const float *tt, const float *ttm, const float *Lt, float lam,
+                  int M, const Exps &ex, cf &G0, cf &X, uint32_t &fails) {
+    const int bU = tbase, bF = tbase + s.nU, bG = bF + s.nF, bH = bG + s.nG;
+    const float D = s.Df;
     if constexpr (!DEF) {
-        const float U = poly_rf<S>(TU, s.nU, tt);
-        float F = poly_rf<S>(TF, s.nF, tt);
+        const float U = poly_rf<S>(T, bU, s.nU, tt);
+        float F = poly_rf<S>(T, bF, s.nF, tt);
         if (s.kind == 1) F = -F;
         float g = D * ipowf_(U, ex.eU0) * ipowf_(F, -ex.eF0);
 #pragma unroll
@@ -741,18 +752,16 @@ DEV void eval_G_f(const PackedSector &s, const PackedTermF *__restrict__ T, cons
             X = mkf(x, 0.f);
         }
     } else {
-        const PackedTermF *TG = TF + s.nF;
-        const PackedTermF *TH = TG + s.nG;
         float g[S];
 #pragma unroll
-        for (int j = 0; j < S; ++j) g[j] = poly_rf<S>(TG + s.gstart[j], s.gstart[j + 1] - s.gstart[j], tt);
+        for (int j = 0; j < S; ++j) g[j] = poly_rf<S>(T, bG + s.gstart[j], s.gstart[j + 1] - s.gstart[j], tt);
         float A[S][S];
         int p = 0;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
 #pragma unroll
             for (int k = j; k < S; ++k) {
-                const float h = poly_rf<S>(TH + s.hstart[p], s.hstart[p + 1] - s.hstart[p], tt);
+                const float h = poly_rf<S>(T, bH + s.hstart[p], s.hstart[p + 1] - s.hstart[p], tt);
                 ++p;
                 A[j][k] = tt[j] * ttm[j] * h;
                 if (k != j) A[k][j] = tt[k] * ttm[k] * h;
@@ -769,8 +778,8 @@ DEV void eval_G_f(const PackedSector &s, const PackedTermF *__restrict__ T, cons
             q[j] = mkf(1.f, -d);
         }
         const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
-        const cf U = needU ? poly_cf<S>(TU, s.nU, z) : mkf(1.f, 0.f);
-        const cf F = poly_cf<S>(TF, s.nF, z);
+        const cf U = needU ? poly_cf<S>(T, bU, s.nU, z) : mkf(1.f, 0.f);
+        const cf F = poly_cf<S>(T, bF, s.nF, z);
         fails += (F.y > QMC_F32_SIGN_NOISE * (fabsf(F.x) + fabsf(F.y))) ? 1u : 0u;
         cf G = cscalef(detJ, D);
         if (ex.eU0 != 0) G = cmulf(G, cipowf(U, ex.eU0));
@@ -803,9 +812,9 @@ DEV void eval_G_f(const PackedSector &s, const PackedTermF *__restrict__ T, cons
     }
 }
 
-template <int S, bool DEF, int MAXM>
-DEV void point_integrand_f(const PackedSector &s, const PackedTermF *__restrict__ T, const float *x, const float *y,
-                           int r, float lam, const Exps &ex, cf (&out)[MAXM + 1], uint32_t &fails) {
+template <int S, bool DEF, int MAXM, class Hdr, class Tab>
+DEV void point_integrand_f(const Hdr &s, const Tab &T, int tbase, const float *x, const float *y, int r, float lam,
+                           const Exps &ex, cf (&out)[MAXM + 1], uint32_t &fails) {
     float t[S], tm[S], w = 1.f;
     bool bad = false;
 #pragma unroll
@@ -838,7 +847,7 @@ DEV void point_integrand_f(const PackedSector &s, const PackedTermF *__restrict_
             ttm[j] = zj ? 1.f : tm[j];
         }
         cf G0, X;
-        eval_G_f<S, DEF, MAXM>(s, T, tt, ttm, Lt, lam, M, ex, G0, X, fails);
+        eval_G_f<S, DEF, MAXM>(s, T, tbase, tt, ttm, Lt, lam, M, ex, G0, X, fails);
         float V[MAXM + 1];
         V[0] = 1.f;
 #pragma unroll
@@ -974,7 +983,7 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel_f32(EvalArgs a) {
 #pragma unroll
                 for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], a.n, invnf, x[j], y[j]);
                 cf val[MAXM + 1];
-                point_integrand_f<S, DEF, MAXM>(sec, T, x, y, a.r, lam, ex, val, fails);
+                point_integrand_f<S, DEF, MAXM>(sec, SmemTabF{T}, 0, x, y, a.r, lam, ex, val, fails);
 #pragma unroll
                 for (int n = 0; n <= MAXM; ++n) {
                     two_sum_acc(acc[2 * n], cmp[2 * n], val[n].x);
@@ -988,6 +997,109 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel_f32(EvalArgs a) {
             }
         }
         /* warp: double-float shuffle tree; warps and items in FP64 */
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) {
+            float s1 = acc[q], c1 = cmp[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float so = __shfl_down_sync(0xffffffffu, s1, off);
+                const float co = __shfl_down_sync(0xffffffffu, c1, off);
+                two_sum_acc(s1, c1, so);
+                c1 += co;
+            }
+            if (lane == 0) s_red[warp][q] = (double)s1 + (double)c1;
+        }
+        uint32_t f = fails;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+        if (lane == 0) s_fail[warp] = f;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            if (q < a.n_slots * 2) {
+                double s2 = 0.0, c2 = 0.0;
+                if (q < 2 * (MAXM + 1))
+                    for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
+                a.partials[item * a.n_slots * 2 + q] = s2 - c2;
+            }
+            if (q == 0) {
+                uint32_t tf = 0;
+                for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
+                a.part_fails[item] = tf;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+/* ------------------------------------------------------------------ K2 with tables in kernel parameters */
+struct ParamTabF {
+    const ParamGroup *g;
+    DEV float hi(int i) const { return g->terms[i].hi; }
+    DEV float lo(int i) const { return g->terms[i].lo; }
+    DEV uint64_t ex(int i) const { return *reinterpret_cast<const uint64_t *>(g->terms[i].e); }
+};
+
+/* Persistent blocks take items from an atomic counter, as in the shared-memory kernels; the tables are read
+   from the kernel parameter block (constant bank), so nothing is staged and a block may change sector at any
+   item. */
+template <int S, bool DEF, int MAXM>
+__global__ void __launch_bounds__(256) qmc_eval_kernel_f32p(EvalArgs a, const __grid_constant__ ParamGroup g) {
+    __shared__ long long s_item;
+    __shared__ double s_red[16][2 * (MAXM + 1)];
+    __shared__ uint32_t s_fail[16];
+    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
+    const long long per_sector = (long long)a.m * a.chunks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const float invnf = 1.f / (float)a.n;
+    const ParamTabF tab{&g};
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= a.total_items) break;
+        const int ls = (int)(item / per_sector);
+        const long long rem = item - (long long)ls * per_sector;
+        const int shift = (int)(rem / a.chunks);
+        const long long chunk = rem - (long long)shift * a.chunks;
+        const ParamSector &sec = g.sec[ls];
+        if (a.sector_prec && a.sector_prec[sec.orig_index] != 1) {
+            __syncthreads();
+            continue;
+        }
+        const float lam = (float)a.lambda[sec.orig_index];
+        uint32_t rj[S], aj[S];
+        float bj[S];
+        const long long i0 = chunk * (long long)blockDim.x * a.P + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            split_shift(a.shifts[6 * shift + j], a.n, aj[j], bj[j]);
+            rj[j] = (uint32_t)(((unsigned long long)i0 * a.z[j]) % a.n);
+        }
+        float acc[2 * (MAXM + 1)], cmp[2 * (MAXM + 1)];
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
+        uint32_t fails = 0;
+        for (int p = 0; p < a.P; ++p) {
+            const long long i = i0 + (long long)p * blockDim.x;
+            if (i < (long long)a.n) {
+                float x[S], y[S];
+#pragma unroll
+                for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], a.n, invnf, x[j], y[j]);
+                cf val[MAXM + 1];
+                point_integrand_f<S, DEF, MAXM>(sec, tab, sec.tbase, x, y, a.r, lam, ex, val, fails);
+#pragma unroll
+                for (int n = 0; n <= MAXM; ++n) {
+                    two_sum_acc(acc[2 * n], cmp[2 * n], val[n].x);
+                    two_sum_acc(acc[2 * n + 1], cmp[2 * n + 1], val[n].y);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const uint32_t v = rj[j] + a.zstep[j];
+                rj[j] = v >= a.n ? v - a.n : v;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) {
             float s1 = acc[q], c1 = cmp[q];
@@ -1071,7 +1183,7 @@ __global__ void __launch_bounds__(128) qmc_probe_kernel(ProbeArgs a) {
         cd v64[MAXM + 1];
         cf v32[MAXM + 1];
         point_integrand<S, DEF, MAXM>(sec, T, x, a.r, lam, ex, v64, f64);
-        point_integrand_f<S, DEF, MAXM>(sec, TF, xf, yf, a.r, (float)lam, ex, v32, f32);
+        point_integrand_f<S, DEF, MAXM>(sec, SmemTabF{TF}, 0, xf, yf, a.r, (float)lam, ex, v32, f32);
 #pragma unroll
         for (int n = 0; n <= MAXM; ++n) {
             const double dr = (double)v32[n].x - v64[n].x, di = (double)v32[n].y - v64[n].y;
@@ -1161,6 +1273,20 @@ static int occupancy_f32_t(int block, int smem, int *out) {
     auto k = qmc_eval_kernel_f32<S, DEF, MAXM>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return QMC_ERR_CUDA;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, block, smem) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+template <int S, bool DEF, int MAXM>
+static int launch_eval_param_t(const EvalArgs &a, const ParamGroup &g, int grid, int block, cudaStream_t st) {
+    qmc_eval_kernel_f32p<S, DEF, MAXM><<<grid, block, 0, st>>>(a, g);
+    return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+template <int S, bool DEF, int MAXM>
+static int occupancy_param_t(int block, int *out) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, qmc_eval_kernel_f32p<S, DEF, MAXM>, block, 0) ==
+                   cudaSuccess
+               ? QMC_OK
+               : QMC_ERR_CUDA;
 }
 
 template <int S, bool DEF, int MAXM>

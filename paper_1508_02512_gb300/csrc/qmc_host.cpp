@@ -385,6 +385,7 @@ int pack_table(const Table &t, const double *inv, int n_inv, int order_min, int 
         PackedSector &ps = w.ps;
         ps.kind = kind;
         ps.D = s.D;
+        ps.Df = (float)s.D;
         ps.orig_index = si;
         int sigma = 0, mask = 0;
         for (int j = 0; j < d; ++j) {
@@ -602,7 +603,8 @@ int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
     auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
     pl.partial_bytes = up((size_t)pl.total_items * h->n_slots * 2 * sizeof(double));
     pl.fail_bytes = up((size_t)pl.total_items * sizeof(uint32_t));
-    pl.counter_bytes = up(2 * QMC_N_CLASSES * sizeof(unsigned long long)); /* per class and precision */
+    /* work counters: per class and precision, plus one per launch of the parameter-table FP32 kernel */
+    pl.counter_bytes = up((2 * QMC_N_CLASSES + QMC_MAX_GROUP_LAUNCHES) * sizeof(unsigned long long));
     pl.total_bytes = pl.partial_bytes + pl.fail_bytes + pl.counter_bytes;
     return QMC_OK;
 }
@@ -720,6 +722,71 @@ int check_pass(const PackedHeader *h, const void *packed_dev, const qmc_pass *pa
 
 int class_maxm(const PackedHeader *h, int c) { return h->class_maxm[c] == 0 ? 0 : (h->class_maxm[c] <= 2 ? 2 : 4); }
 
+/* FP32 evaluation with the sector tables in the kernel's parameter block: the class's sectors are cut into
+   groups of at most QMC_PARAM_SECTORS sectors and QMC_PARAM_TERMS terms, one launch per group, each with its own
+   work counter and its slice of the class's item range (items of a sector are contiguous). */
+int launch_param_groups(const PackedHeader *h, const void *packed_host, int c, int maxm, const EvalArgs &base,
+                        const Plan &pl, const Scratch &sc, int sms, int &group_launches, void *stream) {
+    const unsigned char *img = static_cast<const unsigned char *>(packed_host);
+    const PackedSector *ps = reinterpret_cast<const PackedSector *>(img + h->sectors_off);
+    const PackedTermF *tf = reinterpret_cast<const PackedTermF *>(img + h->termsf_off);
+    int per_sm = 0;
+    int rc = qmc_eval_param_blocks_per_sm(h->dim, c == 1, maxm, pl.block, &per_sm);
+    if (rc) return rc;
+    if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
+    std::unique_ptr<ParamGroup> g(new ParamGroup());
+    const int64_t per_sector = (int64_t)base.m * base.chunks;
+    int s0 = h->class_begin[c];
+    while (s0 < h->class_end[c]) {
+        std::memset(g.get(), 0, sizeof(ParamGroup));
+        int ns = 0, nt = 0;
+        while (s0 + ns < h->class_end[c] && ns < QMC_PARAM_SECTORS && nt + ps[s0 + ns].n_terms <= QMC_PARAM_TERMS) {
+            const PackedSector &q = ps[s0 + ns];
+            ParamSector &d = g->sec[ns];
+            d.kind = q.kind;
+            d.sigma = q.sigma;
+            d.sing_mask = q.sing_mask;
+            d.M = q.M;
+            for (int j = 0; j < 6; ++j) {
+                d.A[j] = q.A[j];
+                d.B[j] = q.B[j];
+            }
+            d.nU = q.nU;
+            d.nF = q.nF;
+            d.nG = q.nG;
+            d.nH = q.nH;
+            d.tbase = nt;
+            d.orig_index = q.orig_index;
+            d.psec = s0 + ns;
+            d.Df = q.Df;
+            for (int j = 0; j < 8; ++j) d.gstart[j] = q.gstart[j];
+            for (int j = 0; j < 24; ++j) d.hstart[j] = q.hstart[j];
+            std::memcpy(&g->terms[nt], tf + q.term0, sizeof(PackedTermF) * q.n_terms);
+            nt += q.n_terms;
+            ++ns;
+        }
+        if (ns == 0) return QMC_ERR_UNSUPPORTED;
+        if (group_launches >= QMC_MAX_GROUP_LAUNCHES) return QMC_ERR_UNSUPPORTED;
+        g->n_sect = ns;
+        g->n_terms = nt;
+        EvalArgs a = base;
+        const int64_t first = (int64_t)(s0 - h->class_begin[c]) * per_sector;
+        a.sector_begin = s0;
+        a.n_sect = ns;
+        a.total_items = (int64_t)ns * per_sector;
+        a.partials = base.partials + first * h->n_slots * 2;
+        a.part_fails = base.part_fails + first;
+        a.counter = sc.counters + 2 * QMC_N_CLASSES + group_launches;
+        ++group_launches;
+        int64_t grid = (int64_t)sms * per_sm;
+        if (grid > a.total_items) grid = a.total_items;
+        rc = qmc_launch_eval_param(h->dim, c == 1, maxm, a, *g, (int)grid, pl.block, stream);
+        if (rc) return rc;
+        s0 += ns;
+    }
+    return QMC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -734,12 +801,14 @@ int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc
     int rc = check_pass(h, packed_dev, pass, scratch_dev, scratch_bytes, pl, sc);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    rc = cuda_status(cudaMemsetAsync(sc.counters, 0, 2 * QMC_N_CLASSES * sizeof(unsigned long long), st));
+    rc = cuda_status(cudaMemsetAsync(sc.counters, 0,
+                                     (2 * QMC_N_CLASSES + QMC_MAX_GROUP_LAUNCHES) * sizeof(unsigned long long), st));
     if (rc) return rc;
     int sms = 0;
     rc = qmc_device_sm_count(&sms);
     if (rc) return rc;
     const size_t smem = sizeof(PackedSector) + (size_t)h->max_terms * sizeof(PackedTerm);
+    int group_launches = 0;
     /* FP64 pass: one kernel per class.  Mixed pass: the FP32 kernel takes the sectors marked 1 in
        pass->sector_precision (all when it is null), the FP64 kernel the others; both share the item space. */
     const bool mixed = pass->precision == QMC_PREC_MIXED;
@@ -782,6 +851,12 @@ int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc
             a.smem_bytes = (int)smem;
             a.sector_prec = mixed ? pass->sector_precision : nullptr;
             a.want_prec = prec;
+            if (prec == 1 && h->max_terms <= QMC_PARAM_TERMS) {
+                /* FP32 with the tables in kernel parameters: groups of consecutive sectors per launch */
+                rc = launch_param_groups(h, packed_host, c, maxm, a, pl, sc, sms, group_launches, stream);
+                if (rc) return rc;
+                continue;
+            }
             int per_sm = 0;
             rc = qmc_eval_blocks_per_sm(h->dim, c == 1, maxm, kprec, pl.block, (int)smem, &per_sm);
             if (rc) return rc;

@@ -55,7 +55,8 @@ struct PackedSector {
     int16_t hstart[24]; /* Hessian polynomial p (j <= k): terms [hstart[p], hstart[p+1]) of the H block */
     double D;
     double flops, transc;
-    double pad;
+    float Df;           /* D rounded to FP32 (the FP32 path must not convert FP64 values per point) */
+    float pad;
 };
 
 struct PackedTerm {
@@ -100,6 +101,31 @@ struct EvalArgs {
     const int32_t *sector_prec;   /* per sector (table order): 0 FP64, 1 FP32; null = all of want_prec */
     int32_t want_prec;            /* items of sectors with another precision are skipped */
 };
+
+/* FP32 kernel with its tables in kernel parameters (constant bank): a group of sectors per launch. */
+#define QMC_PARAM_SECTORS 16
+#define QMC_PARAM_TERMS 1600
+#define QMC_MAX_GROUP_LAUNCHES 1024
+
+struct ParamSector {
+    int32_t kind, sigma, sing_mask, M;
+    int32_t A[6], B[6];
+    int32_t nU, nF, nG, nH;
+    int32_t tbase;      /* first term of the sector in ParamGroup::terms */
+    int32_t orig_index;
+    int32_t psec;       /* packed index */
+    float Df;
+    int16_t gstart[8];
+    int16_t hstart[24];
+};
+
+struct ParamGroup {
+    int32_t n_sect, n_terms, pad0, pad1;
+    ParamSector sec[QMC_PARAM_SECTORS];
+    PackedTermF terms[QMC_PARAM_TERMS];
+};
+
+static_assert(sizeof(ParamSector) % 16 == 0, "param sector must be 16-byte aligned");
 
 /* Precision probe: a strided sample of each sector's lattice points for one shift, in FP32 and FP64. */
 struct ProbeArgs {
@@ -155,3 +181,6 @@ int qmc_launch_points(int dim, int deform, int maxm, int precision, const PointA
 int qmc_device_sm_count(int *sms);
 int qmc_eval_blocks_per_sm(int dim, int deform, int maxm, int precision, int block, int smem_bytes, int *out);
 int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *stream);
+int qmc_launch_eval_param(int dim, int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                          void *stream);
+int qmc_eval_param_blocks_per_sm(int dim, int deform, int maxm, int block, int *out);

@@ -29,6 +29,25 @@ int qmc_occupancy_d6(int deform, int maxm, int precision, int block, int smem, i
 int qmc_launch_probe_d6(int deform, int maxm, const ProbeArgs &a, cudaStream_t st);
 int qmc_launch_points_d6(int deform, int maxm, const PointArgs &a, cudaStream_t st);
 
+int qmc_launch_eval_param_d1(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                              cudaStream_t st);
+int qmc_occupancy_param_d1(int deform, int maxm, int block, int *out);
+int qmc_launch_eval_param_d2(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                              cudaStream_t st);
+int qmc_occupancy_param_d2(int deform, int maxm, int block, int *out);
+int qmc_launch_eval_param_d3(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                              cudaStream_t st);
+int qmc_occupancy_param_d3(int deform, int maxm, int block, int *out);
+int qmc_launch_eval_param_d4(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                              cudaStream_t st);
+int qmc_occupancy_param_d4(int deform, int maxm, int block, int *out);
+int qmc_launch_eval_param_d5(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                              cudaStream_t st);
+int qmc_occupancy_param_d5(int deform, int maxm, int block, int *out);
+int qmc_launch_eval_param_d6(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                              cudaStream_t st);
+int qmc_occupancy_param_d6(int deform, int maxm, int block, int *out);
+
 /* ------------------------------------------------------------------ K4: deterministic per-(sector, shift) sums */
 __global__ void __launch_bounds__(128) qmc_finalize_kernel(FinalizeArgs a) {
     const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -113,6 +132,32 @@ int qmc_launch_points(int dim, int deform, int maxm, int precision, const PointA
         case 4: return qmc_launch_points_d4(deform, maxm, a, st);
         case 5: return qmc_launch_points_d5(deform, maxm, a, st);
         case 6: return qmc_launch_points_d6(deform, maxm, a, st);
+        default: return QMC_ERR_UNSUPPORTED;
+    }
+}
+
+int qmc_launch_eval_param(int dim, int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
+                          void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (dim) {
+        case 1: return qmc_launch_eval_param_d1(deform, maxm, a, g, grid, block, st);
+        case 2: return qmc_launch_eval_param_d2(deform, maxm, a, g, grid, block, st);
+        case 3: return qmc_launch_eval_param_d3(deform, maxm, a, g, grid, block, st);
+        case 4: return qmc_launch_eval_param_d4(deform, maxm, a, g, grid, block, st);
+        case 5: return qmc_launch_eval_param_d5(deform, maxm, a, g, grid, block, st);
+        case 6: return qmc_launch_eval_param_d6(deform, maxm, a, g, grid, block, st);
+        default: return QMC_ERR_UNSUPPORTED;
+    }
+}
+
+int qmc_eval_param_blocks_per_sm(int dim, int deform, int maxm, int block, int *out) {
+    switch (dim) {
+        case 1: return qmc_occupancy_param_d1(deform, maxm, block, out);
+        case 2: return qmc_occupancy_param_d2(deform, maxm, block, out);
+        case 3: return qmc_occupancy_param_d3(deform, maxm, block, out);
+        case 4: return qmc_occupancy_param_d4(deform, maxm, block, out);
+        case 5: return qmc_occupancy_param_d5(deform, maxm, block, out);
+        case 6: return qmc_occupancy_param_d6(deform, maxm, block, out);
         default: return QMC_ERR_UNSUPPORTED;
     }
 }
