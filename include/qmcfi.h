@@ -94,6 +94,17 @@ typedef struct {
                                         1 = evaluate in FP32, anything else = FP64; NULL = every sector FP32 */
 } qmc_pass;
 
+/* One pass of one prepared integral, as an element of a batch (qmc_eval_batch). */
+typedef struct {
+    const void *packed_host;   /* image from qmc_prepare, host copy */
+    const void *packed_dev;    /* the same image in device memory (16-byte aligned) */
+    qmc_pass pass;
+    const double *shifts_dev;  /* pass.n_shifts x 6 */
+    const double *lambda_dev;  /* one per sector */
+    double *sums_dev;          /* outputs as in qmc_eval_sums */
+    int64_t *fails_dev;
+} qmc_batch_item;
+
 /* Text for a status code (static storage). */
 const char *qmc_strerror(int status);
 
@@ -137,6 +148,18 @@ size_t qmc_scratch_bytes(const void *packed, const qmc_pass *pass);
 int qmc_eval_sums(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shifts_dev,
                   const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, double *sums_dev,
                   int64_t *fails_dev, void *stream);
+
+/*
+ * qmc_eval_batch -- many passes (different integrals, kinematic points, lattices or shifts) in shared launches,
+ * asynchronous on `stream`: every (pass, sector class, precision) becomes a job, and jobs that use the same kernel
+ * instantiation go into one persistent launch whose blocks take work items across all of them (continuous
+ * batching for the serving loop).  Each pass's results are identical, bit for bit, to running it alone with
+ * qmc_eval_sums (per-item work and reduction order do not depend on the batch).  scratch: at least
+ * qmc_batch_scratch_bytes(items, n) bytes, 256-byte aligned.  The paper evaluates one integral at a time; the
+ * batching is this library's (Sec. III, Eqs. 16-18 per pass).
+ */
+size_t qmc_batch_scratch_bytes(const qmc_batch_item *items, int32_t n);
+int qmc_eval_batch(const qmc_batch_item *items, int32_t n, void *scratch_dev, size_t scratch_bytes, void *stream);
 
 /* The two launches of qmc_eval_sums, exposed separately (same arguments and semantics): qmc_eval_partials runs
  * the evaluation kernel and leaves one partial sum per work item and slot in the scratch buffer;
@@ -229,7 +252,15 @@ typedef struct {
     double seconds;                   /* wall time of qmc_integrate */
     double kernel_ms;                 /* device time of the evaluation kernels, all passes */
     int32_t passes, lambda_halvings, fp64_reruns, sign_failures;
+    double queued_seconds;            /* serving: time between qmc_submit and admission */
 } qmc_result;
+
+typedef struct {
+    int64_t submitted, completed, queued, active, peak_active;
+    int64_t rounds;                   /* batched rounds run by the scheduler */
+    int64_t batched_passes;           /* passes run, summed over rounds */
+    int64_t device_bytes;             /* device memory held by the context */
+} qmc_serving_stats;
 
 /* Context: owns a CUDA stream binding, the device copies of loaded integrals and its scratch.
  * device: CUDA ordinal; mem_budget: bytes of device memory the context may hold (0 = 1 GiB);
@@ -255,6 +286,26 @@ int qmc_eval_sums_host(qmc_ctx *ctx, const void *packed_host, const qmc_pass *pa
  * sectors that fail the sign check, until every order meets the tolerance (or a limit is reached).
  * Returns the status also stored in out->status. */
 int qmc_integrate(qmc_ctx *ctx, int32_t integral_id, const qmc_options *opt, qmc_result *out);
+
+/* ------------------------------------------------------------------ serving (continuous batching) */
+/* Queue an integration request: the integral `integral_id` (loaded with qmc_load_sectors) at the kinematic point
+ * `invariants`, Laurent orders order_min..order_max, options as for qmc_integrate.  A scheduler thread of the
+ * context admits requests while its device-memory budget has room and runs batched rounds: each active request
+ * contributes the pass at its current lattice size to shared launches (qmc_eval_batch); requests that arrive
+ * meanwhile join at the next round.  A request's result is the same, bit for bit, as qmc_integrate with the same
+ * options would give alone.  The paper has no serving loop; this is the library's deployment layer. */
+int qmc_submit(qmc_ctx *ctx, int32_t integral_id, const double *invariants, int32_t n_invariants, int32_t order_min,
+               int32_t order_max, const qmc_options *opt, int64_t *request_id);
+
+/* QMC_PENDING while the request is queued or running; otherwise fills `out` and returns its final status.
+ * out->seconds is the time from submission to completion, out->queued_seconds the wait before admission. */
+int qmc_poll(qmc_ctx *ctx, int64_t request_id, qmc_result *out);
+
+/* Marks a request cancelled; it leaves at the next round boundary with status QMC_ERR_CANCELLED. */
+int qmc_cancel(qmc_ctx *ctx, int64_t request_id);
+
+/* Counters of the serving loop. */
+int qmc_serving_stats_get(qmc_ctx *ctx, qmc_serving_stats *out);
 
 #ifdef __cplusplus
 }

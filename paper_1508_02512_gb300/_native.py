@@ -56,6 +56,11 @@ class qmc_pass(ctypes.Structure):
                 ("sector_precision", c_void_p)]
 
 
+class qmc_batch_item(ctypes.Structure):
+    _fields_ = [("packed_host", c_void_p), ("packed_dev", c_void_p), ("pass_", qmc_pass), ("shifts_dev", c_void_p),
+                ("lambda_dev", c_void_p), ("sums_dev", c_void_p), ("fails_dev", c_void_p)]
+
+
 class qmc_options(ctypes.Structure):
     _fields_ = [("rel_tol", c_double), ("abs_tol", c_double), ("precision", c_int32), ("n_shifts", c_int32),
                 ("seed", c_uint64), ("lambda_", c_double), ("max_halvings", c_int32), ("transform_r", c_int32),
@@ -69,7 +74,13 @@ class qmc_result(ctypes.Structure):
                 ("value", (c_double * 2) * QMC_MAX_ORDERS), ("error", (c_double * 2) * QMC_MAX_ORDERS),
                 ("n_final", c_int64), ("evals", c_int64), ("seconds", c_double), ("kernel_ms", c_double),
                 ("passes", c_int32), ("lambda_halvings", c_int32), ("fp64_reruns", c_int32),
-                ("sign_failures", c_int32)]
+                ("sign_failures", c_int32), ("queued_seconds", c_double)]
+
+
+class qmc_serving_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("queued", c_int64), ("active", c_int64),
+                ("peak_active", c_int64), ("rounds", c_int64), ("batched_passes", c_int64),
+                ("device_bytes", c_int64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/qmcfi.h
@@ -82,6 +93,8 @@ PROTOTYPES = {
     "qmc_scratch_bytes": (c_size_t, [c_void_p, POINTER(qmc_pass)]),
     "qmc_eval_sums": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_size_t,
                               c_void_p, c_void_p, c_void_p]),
+    "qmc_batch_scratch_bytes": (c_size_t, [c_void_p, c_int32]),
+    "qmc_eval_batch": (c_int, [c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "qmc_eval_partials": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_size_t,
                                   c_void_p]),
     "qmc_reduce_partials": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_size_t, c_void_p, c_void_p,
@@ -99,6 +112,11 @@ PROTOTYPES = {
     "qmc_load_sectors": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_int32)]),
     "qmc_set_kinematics": (c_int, [c_void_p, c_int32, POINTER(c_double), c_int32, c_int32, c_int32]),
     "qmc_eval_sums_host": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p]),
+    "qmc_submit": (c_int, [c_void_p, c_int32, POINTER(c_double), c_int32, c_int32, c_int32, POINTER(qmc_options),
+                           POINTER(c_int64)]),
+    "qmc_poll": (c_int, [c_void_p, c_int64, POINTER(qmc_result)]),
+    "qmc_cancel": (c_int, [c_void_p, c_int64]),
+    "qmc_serving_stats_get": (c_int, [c_void_p, POINTER(qmc_serving_stats)]),
     "qmc_integrate": (c_int, [c_void_p, c_int32, POINTER(qmc_options), POINTER(qmc_result)]),
 }
 

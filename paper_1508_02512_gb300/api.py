@@ -167,6 +167,63 @@ class Context:
         N.check(N.lib().qmc_set_kinematics(self._c, integral_id, _dptr(inv), len(inv), order_min, order_max),
                 "qmc_set_kinematics")
 
+    @staticmethod
+    def options(rel_tol=1e-3, abs_tol=0.0, precision=N.QMC_PREC_FP64, n_shifts=16, seed=0, lam=0.5, transform_r=3,
+                ladder_start=0, lattices=None, shifts=None, max_n=0, max_seconds=0.0, max_halvings=6, block=0,
+                points_per_thread=0):
+        """qmc_options and the Python objects that must outlive the call that uses them."""
+        o = N.qmc_options()
+        o.rel_tol, o.abs_tol, o.precision, o.n_shifts, o.seed = rel_tol, abs_tol, precision, n_shifts, seed
+        o.lambda_, o.max_halvings, o.transform_r, o.ladder_start = lam, max_halvings, transform_r, ladder_start
+        o.max_n, o.max_seconds, o.block, o.points_per_thread = max_n, max_seconds, block, points_per_thread
+        keep = []
+        if lattices is not None:
+            arr = (N.qmc_lattice * len(lattices))(*[make_lattice(n, z) for n, z in lattices])
+            keep.append(arr)
+            o.n_lattices = len(lattices)
+            o.lattices = arr
+        if shifts is not None:
+            sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
+            keep.append(sh)
+            o.shifts = _dptr(sh)
+        return o, keep
+
+    def submit(self, integral_id: int, invariants, order_min: int, order_max: int, **kw) -> int:
+        """qmc_submit: queue a request with the serving loop; returns its id."""
+        o, keep = self.options(**kw)
+        inv = np.ascontiguousarray(np.asarray(invariants, dtype=np.float64))
+        rid = ctypes.c_int64()
+        N.check(N.lib().qmc_submit(self._c, integral_id, _dptr(inv), len(inv), order_min, order_max, ctypes.byref(o),
+                                   ctypes.byref(rid)), "qmc_submit")
+        return rid.value
+
+    def poll(self, request_id: int):
+        """(status, qmc_result or None): status QMC_PENDING while queued or running."""
+        r = N.qmc_result()
+        st = N.lib().qmc_poll(self._c, request_id, ctypes.byref(r))
+        if st == N.QMC_ERR_NOT_FOUND:
+            raise N.QMCError(st, "qmc_poll")
+        return st, (None if st == N.QMC_PENDING else r)
+
+    def wait(self, request_id: int, timeout: float = 600.0, interval: float = 1e-4):
+        import time
+        t0 = time.perf_counter()
+        while True:
+            st, r = self.poll(request_id)
+            if st != N.QMC_PENDING:
+                return r
+            if time.perf_counter() - t0 > timeout:
+                raise TimeoutError(f"request {request_id} still pending after {timeout} s")
+            time.sleep(interval)
+
+    def cancel(self, request_id: int):
+        N.check(N.lib().qmc_cancel(self._c, request_id), "qmc_cancel")
+
+    def serving_stats(self) -> N.qmc_serving_stats:
+        st = N.qmc_serving_stats()
+        N.check(N.lib().qmc_serving_stats_get(self._c, ctypes.byref(st)), "qmc_serving_stats_get")
+        return st
+
     def integrate(self, integral_id: int, rel_tol=1e-3, abs_tol=0.0, precision=N.QMC_PREC_FP64, n_shifts=16, seed=0,
                   lam=0.5, transform_r=3, ladder_start=0, lattices=None, shifts=None, max_n=0, max_seconds=0.0,
                   max_halvings=6, block=0, points_per_thread=0) -> N.qmc_result:

@@ -426,51 +426,75 @@ DEV void kahan_add(double &s, double &c, double v) {
     s = t;
 }
 
-/* ------------------------------------------------------------------ K1: persistent evaluation */
+/* ------------------------------------------------------------------ job lookup */
+/* the job whose item range contains `item` (jobs are in increasing item_begin) */
+DEV int find_job(const JobTable &jt, long long item) {
+    int lo = 0, hi = jt.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jt.jobs[mid].item_begin <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------ K1: persistent FP64 evaluation */
 template <int S, bool DEF, int MAXM>
-__global__ void __launch_bounds__(256) qmc_eval_kernel(EvalArgs a) {
+__global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ JobTable jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
+    __shared__ int s_job;
     __shared__ double s_red[16][2 * (MAXM + 1)];
     __shared__ uint32_t s_fail[16];
     const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
     const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
-    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
-    const long long per_sector = (long long)a.m * a.chunks;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    int cur = -1;
+    int cur = -1, cur_job = -1;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1ull);
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(jt.counter, 1ull);
+            s_item = it;
+            s_job = it < jt.total_items ? find_job(jt, it) : 0;
+        }
         __syncthreads();
         const long long item = s_item;
-        if (item >= a.total_items) break;
-        const int ls = (int)(item / per_sector);
-        const long long rem = item - (long long)ls * per_sector;
-        const int shift = (int)(rem / a.chunks);
-        const long long chunk = rem - (long long)shift * a.chunks;
-        const int psec = a.sector_begin + ls;
-        if (a.sector_prec) {
+        if (item >= jt.total_items) break;
+        const int jb = s_job;
+        const Job &J = jt.jobs[jb];
+        const long long local = item - J.item_begin;
+        const long long per_sector = (long long)J.m * J.chunks;
+        const int ls = (int)(local / per_sector);
+        const long long rem = local - (long long)ls * per_sector;
+        const int shift = (int)(rem / J.chunks);
+        const long long chunk = rem - (long long)shift * J.chunks;
+        const int psec = J.sector_begin + ls;
+        if (J.sector_prec) {
             /* mixed pass: items of sectors evaluated in FP32 belong to the other kernel */
-            const PackedSector *gps = reinterpret_cast<const PackedSector *>(a.packed + a.sectors_off) + psec;
-            if (a.sector_prec[gps->orig_index] == 1) {
+            const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
+            if (J.sector_prec[gps->orig_index] == 1) {
                 __syncthreads();
                 continue;
             }
         }
-        if (psec != cur) {
-            stage_sector(a.packed, a.sectors_off, a.terms_off, psec, smem);
+        if (psec != cur || jb != cur_job) {
+            stage_sector(J.packed, J.sectors_off, J.terms_off, psec, smem);
             __syncthreads();
             cur = psec;
+            cur_job = jb;
         }
-        const double lam = a.lambda[sec.orig_index];
+        const Exps ex{J.eU0, J.eU1, J.eF0, J.eF1};
+        const uint32_t n = J.n;
+        const double invn = J.invn;
+        const double lam = J.lambda[sec.orig_index];
         double delta[S];
-        uint32_t rj[S], Rj[S];
-        const long long i0 = chunk * (long long)blockDim.x * a.P + threadIdx.x;
+        uint32_t rj[S], Rj[S], zs[S];
+        const long long i0 = chunk * (long long)blockDim.x * jt.P + threadIdx.x;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            delta[j] = a.shifts[6 * shift + j];
-            rj[j] = (uint32_t)(((unsigned long long)i0 * a.z[j]) % a.n);
-            Rj[j] = wrap_threshold(delta[j], a.n, a.invn);
+            delta[j] = J.shifts[6 * shift + j];
+            rj[j] = (uint32_t)(((unsigned long long)i0 * J.z[j]) % n);
+            Rj[j] = wrap_threshold(delta[j], n, invn);
+            zs[j] = J.zstep[j];
         }
         /* a thread sums its P points plainly; the block combines threads by a shuffle tree, warps and items
            with compensated (Kahan) sums */
@@ -478,27 +502,26 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel(EvalArgs a) {
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = 0.0;
         uint32_t fails = 0;
-        for (int p = 0; p < a.P; ++p) {
+        for (int p = 0; p < jt.P; ++p) {
             const long long i = i0 + (long long)p * blockDim.x;
-            if (i < (long long)a.n) {
+            if (i < (long long)n) {
                 double x[S];
 #pragma unroll
-                for (int j = 0; j < S; ++j) x[j] = fma((double)rj[j], a.invn, delta[j]) - (rj[j] >= Rj[j] ? 1.0 : 0.0);
+                for (int j = 0; j < S; ++j) x[j] = fma((double)rj[j], invn, delta[j]) - (rj[j] >= Rj[j] ? 1.0 : 0.0);
                 cd val[MAXM + 1];
-                point_integrand<S, DEF, MAXM>(sec, T, x, a.r, lam, ex, val, fails);
+                point_integrand<S, DEF, MAXM>(sec, T, x, jt.r, lam, ex, val, fails);
 #pragma unroll
-                for (int n = 0; n <= MAXM; ++n) {
-                    acc[2 * n] += val[n].x;
-                    acc[2 * n + 1] += val[n].y;
+                for (int m = 0; m <= MAXM; ++m) {
+                    acc[2 * m] += val[m].x;
+                    acc[2 * m + 1] += val[m].y;
                 }
             }
 #pragma unroll
             for (int j = 0; j < S; ++j) {
-                const uint32_t v = rj[j] + a.zstep[j];
-                rj[j] = v >= a.n ? v - a.n : v;
+                const uint32_t v = rj[j] + zs[j];
+                rj[j] = v >= n ? v - n : v;
             }
         }
-        /* block reduction: warp shuffles, then warp 0 over the warps in a fixed order */
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) {
             double v = acc[q];
@@ -513,16 +536,16 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel(EvalArgs a) {
         __syncthreads();
         if (threadIdx.x < 32) {
             const int q = threadIdx.x;
-            if (q < a.n_slots * 2) {
-                double s = 0.0, c = 0.0;
+            if (q < J.n_slots * 2) {
+                double s2 = 0.0, c2 = 0.0;
                 if (q < 2 * (MAXM + 1))
-                    for (int w = 0; w < nwarps; ++w) kahan_add(s, c, s_red[w][q]);
-                a.partials[item * a.n_slots * 2 + q] = s - c;
+                    for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
+                J.partials[local * J.n_slots * 2 + q] = s2 - c2;
             }
             if (q == 0) {
                 uint32_t tf = 0;
                 for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
-                a.part_fails[item] = tf;
+                J.part_fails[local] = tf;
             }
         }
         __syncthreads();
@@ -929,71 +952,83 @@ DEV void stage_sector_f(const unsigned char *packed, int64_t sectors_off, int64_
 
 /* ------------------------------------------------------------------ K2: persistent FP32 evaluation */
 template <int S, bool DEF, int MAXM>
-__global__ void __launch_bounds__(256) qmc_eval_kernel_f32(EvalArgs a) {
+__global__ void __launch_bounds__(256) qmc_eval_kernel_f32(const __grid_constant__ JobTable jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
+    __shared__ int s_job;
     __shared__ double s_red[16][2 * (MAXM + 1)];
     __shared__ uint32_t s_fail[16];
     const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
     const PackedTermF *T = reinterpret_cast<const PackedTermF *>(smem + sizeof(PackedSector));
-    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
-    const long long per_sector = (long long)a.m * a.chunks;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const float invnf = 1.f / (float)a.n;
-    int cur = -1;
+    int cur = -1, cur_job = -1;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1ull);
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(jt.counter, 1ull);
+            s_item = it;
+            s_job = it < jt.total_items ? find_job(jt, it) : 0;
+        }
         __syncthreads();
         const long long item = s_item;
-        if (item >= a.total_items) break;
-        const int ls = (int)(item / per_sector);
-        const long long rem = item - (long long)ls * per_sector;
-        const int shift = (int)(rem / a.chunks);
-        const long long chunk = rem - (long long)shift * a.chunks;
-        const int psec = a.sector_begin + ls;
-        if (a.sector_prec) {
-            const PackedSector *gps = reinterpret_cast<const PackedSector *>(a.packed + a.sectors_off) + psec;
-            if (a.sector_prec[gps->orig_index] != 1) {
+        if (item >= jt.total_items) break;
+        const int jb = s_job;
+        const Job &J = jt.jobs[jb];
+        const long long local = item - J.item_begin;
+        const long long per_sector = (long long)J.m * J.chunks;
+        const int ls = (int)(local / per_sector);
+        const long long rem = local - (long long)ls * per_sector;
+        const int shift = (int)(rem / J.chunks);
+        const long long chunk = rem - (long long)shift * J.chunks;
+        const int psec = J.sector_begin + ls;
+        if (J.sector_prec) {
+            /* mixed pass: items of sectors evaluated in FP64 belong to the other kernel */
+            const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
+            if (J.sector_prec[gps->orig_index] != 1) {
                 __syncthreads();
                 continue;
             }
         }
-        if (psec != cur) {
-            stage_sector_f(a.packed, a.sectors_off, a.termsf_off, psec, smem);
+        if (psec != cur || jb != cur_job) {
+            stage_sector_f(J.packed, J.sectors_off, J.termsf_off, psec, smem);
             __syncthreads();
             cur = psec;
+            cur_job = jb;
         }
-        const float lam = (float)a.lambda[sec.orig_index];
-        uint32_t rj[S], aj[S];
+        const Exps ex{J.eU0, J.eU1, J.eF0, J.eF1};
+        const uint32_t n = J.n;
+        const float invnf = 1.f / (float)n;
+        const float lam = (float)J.lambda[sec.orig_index];
+        uint32_t rj[S], aj[S], zs[S];
         float bj[S];
-        const long long i0 = chunk * (long long)blockDim.x * a.P + threadIdx.x;
+        const long long i0 = chunk * (long long)blockDim.x * jt.P + threadIdx.x;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            split_shift(a.shifts[6 * shift + j], a.n, aj[j], bj[j]);
-            rj[j] = (uint32_t)(((unsigned long long)i0 * a.z[j]) % a.n);
+            split_shift(J.shifts[6 * shift + j], n, aj[j], bj[j]);
+            rj[j] = (uint32_t)(((unsigned long long)i0 * J.z[j]) % n);
+            zs[j] = J.zstep[j];
         }
         float acc[2 * (MAXM + 1)], cmp[2 * (MAXM + 1)];
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
         uint32_t fails = 0;
-        for (int p = 0; p < a.P; ++p) {
+        for (int p = 0; p < jt.P; ++p) {
             const long long i = i0 + (long long)p * blockDim.x;
-            if (i < (long long)a.n) {
+            if (i < (long long)n) {
                 float x[S], y[S];
 #pragma unroll
-                for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], a.n, invnf, x[j], y[j]);
+                for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], n, invnf, x[j], y[j]);
                 cf val[MAXM + 1];
-                point_integrand_f<S, DEF, MAXM>(sec, SmemTabF{T}, 0, x, y, a.r, lam, ex, val, fails);
+                point_integrand_f<S, DEF, MAXM>(sec, SmemTabF{T}, 0, x, y, jt.r, lam, ex, val, fails);
 #pragma unroll
-                for (int n = 0; n <= MAXM; ++n) {
-                    two_sum_acc(acc[2 * n], cmp[2 * n], val[n].x);
-                    two_sum_acc(acc[2 * n + 1], cmp[2 * n + 1], val[n].y);
+                for (int m = 0; m <= MAXM; ++m) {
+                    two_sum_acc(acc[2 * m], cmp[2 * m], val[m].x);
+                    two_sum_acc(acc[2 * m + 1], cmp[2 * m + 1], val[m].y);
                 }
             }
 #pragma unroll
             for (int j = 0; j < S; ++j) {
-                const uint32_t v = rj[j] + a.zstep[j];
-                rj[j] = v >= a.n ? v - a.n : v;
+                const uint32_t v = rj[j] + zs[j];
+                rj[j] = v >= n ? v - n : v;
             }
         }
         /* warp: double-float shuffle tree; warps and items in FP64 */
@@ -1016,119 +1051,16 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel_f32(EvalArgs a) {
         __syncthreads();
         if (threadIdx.x < 32) {
             const int q = threadIdx.x;
-            if (q < a.n_slots * 2) {
+            if (q < J.n_slots * 2) {
                 double s2 = 0.0, c2 = 0.0;
                 if (q < 2 * (MAXM + 1))
                     for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
-                a.partials[item * a.n_slots * 2 + q] = s2 - c2;
+                J.partials[local * J.n_slots * 2 + q] = s2 - c2;
             }
             if (q == 0) {
                 uint32_t tf = 0;
                 for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
-                a.part_fails[item] = tf;
-            }
-        }
-        __syncthreads();
-    }
-}
-
-/* ------------------------------------------------------------------ K2 with tables in kernel parameters */
-struct ParamTabF {
-    const ParamGroup *g;
-    DEV float hi(int i) const { return g->terms[i].hi; }
-    DEV float lo(int i) const { return g->terms[i].lo; }
-    DEV uint64_t ex(int i) const { return *reinterpret_cast<const uint64_t *>(g->terms[i].e); }
-};
-
-/* Persistent blocks take items from an atomic counter, as in the shared-memory kernels; the tables are read
-   from the kernel parameter block (constant bank), so nothing is staged and a block may change sector at any
-   item. */
-template <int S, bool DEF, int MAXM>
-__global__ void __launch_bounds__(256) qmc_eval_kernel_f32p(EvalArgs a, const __grid_constant__ ParamGroup g) {
-    __shared__ long long s_item;
-    __shared__ double s_red[16][2 * (MAXM + 1)];
-    __shared__ uint32_t s_fail[16];
-    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
-    const long long per_sector = (long long)a.m * a.chunks;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const float invnf = 1.f / (float)a.n;
-    const ParamTabF tab{&g};
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(a.counter, 1ull);
-        __syncthreads();
-        const long long item = s_item;
-        if (item >= a.total_items) break;
-        const int ls = (int)(item / per_sector);
-        const long long rem = item - (long long)ls * per_sector;
-        const int shift = (int)(rem / a.chunks);
-        const long long chunk = rem - (long long)shift * a.chunks;
-        const ParamSector &sec = g.sec[ls];
-        if (a.sector_prec && a.sector_prec[sec.orig_index] != 1) {
-            __syncthreads();
-            continue;
-        }
-        const float lam = (float)a.lambda[sec.orig_index];
-        uint32_t rj[S], aj[S];
-        float bj[S];
-        const long long i0 = chunk * (long long)blockDim.x * a.P + threadIdx.x;
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            split_shift(a.shifts[6 * shift + j], a.n, aj[j], bj[j]);
-            rj[j] = (uint32_t)(((unsigned long long)i0 * a.z[j]) % a.n);
-        }
-        float acc[2 * (MAXM + 1)], cmp[2 * (MAXM + 1)];
-#pragma unroll
-        for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
-        uint32_t fails = 0;
-        for (int p = 0; p < a.P; ++p) {
-            const long long i = i0 + (long long)p * blockDim.x;
-            if (i < (long long)a.n) {
-                float x[S], y[S];
-#pragma unroll
-                for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], a.n, invnf, x[j], y[j]);
-                cf val[MAXM + 1];
-                point_integrand_f<S, DEF, MAXM>(sec, tab, sec.tbase, x, y, a.r, lam, ex, val, fails);
-#pragma unroll
-                for (int n = 0; n <= MAXM; ++n) {
-                    two_sum_acc(acc[2 * n], cmp[2 * n], val[n].x);
-                    two_sum_acc(acc[2 * n + 1], cmp[2 * n + 1], val[n].y);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                const uint32_t v = rj[j] + a.zstep[j];
-                rj[j] = v >= a.n ? v - a.n : v;
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 2 * (MAXM + 1); ++q) {
-            float s1 = acc[q], c1 = cmp[q];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const float so = __shfl_down_sync(0xffffffffu, s1, off);
-                const float co = __shfl_down_sync(0xffffffffu, c1, off);
-                two_sum_acc(s1, c1, so);
-                c1 += co;
-            }
-            if (lane == 0) s_red[warp][q] = (double)s1 + (double)c1;
-        }
-        uint32_t f = fails;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
-        if (lane == 0) s_fail[warp] = f;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const int q = threadIdx.x;
-            if (q < a.n_slots * 2) {
-                double s2 = 0.0, c2 = 0.0;
-                if (q < 2 * (MAXM + 1))
-                    for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
-                a.partials[item * a.n_slots * 2 + q] = s2 - c2;
-            }
-            if (q == 0) {
-                uint32_t tf = 0;
-                for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
-                a.part_fails[item] = tf;
+                J.part_fails[local] = tf;
             }
         }
         __syncthreads();
@@ -1244,11 +1176,11 @@ __global__ void __launch_bounds__(256) qmc_points_kernel(PointArgs a) {
 
 /* ------------------------------------------------------------------ dispatch */
 template <int S, bool DEF, int MAXM>
-static int launch_eval_t(const EvalArgs &a, int grid, int block, cudaStream_t st) {
+static int launch_eval_t(const JobTable &t, int grid, int block, cudaStream_t st) {
     auto k = qmc_eval_kernel<S, DEF, MAXM>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem_bytes) != cudaSuccess)
         return QMC_ERR_CUDA;
-    k<<<grid, block, a.smem_bytes, st>>>(a);
+    k<<<grid, block, t.smem_bytes, st>>>(t);
     return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
@@ -1260,11 +1192,11 @@ static int occupancy_t(int block, int smem, int *out) {
 }
 
 template <int S, bool DEF, int MAXM>
-static int launch_eval_f32_t(const EvalArgs &a, int grid, int block, cudaStream_t st) {
+static int launch_eval_f32_t(const JobTable &t, int grid, int block, cudaStream_t st) {
     auto k = qmc_eval_kernel_f32<S, DEF, MAXM>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem_bytes) != cudaSuccess)
         return QMC_ERR_CUDA;
-    k<<<grid, block, a.smem_bytes, st>>>(a);
+    k<<<grid, block, t.smem_bytes, st>>>(t);
     return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
@@ -1273,20 +1205,6 @@ static int occupancy_f32_t(int block, int smem, int *out) {
     auto k = qmc_eval_kernel_f32<S, DEF, MAXM>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return QMC_ERR_CUDA;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, block, smem) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
-}
-
-template <int S, bool DEF, int MAXM>
-static int launch_eval_param_t(const EvalArgs &a, const ParamGroup &g, int grid, int block, cudaStream_t st) {
-    qmc_eval_kernel_f32p<S, DEF, MAXM><<<grid, block, 0, st>>>(a, g);
-    return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
-}
-
-template <int S, bool DEF, int MAXM>
-static int occupancy_param_t(int block, int *out) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, qmc_eval_kernel_f32p<S, DEF, MAXM>, block, 0) ==
-                   cudaSuccess
-               ? QMC_OK
-               : QMC_ERR_CUDA;
 }
 
 template <int S, bool DEF, int MAXM>

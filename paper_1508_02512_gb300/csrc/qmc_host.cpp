@@ -13,9 +13,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <string>
 #include <vector>
@@ -572,10 +575,9 @@ const PackedSector *sectors_of(const void *packed) {
 struct Plan {
     int block, P;
     int64_t chunks;
-    int64_t items[QMC_N_CLASSES];
-    int64_t item_off[QMC_N_CLASSES];
+    int64_t items[QMC_N_CLASSES];     /* items of each sector class */
+    int64_t item_off[QMC_N_CLASSES];  /* first item of the class within the pass */
     int64_t total_items;
-    size_t partial_bytes, fail_bytes, counter_bytes, total_bytes;
 };
 
 int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
@@ -600,12 +602,6 @@ int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
         off += pl.items[c];
     }
     pl.total_items = off;
-    auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
-    pl.partial_bytes = up((size_t)pl.total_items * h->n_slots * 2 * sizeof(double));
-    pl.fail_bytes = up((size_t)pl.total_items * sizeof(uint32_t));
-    /* work counters: per class and precision, plus one per launch of the parameter-table FP32 kernel */
-    pl.counter_bytes = up((2 * QMC_N_CLASSES + QMC_MAX_GROUP_LAUNCHES) * sizeof(unsigned long long));
-    pl.total_bytes = pl.partial_bytes + pl.fail_bytes + pl.counter_bytes;
     return QMC_OK;
 }
 
@@ -689,185 +685,269 @@ int qmc_sector_desc_get(const void *packed, int32_t sector, qmc_sector_desc *out
     return QMC_ERR_ARG;
 }
 
-size_t qmc_scratch_bytes(const void *packed, const qmc_pass *pass) {
-    Plan pl;
-    if (make_plan(header_of(packed), pass, pl) != QMC_OK) return 0;
-    return pl.total_bytes;
-}
-
 }  // extern "C"
 
 namespace {
 
-/* Validates the arguments shared by the evaluation entry points and lays out the scratch buffer. */
-struct Scratch {
-    double *partials;
-    uint32_t *pfails;
-    unsigned long long *counters;
+int class_maxm(const PackedHeader *h, int c) { return h->class_maxm[c] == 0 ? 0 : (h->class_maxm[c] <= 2 ? 2 : 4); }
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+/* Scratch layout of a batch of passes: each pass owns a slice of per-item partials and sign-failure counts (its
+   items in (class, sector, shift, chunk) order); the evaluation launches share an array of work counters. */
+struct BatchLayout {
+    std::vector<Plan> plans;
+    std::vector<size_t> partial_off, fail_off;
+    size_t counters_off = 0;
+    int n_counters = 0;
+    size_t total = 0;
 };
 
-int check_pass(const PackedHeader *h, const void *packed_dev, const qmc_pass *pass, void *scratch_dev,
-               size_t scratch_bytes, Plan &pl, Scratch &sc) {
-    if (!h || !packed_dev || !pass || !scratch_dev) return QMC_ERR_ARG;
-    if (((uintptr_t)scratch_dev & 255) || ((uintptr_t)packed_dev & 15)) return QMC_ERR_ARG;
-    int rc = make_plan(h, pass, pl);
-    if (rc) return rc;
-    if (scratch_bytes < pl.total_bytes) return QMC_ERR_MEMORY;
-    unsigned char *scr = static_cast<unsigned char *>(scratch_dev);
-    sc.partials = reinterpret_cast<double *>(scr);
-    sc.pfails = reinterpret_cast<uint32_t *>(scr + pl.partial_bytes);
-    sc.counters = reinterpret_cast<unsigned long long *>(scr + pl.partial_bytes + pl.fail_bytes);
+int batch_layout(const qmc_batch_item *items, int n, BatchLayout &L) {
+    if (!items || n < 1) return QMC_ERR_ARG;
+    L.plans.resize(n);
+    L.partial_off.resize(n);
+    L.fail_off.resize(n);
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const PackedHeader *h = header_of(items[i].packed_host);
+        int rc = make_plan(h, &items[i].pass, L.plans[i]);
+        if (rc) return rc;
+        L.partial_off[i] = off;
+        off += up256((size_t)L.plans[i].total_items * h->n_slots * 2 * sizeof(double));
+        L.fail_off[i] = off;
+        off += up256((size_t)L.plans[i].total_items * sizeof(uint32_t));
+    }
+    L.n_counters = 4 * n + 4; /* at most one launch per (pass, class, precision) */
+    L.counters_off = off;
+    off += up256((size_t)L.n_counters * sizeof(unsigned long long));
+    L.total = off;
     return QMC_OK;
 }
 
-int class_maxm(const PackedHeader *h, int c) { return h->class_maxm[c] == 0 ? 0 : (h->class_maxm[c] <= 2 ? 2 : 4); }
-
-/* FP32 evaluation with the sector tables in the kernel's parameter block: the class's sectors are cut into
-   groups of at most QMC_PARAM_SECTORS sectors and QMC_PARAM_TERMS terms, one launch per group, each with its own
-   work counter and its slice of the class's item range (items of a sector are contiguous). */
-int launch_param_groups(const PackedHeader *h, const void *packed_host, int c, int maxm, const EvalArgs &base,
-                        const Plan &pl, const Scratch &sc, int sms, int &group_launches, void *stream) {
-    const unsigned char *img = static_cast<const unsigned char *>(packed_host);
-    const PackedSector *ps = reinterpret_cast<const PackedSector *>(img + h->sectors_off);
-    const PackedTermF *tf = reinterpret_cast<const PackedTermF *>(img + h->termsf_off);
-    int per_sm = 0;
-    int rc = qmc_eval_param_blocks_per_sm(h->dim, c == 1, maxm, pl.block, &per_sm);
-    if (rc) return rc;
-    if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
-    std::unique_ptr<ParamGroup> g(new ParamGroup());
-    const int64_t per_sector = (int64_t)base.m * base.chunks;
-    int s0 = h->class_begin[c];
-    while (s0 < h->class_end[c]) {
-        std::memset(g.get(), 0, sizeof(ParamGroup));
-        int ns = 0, nt = 0;
-        while (s0 + ns < h->class_end[c] && ns < QMC_PARAM_SECTORS && nt + ps[s0 + ns].n_terms <= QMC_PARAM_TERMS) {
-            const PackedSector &q = ps[s0 + ns];
-            ParamSector &d = g->sec[ns];
-            d.kind = q.kind;
-            d.sigma = q.sigma;
-            d.sing_mask = q.sing_mask;
-            d.M = q.M;
-            for (int j = 0; j < 6; ++j) {
-                d.A[j] = q.A[j];
-                d.B[j] = q.B[j];
-            }
-            d.nU = q.nU;
-            d.nF = q.nF;
-            d.nG = q.nG;
-            d.nH = q.nH;
-            d.tbase = nt;
-            d.orig_index = q.orig_index;
-            d.psec = s0 + ns;
-            d.Df = q.Df;
-            for (int j = 0; j < 8; ++j) d.gstart[j] = q.gstart[j];
-            for (int j = 0; j < 24; ++j) d.hstart[j] = q.hstart[j];
-            std::memcpy(&g->terms[nt], tf + q.term0, sizeof(PackedTermF) * q.n_terms);
-            nt += q.n_terms;
-            ++ns;
-        }
-        if (ns == 0) return QMC_ERR_UNSUPPORTED;
-        if (group_launches >= QMC_MAX_GROUP_LAUNCHES) return QMC_ERR_UNSUPPORTED;
-        g->n_sect = ns;
-        g->n_terms = nt;
-        EvalArgs a = base;
-        const int64_t first = (int64_t)(s0 - h->class_begin[c]) * per_sector;
-        a.sector_begin = s0;
-        a.n_sect = ns;
-        a.total_items = (int64_t)ns * per_sector;
-        a.partials = base.partials + first * h->n_slots * 2;
-        a.part_fails = base.part_fails + first;
-        a.counter = sc.counters + 2 * QMC_N_CLASSES + group_launches;
-        ++group_launches;
-        int64_t grid = (int64_t)sms * per_sm;
-        if (grid > a.total_items) grid = a.total_items;
-        rc = qmc_launch_eval_param(h->dim, c == 1, maxm, a, *g, (int)grid, pl.block, stream);
-        if (rc) return rc;
-        s0 += ns;
+int check_items(const qmc_batch_item *items, int n, bool need_eval_inputs, bool need_outputs) {
+    for (int i = 0; i < n; ++i) {
+        const qmc_batch_item &b = items[i];
+        if (!header_of(b.packed_host) || !b.packed_dev || ((uintptr_t)b.packed_dev & 15)) return QMC_ERR_ARG;
+        if (need_eval_inputs && (!b.shifts_dev || !b.lambda_dev)) return QMC_ERR_ARG;
+        if (need_outputs && (!b.sums_dev || !b.fails_dev)) return QMC_ERR_ARG;
     }
     return QMC_OK;
+}
+
+struct LaunchKey {
+    int dim, deform, maxm, prec, block, P, r;
+    bool operator<(const LaunchKey &o) const {
+        const int a[7] = {dim, deform, maxm, prec, block, P, r}, b[7] = {o.dim, o.deform, o.maxm, o.prec, o.block, o.P, o.r};
+        for (int k = 0; k < 7; ++k)
+            if (a[k] != b[k]) return a[k] < b[k];
+        return false;
+    }
+};
+
+/* Evaluation launches of a batch: every (pass, class, precision) becomes a job; jobs sharing a kernel
+   instantiation and launch shape go into one persistent launch (tables of up to QMC_MAX_JOBS jobs). */
+int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned char *scr, void *stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(scr + L.counters_off);
+    int rc = cuda_status(cudaMemsetAsync(counters, 0, (size_t)L.n_counters * sizeof(unsigned long long), st));
+    if (rc) return rc;
+    int sms = 0;
+    rc = qmc_device_sm_count(&sms);
+    if (rc) return rc;
+    std::map<LaunchKey, std::vector<Job>> groups;
+    std::map<LaunchKey, int> smem_need;
+    for (int i = 0; i < n; ++i) {
+        const qmc_batch_item &b = items[i];
+        const PackedHeader *h = header_of(b.packed_host);
+        const Plan &pl = L.plans[i];
+        const bool mixed = b.pass.precision == QMC_PREC_MIXED;
+        for (int c = 0; c < QMC_N_CLASSES; ++c) {
+            if (pl.items[c] == 0) continue;
+            for (int prec = 0; prec < 2; ++prec) {
+                if (!mixed && prec == 1) continue;
+                if (mixed && prec == 0 && !b.pass.sector_precision) continue;
+                Job J;
+                std::memset(&J, 0, sizeof(J));
+                J.packed = static_cast<const unsigned char *>(b.packed_dev);
+                J.sectors_off = h->sectors_off;
+                J.terms_off = h->terms_off;
+                J.termsf_off = h->termsf_off;
+                J.chunks = pl.chunks;
+                J.shifts = b.shifts_dev;
+                J.lambda = b.lambda_dev;
+                J.sector_prec = mixed ? b.pass.sector_precision : nullptr;
+                J.partials = reinterpret_cast<double *>(scr + L.partial_off[i]) + pl.item_off[c] * h->n_slots * 2;
+                J.part_fails = reinterpret_cast<uint32_t *>(scr + L.fail_off[i]) + pl.item_off[c];
+                J.n = (uint32_t)b.pass.lattice.n;
+                J.invn = 1.0 / (double)b.pass.lattice.n;
+                for (int j = 0; j < QMC_MAX_DIM; ++j) {
+                    J.z[j] = j < h->dim ? b.pass.lattice.z[j] : 0;
+                    J.zstep[j] = (uint32_t)(((uint64_t)pl.block * J.z[j]) % (uint64_t)b.pass.lattice.n);
+                }
+                J.sector_begin = h->class_begin[c];
+                J.n_sect = h->class_end[c] - h->class_begin[c];
+                J.m = b.pass.n_shifts;
+                J.n_slots = h->n_slots;
+                J.eU0 = h->eU0;
+                J.eU1 = h->eU1;
+                J.eF0 = h->eF0;
+                J.eF1 = h->eF1;
+                const LaunchKey key{h->dim, c, class_maxm(h, c), prec == 0 ? QMC_PREC_FP64 : QMC_PREC_MIXED, pl.block,
+                                    pl.P, b.pass.transform_r};
+                groups[key].push_back(J);
+                const int need = (int)(sizeof(PackedSector) + (size_t)h->max_terms * sizeof(PackedTerm));
+                smem_need[key] = std::max(smem_need[key], need);
+            }
+        }
+    }
+    int counter = 0;
+    std::unique_ptr<JobTable> jt(new JobTable());
+    for (auto &kv : groups) {
+        const LaunchKey &k = kv.first;
+        const std::vector<Job> &jobs = kv.second;
+        for (size_t b0 = 0; b0 < jobs.size(); b0 += QMC_MAX_JOBS) {
+            std::memset(jt.get(), 0, sizeof(JobTable));
+            const size_t nj = std::min(jobs.size() - b0, (size_t)QMC_MAX_JOBS);
+            int64_t total = 0;
+            for (size_t q = 0; q < nj; ++q) {
+                jt->jobs[q] = jobs[b0 + q];
+                jt->jobs[q].item_begin = total;
+                total += (int64_t)jt->jobs[q].n_sect * jt->jobs[q].m * jt->jobs[q].chunks;
+            }
+            jt->n_jobs = (int32_t)nj;
+            jt->r = k.r;
+            jt->P = k.P;
+            jt->want_prec = k.prec == QMC_PREC_FP64 ? 0 : 1;
+            jt->total_items = total;
+            if (counter >= L.n_counters) return QMC_ERR_UNSUPPORTED;
+            jt->counter = counters + counter++;
+            jt->smem_bytes = smem_need[k];
+            int per_sm = 0;
+            rc = qmc_eval_blocks_per_sm(k.dim, k.deform, k.maxm, k.prec, k.block, jt->smem_bytes, &per_sm);
+            if (rc) return rc;
+            if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
+            int64_t grid = (int64_t)sms * per_sm;
+            for (int i = 0; i < n; ++i)
+                if (items[i].pass.grid > 0) grid = std::min<int64_t>(grid, items[i].pass.grid);
+            if (grid > total) grid = total;
+            rc = qmc_launch_eval(k.dim, k.deform, k.maxm, k.prec, *jt, (int)grid, k.block, stream);
+            if (rc) return rc;
+        }
+    }
+    return QMC_OK;
+}
+
+/* Reductions of a batch: one warp per (pass, sector, shift) over that pair's item partials, in fixed order. */
+int run_reduce(const qmc_batch_item *items, int n, const BatchLayout &L, const unsigned char *scr, void *stream) {
+    std::unique_ptr<FinTable> ft(new FinTable());
+    std::memset(ft.get(), 0, sizeof(FinTable));
+    int64_t pairs = 0;
+    auto flush = [&]() -> int {
+        if (ft->n_jobs == 0) return QMC_OK;
+        ft->total_pairs = pairs;
+        const int rc = qmc_launch_finalize(*ft, stream);
+        std::memset(ft.get(), 0, sizeof(FinTable));
+        pairs = 0;
+        return rc;
+    };
+    for (int i = 0; i < n; ++i) {
+        const qmc_batch_item &b = items[i];
+        const PackedHeader *h = header_of(b.packed_host);
+        const Plan &pl = L.plans[i];
+        for (int c = 0; c < QMC_N_CLASSES; ++c) {
+            if (pl.items[c] == 0) continue;
+            if (ft->n_jobs == QMC_MAX_JOBS) {
+                const int rc = flush();
+                if (rc) return rc;
+            }
+            FinJob &J = ft->jobs[ft->n_jobs++];
+            J.packed = static_cast<const unsigned char *>(b.packed_dev);
+            J.sectors_off = h->sectors_off;
+            J.chunks = pl.chunks;
+            J.pair_begin = pairs;
+            J.partials = reinterpret_cast<const double *>(scr + L.partial_off[i]) + pl.item_off[c] * h->n_slots * 2;
+            J.part_fails = reinterpret_cast<const uint32_t *>(scr + L.fail_off[i]) + pl.item_off[c];
+            J.sums = b.sums_dev;
+            J.fails = b.fails_dev;
+            J.sector_begin = h->class_begin[c];
+            J.n_sect = h->class_end[c] - h->class_begin[c];
+            J.m = b.pass.n_shifts;
+            J.n_slots = h->n_slots;
+            pairs += (int64_t)J.n_sect * J.m;
+        }
+    }
+    return flush();
+}
+
+qmc_batch_item single_item(const void *packed_host, const void *packed_dev, const qmc_pass *pass,
+                           const double *shifts_dev, const double *lambda_dev, double *sums_dev, int64_t *fails_dev) {
+    qmc_batch_item b;
+    std::memset(&b, 0, sizeof(b));
+    b.packed_host = packed_host;
+    b.packed_dev = packed_dev;
+    if (pass) b.pass = *pass;
+    b.shifts_dev = shifts_dev;
+    b.lambda_dev = lambda_dev;
+    b.sums_dev = sums_dev;
+    b.fails_dev = fails_dev;
+    return b;
 }
 
 }  // namespace
 
 extern "C" {
 
+size_t qmc_batch_scratch_bytes(const qmc_batch_item *items, int32_t n) {
+    BatchLayout L;
+    try {
+        if (batch_layout(items, n, L) != QMC_OK) return 0;
+    } catch (...) {
+        return 0;
+    }
+    return L.total;
+}
+
+size_t qmc_scratch_bytes(const void *packed, const qmc_pass *pass) {
+    if (!pass) return 0;
+    const qmc_batch_item b = single_item(packed, nullptr, pass, nullptr, nullptr, nullptr, nullptr);
+    return qmc_batch_scratch_bytes(&b, 1);
+}
+
+int qmc_eval_batch(const qmc_batch_item *items, int32_t n, void *scratch_dev, size_t scratch_bytes, void *stream) {
+    try {
+        BatchLayout L;
+        int rc = batch_layout(items, n, L);
+        if (rc) return rc;
+        rc = check_items(items, n, true, true);
+        if (rc) return rc;
+        if (!scratch_dev || ((uintptr_t)scratch_dev & 255)) return QMC_ERR_ARG;
+        if (scratch_bytes < L.total) return QMC_ERR_MEMORY;
+        unsigned char *scr = static_cast<unsigned char *>(scratch_dev);
+        rc = run_eval(items, n, L, scr, stream);
+        if (rc) return rc;
+        return run_reduce(items, n, L, scr, stream);
+    } catch (const std::bad_alloc &) {
+        return QMC_ERR_MEMORY;
+    }
+}
+
 int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc_pass *pass,
                       const double *shifts_dev, const double *lambda_dev, void *scratch_dev, size_t scratch_bytes,
                       void *stream) {
-    const PackedHeader *h = header_of(packed_host);
-    if (!shifts_dev || !lambda_dev) return QMC_ERR_ARG;
-    Plan pl;
-    Scratch sc;
-    int rc = check_pass(h, packed_dev, pass, scratch_dev, scratch_bytes, pl, sc);
-    if (rc) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-    rc = cuda_status(cudaMemsetAsync(sc.counters, 0,
-                                     (2 * QMC_N_CLASSES + QMC_MAX_GROUP_LAUNCHES) * sizeof(unsigned long long), st));
-    if (rc) return rc;
-    int sms = 0;
-    rc = qmc_device_sm_count(&sms);
-    if (rc) return rc;
-    const size_t smem = sizeof(PackedSector) + (size_t)h->max_terms * sizeof(PackedTerm);
-    int group_launches = 0;
-    /* FP64 pass: one kernel per class.  Mixed pass: the FP32 kernel takes the sectors marked 1 in
-       pass->sector_precision (all when it is null), the FP64 kernel the others; both share the item space. */
-    const bool mixed = pass->precision == QMC_PREC_MIXED;
-    for (int c = 0; c < QMC_N_CLASSES; ++c) {
-        if (pl.items[c] == 0) continue;
-        const int maxm = class_maxm(h, c);
-        for (int prec = 0; prec < 2; ++prec) {
-            const int kprec = prec == 0 ? QMC_PREC_FP64 : QMC_PREC_MIXED;
-            if (!mixed && prec == 1) continue;
-            if (mixed && prec == 0 && !pass->sector_precision) continue;
-            EvalArgs a;
-            std::memset(&a, 0, sizeof(a));
-            a.packed = static_cast<const unsigned char *>(packed_dev);
-            a.sectors_off = h->sectors_off;
-            a.terms_off = h->terms_off;
-            a.termsf_off = h->termsf_off;
-            a.sector_begin = h->class_begin[c];
-            a.n_sect = h->class_end[c] - h->class_begin[c];
-            a.m = pass->n_shifts;
-            a.r = pass->transform_r;
-            a.P = pl.P;
-            a.n_slots = h->n_slots;
-            a.n = (uint32_t)pass->lattice.n;
-            for (int j = 0; j < QMC_MAX_DIM; ++j) {
-                a.z[j] = j < h->dim ? pass->lattice.z[j] : 0;
-                a.zstep[j] = (uint32_t)(((uint64_t)pl.block * a.z[j]) % (uint64_t)pass->lattice.n);
-            }
-            a.invn = 1.0 / (double)pass->lattice.n;
-            a.chunks = pl.chunks;
-            a.total_items = pl.items[c];
-            a.shifts = shifts_dev;
-            a.lambda = lambda_dev;
-            a.partials = sc.partials + pl.item_off[c] * h->n_slots * 2;
-            a.part_fails = sc.pfails + pl.item_off[c];
-            a.counter = sc.counters + 2 * c + prec;
-            a.eU0 = h->eU0;
-            a.eU1 = h->eU1;
-            a.eF0 = h->eF0;
-            a.eF1 = h->eF1;
-            a.smem_bytes = (int)smem;
-            a.sector_prec = mixed ? pass->sector_precision : nullptr;
-            a.want_prec = prec;
-            if (prec == 1 && h->max_terms <= QMC_PARAM_TERMS) {
-                /* FP32 with the tables in kernel parameters: groups of consecutive sectors per launch */
-                rc = launch_param_groups(h, packed_host, c, maxm, a, pl, sc, sms, group_launches, stream);
-                if (rc) return rc;
-                continue;
-            }
-            int per_sm = 0;
-            rc = qmc_eval_blocks_per_sm(h->dim, c == 1, maxm, kprec, pl.block, (int)smem, &per_sm);
-            if (rc) return rc;
-            if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
-            int64_t grid = pass->grid > 0 ? pass->grid : (int64_t)sms * per_sm;
-            if (grid > pl.items[c]) grid = pl.items[c];
-            rc = qmc_launch_eval(h->dim, c == 1, maxm, kprec, a, (int)grid, pl.block, stream);
-            if (rc) return rc;
-        }
+    const qmc_batch_item b = single_item(packed_host, packed_dev, pass, shifts_dev, lambda_dev, nullptr, nullptr);
+    try {
+        BatchLayout L;
+        int rc = batch_layout(&b, 1, L);
+        if (rc) return rc;
+        rc = check_items(&b, 1, true, false);
+        if (rc) return rc;
+        if (!scratch_dev || ((uintptr_t)scratch_dev & 255)) return QMC_ERR_ARG;
+        if (scratch_bytes < L.total) return QMC_ERR_MEMORY;
+        return run_eval(&b, 1, L, static_cast<unsigned char *>(scratch_dev), stream);
+    } catch (const std::bad_alloc &) {
+        return QMC_ERR_MEMORY;
     }
-    return QMC_OK;
 }
 
 int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
@@ -910,40 +990,26 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
 
 int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const void *scratch_dev,
                         size_t scratch_bytes, double *sums_dev, int64_t *fails_dev, void *stream) {
-    const PackedHeader *h = header_of(packed_host);
-    if (!sums_dev || !fails_dev) return QMC_ERR_ARG;
-    Plan pl;
-    Scratch sc;
-    int rc = check_pass(h, packed_dev, pass, const_cast<void *>(scratch_dev), scratch_bytes, pl, sc);
-    if (rc) return rc;
-    for (int c = 0; c < QMC_N_CLASSES; ++c) {
-        if (pl.items[c] == 0) continue;
-        FinalizeArgs f;
-        f.packed = static_cast<const unsigned char *>(packed_dev);
-        f.sectors_off = h->sectors_off;
-        f.sector_begin = h->class_begin[c];
-        f.n_sect = h->class_end[c] - h->class_begin[c];
-        f.m = pass->n_shifts;
-        f.n_slots = h->n_slots;
-        f.chunks = pl.chunks;
-        f.partials = sc.partials + pl.item_off[c] * h->n_slots * 2;
-        f.part_fails = sc.pfails + pl.item_off[c];
-        f.sums = sums_dev;
-        f.fails = fails_dev;
-        rc = qmc_launch_finalize(f, stream);
+    const qmc_batch_item b = single_item(packed_host, packed_dev, pass, nullptr, nullptr, sums_dev, fails_dev);
+    try {
+        BatchLayout L;
+        int rc = batch_layout(&b, 1, L);
         if (rc) return rc;
+        rc = check_items(&b, 1, false, true);
+        if (rc) return rc;
+        if (!scratch_dev || ((uintptr_t)scratch_dev & 255)) return QMC_ERR_ARG;
+        if (scratch_bytes < L.total) return QMC_ERR_MEMORY;
+        return run_reduce(&b, 1, L, static_cast<const unsigned char *>(scratch_dev), stream);
+    } catch (const std::bad_alloc &) {
+        return QMC_ERR_MEMORY;
     }
-    return QMC_OK;
 }
 
 int qmc_eval_sums(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shifts_dev,
                   const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, double *sums_dev,
                   int64_t *fails_dev, void *stream) {
-    if (!sums_dev || !fails_dev) return QMC_ERR_ARG;
-    int rc = qmc_eval_partials(packed_host, packed_dev, pass, shifts_dev, lambda_dev, scratch_dev, scratch_bytes,
-                               stream);
-    if (rc) return rc;
-    return qmc_reduce_partials(packed_host, packed_dev, pass, scratch_dev, scratch_bytes, sums_dev, fails_dev, stream);
+    const qmc_batch_item b = single_item(packed_host, packed_dev, pass, shifts_dev, lambda_dev, sums_dev, fails_dev);
+    return qmc_eval_batch(&b, 1, scratch_dev, scratch_bytes, stream);
 }
 
 int qmc_eval_points(const void *packed_host, const void *packed_dev, int32_t sector, const qmc_pass *pass,
@@ -1091,6 +1157,8 @@ struct Integral {
     qmc_info info;
 };
 
+struct Serving;
+
 struct qmc_ctx {
     int device = 0;
     size_t budget = 0, used = 0;
@@ -1100,6 +1168,7 @@ struct qmc_ctx {
     DevBuf scratch, sums, fails, shifts, lambda, hpacked, prec, probe;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::mutex mu;
+    Serving *serving = nullptr;
 };
 
 namespace {
@@ -1153,8 +1222,11 @@ int qmc_create(qmc_ctx **out, int32_t device, size_t mem_budget, void *stream) {
     return QMC_OK;
 }
 
+void serving_shutdown(qmc_ctx *c);
+
 int qmc_destroy(qmc_ctx *c) {
     if (!c) return QMC_ERR_ARG;
+    serving_shutdown(c);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (auto &kv : c->integrals) dev_release(c, kv.second.dpacked);
@@ -1417,6 +1489,461 @@ int qmc_eval_sums_host(qmc_ctx *c, const void *packed_host, const qmc_pass *pass
     if (!rc) rc = cuda_status(cudaMemcpyAsync(fails_host, c->fails.p, fails_bytes, cudaMemcpyDeviceToHost, st));
     if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
     return rc;
+}
+
+}  // extern "C"
+
+/* ====================================================================== serving: continuous batching */
+/*
+ * Requests (an integral at a kinematic point, with options) are queued by qmc_submit.  A scheduler thread admits
+ * them while the context's device-memory budget allows their tables, shift sums and first-pass scratch, and then
+ * runs rounds: in each round every active request contributes the pass at its current lattice size to one
+ * qmc_eval_batch (persistent launches shared by all requests of the same sector class), the per-shift sums come
+ * back, and each request independently halves lambda of failing sectors, checks its convergence and either
+ * finishes, retries the same size, or moves to the next lattice size.  Requests that arrive while others are
+ * running join at the next round.  A request's passes are computed exactly as they would be alone, so its
+ * result does not depend on what else is in the batch.
+ */
+namespace {
+
+enum { REQ_QUEUED = 0, REQ_ACTIVE = 1, REQ_DONE = 2 };
+
+struct Request {
+    int64_t id = 0;
+    int32_t integral_id = 0;
+    std::vector<unsigned char> table;
+    std::vector<double> inv;
+    int32_t omin = 0, omax = 0;
+    qmc_options opt;
+    std::vector<double> shifts;
+    std::vector<qmc_lattice> ladder;
+    std::vector<unsigned char> packed;
+    qmc_info info;
+    DevBuf dpacked, dshifts, dlambda, dsums, dfails, dprec, dprobe;
+    size_t rung = 0;
+    std::vector<double> lam;
+    std::vector<int> halv;
+    std::vector<int32_t> prec;
+    bool probe_due = false;
+    std::vector<double> sums;
+    std::vector<int64_t> fails;
+    qmc_result res;
+    std::chrono::steady_clock::time_point t_submit, t_admit;
+    bool cancelled = false;
+    int state = REQ_QUEUED;
+};
+
+}  // namespace
+
+struct Serving {
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> active;
+    std::map<int64_t, std::shared_ptr<Request>> all;
+    int64_t next_id = 1;
+    qmc_serving_stats stats;
+};
+
+namespace {
+
+void release_request(qmc_ctx *c, Request &r) {
+    for (DevBuf *b : {&r.dpacked, &r.dshifts, &r.dlambda, &r.dsums, &r.dfails, &r.dprec, &r.dprobe}) dev_release(c, *b);
+}
+
+void finish(Serving *S, qmc_ctx *c, Request &r, int status) {
+    release_request(c, r);
+    if (status != QMC_OK && r.rung < r.ladder.size() && r.res.n_final == 0) r.res.n_final = r.ladder[r.rung].n;
+    r.res.status = status;
+    r.res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
+    r.res.queued_seconds = std::chrono::duration<double>(r.t_admit - r.t_submit).count();
+    std::lock_guard<std::mutex> g(S->mu);
+    r.state = REQ_DONE;
+    S->stats.completed += 1;
+}
+
+/* host preparation and device buffers of a newly admitted request (called with the context mutex held) */
+int admit(qmc_ctx *c, Request &r) {
+    int rc = qmc_prepare(r.table.data(), r.table.size(), r.inv.data(), (int32_t)r.inv.size(), r.omin, r.omax, nullptr,
+                         0, &r.info);
+    if (rc) return rc;
+    r.packed.assign((size_t)r.info.packed_bytes, 0);
+    rc = qmc_prepare(r.table.data(), r.table.size(), r.inv.data(), (int32_t)r.inv.size(), r.omin, r.omax,
+                     r.packed.data(), r.packed.size(), &r.info);
+    if (rc) return rc;
+    const PackedHeader *h = header_of(r.packed.data());
+    const int ns = h->n_sectors, m = (int)(r.shifts.size() / 6);
+    const size_t sums_bytes = (size_t)ns * m * h->n_slots * 2 * sizeof(double);
+    rc = dev_reserve(c, r.dpacked, r.packed.size());
+    if (!rc) rc = dev_reserve(c, r.dshifts, r.shifts.size() * sizeof(double));
+    if (!rc) rc = dev_reserve(c, r.dlambda, ns * sizeof(double));
+    if (!rc) rc = dev_reserve(c, r.dsums, sums_bytes);
+    if (!rc) rc = dev_reserve(c, r.dfails, (size_t)ns * m * sizeof(int64_t));
+    if (!rc) rc = dev_reserve(c, r.dprec, ns * sizeof(int32_t));
+    if (!rc) rc = dev_reserve(c, r.dprobe, (size_t)ns * h->n_slots * 4 * sizeof(double));
+    if (rc) return rc;
+    rc = cuda_status(cudaMemcpyAsync(r.dpacked.p, r.packed.data(), r.packed.size(), cudaMemcpyHostToDevice, c->stream));
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(r.dshifts.p, r.shifts.data(), r.shifts.size() * sizeof(double),
+                                         cudaMemcpyHostToDevice, c->stream));
+    r.lam.assign(ns, r.opt.lambda > 0 ? r.opt.lambda : 0.5);
+    r.halv.assign(ns, 0);
+    r.prec.assign(ns, 1);
+    r.probe_due = r.opt.precision == QMC_PREC_MIXED;
+    r.sums.assign(sums_bytes / sizeof(double), 0.0);
+    r.fails.assign((size_t)ns * m, 0);
+    r.res.order_min = h->order_min;
+    r.res.n_orders = h->order_max - h->order_min + 1;
+    return rc;
+}
+
+qmc_pass pass_of(const Request &r) {
+    qmc_pass p;
+    std::memset(&p, 0, sizeof(p));
+    p.lattice = r.ladder[r.rung];
+    p.n_shifts = (int32_t)(r.shifts.size() / 6);
+    p.transform_r = r.opt.transform_r > 0 ? r.opt.transform_r : 3;
+    p.precision = r.opt.precision;
+    p.block = r.opt.block;
+    p.points_per_thread = r.opt.points_per_thread;
+    p.sector_precision = r.opt.precision == QMC_PREC_MIXED ? (const int32_t *)r.dprec.p : nullptr;
+    return p;
+}
+
+/* FP32 budget check of a mixed-precision request (as in qmc_integrate) */
+int probe(qmc_ctx *c, Request &r) {
+    const PackedHeader *h = header_of(r.packed.data());
+    const int ns = h->n_sectors;
+    qmc_pass p = pass_of(r);
+    const int64_t nsamp = r.opt.probe_samples > 0 ? r.opt.probe_samples : 4096;
+    const double budget = (r.opt.fp32_budget > 0 ? r.opt.fp32_budget : 0.1) * r.opt.rel_tol;
+    std::vector<double> pr((size_t)ns * h->n_slots * 4);
+    int rc = cuda_status(cudaMemcpyAsync(r.dlambda.p, r.lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
+                                         c->stream));
+    if (!rc)
+        rc = qmc_probe_precision(r.packed.data(), r.dpacked.p, &p, (const double *)r.dshifts.p,
+                                 (const double *)r.dlambda.p, nsamp, (double *)r.dprobe.p, c->stream);
+    if (!rc)
+        rc = cuda_status(cudaMemcpyAsync(pr.data(), r.dprobe.p, pr.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+    if (rc) return rc;
+    r.res.fp64_reruns = 0;
+    for (int s2 = 0; s2 < ns; ++s2) {
+        bool bad = false;
+        for (int o = 0; o < h->n_slots; ++o) {
+            const double *v = &pr[((size_t)s2 * h->n_slots + o) * 4];
+            if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
+        }
+        r.prec[s2] = bad ? 0 : 1;
+        r.res.fp64_reruns += bad;
+    }
+    r.probe_due = false;
+    return cuda_status(cudaMemcpyAsync(r.dprec.p, r.prec.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                       c->stream));
+}
+
+/* after a pass: lambda halving, combination, convergence; returns true when the request is finished */
+bool advance(Serving *S, qmc_ctx *c, Request &r) {
+    const PackedHeader *h = header_of(r.packed.data());
+    const int ns = h->n_sectors, m = (int)(r.shifts.size() / 6);
+    const int max_h = r.opt.max_halvings > 0 ? r.opt.max_halvings : 6;
+    bool again = false;
+    for (int s2 = 0; s2 < ns; ++s2) {
+        int64_t f = 0;
+        for (int k = 0; k < m; ++k) f += r.fails[(size_t)s2 * m + k];
+        if (f > 0) {
+            r.res.sign_failures += (int32_t)std::min<int64_t>(f, INT32_MAX);
+            if (r.halv[s2] >= max_h) {
+                finish(S, c, r, QMC_ERR_DEFORMATION);
+                return true;
+            }
+            r.lam[s2] *= 0.5;
+            r.halv[s2] += 1;
+            r.res.lambda_halvings += 1;
+            again = true;
+        }
+    }
+    if (again) {
+        r.probe_due = r.opt.precision == QMC_PREC_MIXED;
+        return false;
+    }
+    const qmc_pass p = pass_of(r);
+    const int nord = h->order_max - h->order_min + 1;
+    std::vector<double> Q((size_t)m * nord * 2), mean(nord * 2), err(nord * 2);
+    qmc_combine(r.packed.data(), &p, r.sums.data(), Q.data(), mean.data(), err.data());
+    r.res.n_final = p.lattice.n;
+    for (int o = 0; o < nord && o < QMC_MAX_ORDERS; ++o) {
+        r.res.value[o][0] = mean[2 * o];
+        r.res.value[o][1] = mean[2 * o + 1];
+        r.res.error[o][0] = err[2 * o];
+        r.res.error[o][1] = err[2 * o + 1];
+    }
+    double vmax = 0.0;
+    for (int o = 0; o < nord; ++o) vmax = std::max(vmax, std::hypot(mean[2 * o], mean[2 * o + 1]));
+    bool ok = true;
+    for (int o = 0; o < nord; ++o) {
+        const double e = std::hypot(err[2 * o], err[2 * o + 1]);
+        const double v = std::hypot(mean[2 * o], mean[2 * o + 1]);
+        ok &= e <= std::max(r.opt.rel_tol * std::max(v, 1e-6 * vmax), r.opt.abs_tol);
+    }
+    if (ok) {
+        finish(S, c, r, QMC_OK);
+        return true;
+    }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
+    if (r.opt.max_seconds > 0 && el > r.opt.max_seconds) {
+        finish(S, c, r, QMC_ERR_TIMEOUT);
+        return true;
+    }
+    ++r.rung;
+    if (r.rung >= r.ladder.size() || (r.opt.max_n > 0 && r.ladder[r.rung].n > r.opt.max_n)) {
+        finish(S, c, r, QMC_ERR_NOT_CONVERGED);
+        return true;
+    }
+    return false;
+}
+
+void serve_loop(qmc_ctx *c) {
+    Serving *S = c->serving;
+    cudaSetDevice(c->device);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> fresh, cancelled;
+        /* lock order: the context mutex is never taken while the serving mutex is held */
+        size_t in_use;
+        {
+            std::lock_guard<std::mutex> g(c->mu);
+            in_use = c->used;
+        }
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
+            if (S->stop) return;
+            /* cancelled requests leave at the round boundary (finished below, outside this lock) */
+            for (auto it = S->active.begin(); it != S->active.end();) {
+                if ((*it)->cancelled) {
+                    cancelled.push_back(*it);
+                    it = S->active.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            /* admission: requests are taken in arrival order while the budget keeps room for their tables and
+               sums plus a first-pass share of scratch; at least one request always runs */
+            while (!S->queue.empty()) {
+                auto r = S->queue.front();
+                if (r->cancelled) {
+                    S->queue.pop_front();
+                    r->state = REQ_DONE;
+                    r->res.status = QMC_ERR_CANCELLED;
+                    S->stats.completed += 1;
+                    continue;
+                }
+                const size_t est = 2 * r->table.size() + ((size_t)8 << 20);
+                if (!S->active.empty() && in_use + est > c->budget) break;
+                S->queue.pop_front();
+                fresh.push_back(r);
+                in_use += est;
+                if (S->active.size() + fresh.size() >= QMC_MAX_JOBS / 4) break;
+            }
+        }
+        std::lock_guard<std::mutex> g(c->mu);
+        for (auto &r : cancelled) finish(S, c, *r, QMC_ERR_CANCELLED);
+        for (auto &r : fresh) {
+            r->t_admit = std::chrono::steady_clock::now();
+            int rc = admit(c, *r);
+            if (!rc && r->probe_due) rc = probe(c, *r);
+            if (rc) {
+                finish(S, c, *r, rc);
+                continue;
+            }
+            std::lock_guard<std::mutex> g2(S->mu);
+            r->state = REQ_ACTIVE;
+            S->active.push_back(r);
+            S->stats.peak_active = std::max<int64_t>(S->stats.peak_active, (int64_t)S->active.size());
+        }
+        std::vector<std::shared_ptr<Request>> batch;
+        {
+            std::lock_guard<std::mutex> g2(S->mu);
+            batch = S->active;
+        }
+        if (batch.empty()) continue;
+        /* this round: one pass per active request, in shared launches */
+        int rc = QMC_OK;
+        for (auto &r : batch) {
+            if (r->probe_due) rc = probe(c, *r);
+            if (rc) break;
+            rc = cuda_status(cudaMemcpyAsync(r->dlambda.p, r->lam.data(), r->lam.size() * sizeof(double),
+                                             cudaMemcpyHostToDevice, c->stream));
+            if (rc) break;
+        }
+        std::vector<qmc_batch_item> items(batch.size());
+        for (size_t i = 0; i < batch.size() && !rc; ++i) {
+            Request &r = *batch[i];
+            qmc_batch_item &b = items[i];
+            std::memset(&b, 0, sizeof(b));
+            b.packed_host = r.packed.data();
+            b.packed_dev = r.dpacked.p;
+            b.pass = pass_of(r);
+            b.shifts_dev = (const double *)r.dshifts.p;
+            b.lambda_dev = (const double *)r.dlambda.p;
+            b.sums_dev = (double *)r.dsums.p;
+            b.fails_dev = (int64_t *)r.dfails.p;
+        }
+        size_t need = rc ? 0 : qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
+        if (!rc && !need) rc = QMC_ERR_ARG;
+        /* the round shrinks (later requests wait) when its scratch would not fit the budget */
+        while (!rc && items.size() > 1 && c->used - c->scratch.bytes + ((need + 4095) & ~size_t(4095)) > c->budget) {
+            items.pop_back();
+            batch.pop_back();
+            need = qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
+        }
+        if (!rc) rc = dev_reserve(c, c->scratch, need);
+        if (!rc) rc = qmc_eval_batch(items.data(), (int32_t)items.size(), c->scratch.p, c->scratch.bytes, c->stream);
+        for (size_t i = 0; i < batch.size() && !rc; ++i) {
+            Request &r = *batch[i];
+            rc = cuda_status(cudaMemcpyAsync(r.sums.data(), r.dsums.p, r.sums.size() * sizeof(double),
+                                             cudaMemcpyDeviceToHost, c->stream));
+            if (!rc)
+                rc = cuda_status(cudaMemcpyAsync(r.fails.data(), r.dfails.p, r.fails.size() * sizeof(int64_t),
+                                                 cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+        {
+            std::lock_guard<std::mutex> g2(S->mu);
+            S->stats.rounds += 1;
+            S->stats.batched_passes += (int64_t)batch.size();
+        }
+        std::vector<std::shared_ptr<Request>> done;
+        for (auto &rp : batch) {
+            Request &r = *rp;
+            if (rc) {
+                finish(S, c, r, rc);
+                done.push_back(rp);
+                continue;
+            }
+            r.res.passes += 1;
+            r.res.evals += (int64_t)r.info.n_sectors * (int64_t)(r.shifts.size() / 6) * r.ladder[r.rung].n;
+            if (advance(S, c, r)) done.push_back(rp);
+        }
+        std::lock_guard<std::mutex> g2(S->mu);
+        for (auto &d : done) S->active.erase(std::remove(S->active.begin(), S->active.end(), d), S->active.end());
+    }
+}
+
+}  // namespace
+
+void serving_shutdown(qmc_ctx *c) {
+    if (!c->serving) return;
+    {
+        std::lock_guard<std::mutex> g(c->serving->mu);
+        c->serving->stop = true;
+    }
+    c->serving->cv.notify_all();
+    if (c->serving->th.joinable()) c->serving->th.join();
+    for (auto &kv : c->serving->all) release_request(c, *kv.second);
+    delete c->serving;
+    c->serving = nullptr;
+}
+
+extern "C" {
+
+int qmc_submit(qmc_ctx *c, int32_t integral_id, const double *invariants, int32_t n_invariants, int32_t order_min,
+               int32_t order_max, const qmc_options *opt, int64_t *request_id) {
+    if (!c || !opt || !request_id || (n_invariants > 0 && !invariants)) return QMC_ERR_ARG;
+    auto r = std::make_shared<Request>();
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        auto it = c->integrals.find(integral_id);
+        if (it == c->integrals.end()) return QMC_ERR_NOT_FOUND;
+        r->table = it->second.table;
+    }
+    r->integral_id = integral_id;
+    r->inv.assign(invariants, invariants + n_invariants);
+    r->omin = order_min;
+    r->omax = order_max;
+    r->opt = *opt;
+    std::memset(&r->res, 0, sizeof(r->res));
+    const int m = opt->n_shifts > 0 ? opt->n_shifts : 16;
+    if (m < 2 || m > 4096 || opt->rel_tol < 0) return QMC_ERR_ARG;
+    if (opt->shifts) r->shifts.assign(opt->shifts, opt->shifts + (size_t)m * 6);
+    else splitmix_shifts(opt->seed, m, r->shifts);
+    if (opt->n_lattices > 0) {
+        if (!opt->lattices) return QMC_ERR_ARG;
+        r->ladder.assign(opt->lattices, opt->lattices + opt->n_lattices);
+    } else {
+        for (int i = std::max(0, opt->ladder_start); i < QMC_BUILTIN_LATTICES; ++i) {
+            qmc_lattice L;
+            L.n = qmc_builtin_lattice[i].n;
+            for (int j = 0; j < QMC_MAX_DIM; ++j) L.z[j] = qmc_builtin_lattice[i].z[j];
+            r->ladder.push_back(L);
+        }
+    }
+    if (r->ladder.empty()) return QMC_ERR_ARG;
+    r->t_submit = std::chrono::steady_clock::now();
+    r->t_admit = r->t_submit;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        if (!c->serving) {
+            c->serving = new Serving();
+            std::memset(&c->serving->stats, 0, sizeof(qmc_serving_stats));
+            c->serving->th = std::thread(serve_loop, c);
+        }
+    }
+    Serving *S = c->serving;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        r->id = S->next_id++;
+        S->queue.push_back(r);
+        S->all[r->id] = r;
+        S->stats.submitted += 1;
+    }
+    S->cv.notify_all();
+    *request_id = r->id;
+    return QMC_OK;
+}
+
+int qmc_poll(qmc_ctx *c, int64_t request_id, qmc_result *out) {
+    if (!c || !out) return QMC_ERR_ARG;
+    if (!c->serving) return QMC_ERR_NOT_FOUND;
+    Serving *S = c->serving;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(request_id);
+    if (it == S->all.end()) return QMC_ERR_NOT_FOUND;
+    if (it->second->state != REQ_DONE) return QMC_PENDING;
+    *out = it->second->res;
+    return out->status;
+}
+
+int qmc_cancel(qmc_ctx *c, int64_t request_id) {
+    if (!c || !c->serving) return QMC_ERR_NOT_FOUND;
+    Serving *S = c->serving;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(request_id);
+    if (it == S->all.end()) return QMC_ERR_NOT_FOUND;
+    it->second->cancelled = true;
+    S->cv.notify_all();
+    return QMC_OK;
+}
+
+int qmc_serving_stats_get(qmc_ctx *c, qmc_serving_stats *out) {
+    if (!c || !out) return QMC_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    if (!c->serving) return QMC_OK;
+    Serving *S = c->serving;
+    int64_t used;
+    {
+        std::lock_guard<std::mutex> g(c->mu);
+        used = (int64_t)c->used;
+    }
+    std::lock_guard<std::mutex> g(S->mu);
+    *out = S->stats;
+    out->queued = (int64_t)S->queue.size();
+    out->active = (int64_t)S->active.size();
+    out->device_bytes = used;
+    return QMC_OK;
 }
 
 }  // extern "C"

@@ -74,58 +74,60 @@ static_assert(sizeof(PackedTermF) == 16, "FP32 term must be 16 bytes");
 static_assert(sizeof(PackedSector) % 16 == 0, "sector record must be 16-byte aligned");
 static_assert(sizeof(PackedHeader) % 16 == 0, "header must be 16-byte aligned");
 
-/* Per-launch arguments of the evaluation kernels (passed by value). */
-struct EvalArgs {
+/* One evaluation job: one pass of one prepared integral over one sector class (a contiguous range of its packed
+   sectors), every shift and every lattice point.  An evaluation launch covers a table of jobs that share the
+   kernel instantiation (sector dimension, deformation, series length, precision): a single integral's pass, or
+   the passes of many requests at once (continuous batching).  Items of a job are numbered (sector, shift, chunk),
+   chunk = blockDim * P consecutive lattice indices; item_begin places them in the launch's item space. */
+struct Job {
     const unsigned char *packed;  /* device image */
-    int64_t sectors_off, terms_off;
-    int32_t sector_begin;         /* first packed sector of the class */
-    int32_t n_sect;               /* sectors in the class */
-    int32_t m;                    /* shifts */
-    int32_t r;                    /* transform order */
-    int32_t P;                    /* points per thread */
-    int32_t n_slots;              /* partial/sum stride */
+    int64_t sectors_off, terms_off, termsf_off;
+    int64_t chunks;               /* chunks per (sector, shift) */
+    int64_t item_begin;           /* first item of this job in the launch */
+    const double *shifts;         /* m x 6 */
+    const double *lambda;         /* per sector, table order */
+    const int32_t *sector_prec;   /* mixed passes: per sector (table order), 1 = FP32; null = all of want_prec */
+    double *partials;             /* this job's items x n_slots x 2 */
+    uint32_t *part_fails;         /* this job's items */
+    double invn;
     uint32_t n;                   /* lattice size */
     uint32_t z[QMC_MAX_DIM];
     uint32_t zstep[QMC_MAX_DIM];  /* (blockDim * z_j) mod n */
-    double invn;
-    int64_t chunks;               /* chunks per (sector, shift) */
-    int64_t total_items;          /* n_sect * m * chunks */
-    const double *shifts;         /* m x 6 */
-    const double *lambda;         /* per sector, table order */
-    double *partials;             /* total_items x n_slots x 2 */
-    uint32_t *part_fails;         /* total_items */
-    unsigned long long *counter;  /* work counter (zeroed before launch) */
+    int32_t sector_begin, n_sect, m, n_slots;
     int32_t eU0, eU1, eF0, eF1;
-    int32_t smem_bytes;
-    int64_t termsf_off;
-    const int32_t *sector_prec;   /* per sector (table order): 0 FP64, 1 FP32; null = all of want_prec */
-    int32_t want_prec;            /* items of sectors with another precision are skipped */
+    int32_t pad[3];
 };
 
-/* FP32 kernel with its tables in kernel parameters (constant bank): a group of sectors per launch. */
-#define QMC_PARAM_SECTORS 16
-#define QMC_PARAM_TERMS 1600
-#define QMC_MAX_GROUP_LAUNCHES 1024
+#define QMC_MAX_JOBS 96
 
-struct ParamSector {
-    int32_t kind, sigma, sing_mask, M;
-    int32_t A[6], B[6];
-    int32_t nU, nF, nG, nH;
-    int32_t tbase;      /* first term of the sector in ParamGroup::terms */
-    int32_t orig_index;
-    int32_t psec;       /* packed index */
-    float Df;
-    int16_t gstart[8];
-    int16_t hstart[24];
+/* Kernel parameter block of an evaluation launch (read from the constant bank). */
+struct JobTable {
+    int32_t n_jobs, r, P, want_prec;
+    int64_t total_items;
+    unsigned long long *counter;  /* work counter of this launch (zeroed before it) */
+    int32_t smem_bytes, pad;
+    Job jobs[QMC_MAX_JOBS];
 };
 
-struct ParamGroup {
-    int32_t n_sect, n_terms, pad0, pad1;
-    ParamSector sec[QMC_PARAM_SECTORS];
-    PackedTermF terms[QMC_PARAM_TERMS];
+/* Reduction of one job's partials into its per-(sector, shift) sums. */
+struct FinJob {
+    const unsigned char *packed;
+    int64_t sectors_off, chunks, pair_begin;
+    const double *partials;
+    const uint32_t *part_fails;
+    double *sums;                 /* n_sectors(table order) x m x n_slots x 2 */
+    int64_t *fails;               /* n_sectors x m */
+    int32_t sector_begin, n_sect, m, n_slots;
 };
 
-static_assert(sizeof(ParamSector) % 16 == 0, "param sector must be 16-byte aligned");
+struct FinTable {
+    int32_t n_jobs, pad;
+    int64_t total_pairs;
+    FinJob jobs[QMC_MAX_JOBS];
+};
+
+static_assert(sizeof(JobTable) < 32000, "job table must fit the kernel parameter limit");
+static_assert(sizeof(FinTable) < 32000, "finalize table must fit the kernel parameter limit");
 
 /* Precision probe: a strided sample of each sector's lattice points for one shift, in FP32 and FP64. */
 struct ProbeArgs {
@@ -142,17 +144,6 @@ struct ProbeArgs {
     double *out;                  /* n_sectors(table order) x n_slots x 4: sum|v64|, sum|v32-v64|, sum(v32-v64) re, im */
     int32_t eU0, eU1, eF0, eF1;
     int32_t smem_bytes;
-};
-
-struct FinalizeArgs {
-    const unsigned char *packed;
-    int64_t sectors_off;
-    int32_t sector_begin, n_sect, m, n_slots;
-    int64_t chunks;
-    const double *partials;
-    const uint32_t *part_fails;
-    double *sums;                 /* n_sectors(table order) x m x n_slots x 2 */
-    int64_t *fails;               /* n_sectors x m */
 };
 
 struct PointArgs {
@@ -174,13 +165,10 @@ struct PointArgs {
 };
 
 /* Launchers implemented in qmc_kernels.cu (C++ linkage, internal). */
-int qmc_launch_eval(int dim, int deform, int maxm, int precision, const EvalArgs &a, int grid, int block,
+int qmc_launch_eval(int dim, int deform, int maxm, int precision, const JobTable &t, int grid, int block,
                     void *stream);
-int qmc_launch_finalize(const FinalizeArgs &a, void *stream);
+int qmc_launch_finalize(const FinTable &t, void *stream);
 int qmc_launch_points(int dim, int deform, int maxm, int precision, const PointArgs &a, void *stream);
 int qmc_device_sm_count(int *sms);
 int qmc_eval_blocks_per_sm(int dim, int deform, int maxm, int precision, int block, int smem_bytes, int *out);
 int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *stream);
-int qmc_launch_eval_param(int dim, int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
-                          void *stream);
-int qmc_eval_param_blocks_per_sm(int dim, int deform, int maxm, int block, int *out);

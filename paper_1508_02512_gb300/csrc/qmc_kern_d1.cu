@@ -2,7 +2,7 @@
  * dimension so that the library builds in parallel). */
 #include "qmc_device.cuh"
 
-int qmc_launch_eval_d1(int deform, int maxm, int precision, const EvalArgs &a, int grid, int block, cudaStream_t st) {
+int qmc_launch_eval_d1(int deform, int maxm, int precision, const JobTable &a, int grid, int block, cudaStream_t st) {
     if (precision == QMC_PREC_MIXED) {
         switch (deform * 10 + maxm) {
         case 0: return launch_eval_f32_t<1, false, 0>(a, grid, block, st);
@@ -72,27 +72,3 @@ int qmc_launch_probe_d1(int deform, int maxm, const ProbeArgs &a, cudaStream_t s
     }
 }
 
-int qmc_launch_eval_param_d1(int deform, int maxm, const EvalArgs &a, const ParamGroup &g, int grid, int block,
-                              cudaStream_t st) {
-    switch (deform * 10 + maxm) {
-        case 0: return launch_eval_param_t<1, false, 0>(a, g, grid, block, st);
-        case 2: return launch_eval_param_t<1, false, 2>(a, g, grid, block, st);
-        case 4: return launch_eval_param_t<1, false, 4>(a, g, grid, block, st);
-        case 10: return launch_eval_param_t<1, true, 0>(a, g, grid, block, st);
-        case 12: return launch_eval_param_t<1, true, 2>(a, g, grid, block, st);
-        case 14: return launch_eval_param_t<1, true, 4>(a, g, grid, block, st);
-        default: return QMC_ERR_UNSUPPORTED;
-    }
-}
-
-int qmc_occupancy_param_d1(int deform, int maxm, int block, int *out) {
-    switch (deform * 10 + maxm) {
-        case 0: return occupancy_param_t<1, false, 0>(block, out);
-        case 2: return occupancy_param_t<1, false, 2>(block, out);
-        case 4: return occupancy_param_t<1, false, 4>(block, out);
-        case 10: return occupancy_param_t<1, true, 0>(block, out);
-        case 12: return occupancy_param_t<1, true, 2>(block, out);
-        case 14: return occupancy_param_t<1, true, 4>(block, out);
-        default: return QMC_ERR_UNSUPPORTED;
-    }
-}

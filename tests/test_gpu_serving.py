@@ -1,0 +1,166 @@
+"""Batching and serving: qmc_eval_batch runs many passes in shared persistent launches with results identical to
+running each alone; the serving loop (qmc_submit/qmc_poll/qmc_cancel) admits requests of uneven sector count and
+dimension, overlaps their passes on the device, and returns for every request exactly the result it gives alone
+(and that qmc_integrate gives with the same options)."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1508_02512_gb300 import _native as N  # noqa: E402
+from paper_1508_02512_gb300 import api  # noqa: E402
+from paper_1508_02512_gb300 import tables as T  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def table(cfg):
+    return T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+
+
+def point(cfg, **kw):
+    return W.kinematics(cfg.topology, **{**cfg.point, **kw})
+
+
+def test_batch_equals_alone():
+    lat = dict(api.builtin_lattices())
+    specs = [(W.CONFIG0, point(W.CONFIG0), -2, 0, 4093, 0.0, N.QMC_PREC_FP64),
+             (W.CONFIG1, point(W.CONFIG1), 0, 0, 8191, 0.5, N.QMC_PREC_FP64),
+             (W.CONFIG1, point(W.CONFIG1, s=7.0, t=-2.5), 0, 0, 2039, 0.5, N.QMC_PREC_FP64),
+             (W.CONFIG0, point(W.CONFIG0, s=-5.0), -2, 0, 1021, 0.0, N.QMC_PREC_MIXED),
+             (W.CONFIG2, point(W.CONFIG2), -2, 0, 1021, 0.25, N.QMC_PREC_FP64)]
+    preps, devs, passes, ins, outs = [], [], [], [], []
+    for k, (cfg, kin, omin, omax, n, lam, prec) in enumerate(specs):
+        prep = api.prepare(table(cfg), kin, omin, omax)
+        dev = api.DeviceIntegral(prep)
+        p = api.make_pass(n, lat[n], 6, 3, precision=prec)
+        sh = torch.tensor(W.shifts(40 + k, 6), device="cuda")
+        lm = torch.full((prep.info.n_sectors,), lam, dtype=torch.float64, device="cuda")
+        preps.append(prep)
+        devs.append(dev)
+        passes.append(p)
+        ins.append((sh, lm))
+        outs.append(dev.outputs(p))
+    alone = []
+    for prep, dev, p, (sh, lm), (sums, fails) in zip(preps, devs, passes, ins, outs):
+        dev.eval_sums(p, sh, lm, sums, fails)
+        torch.cuda.synchronize()
+        alone.append((sums.clone(), fails.clone()))
+        sums.zero_()
+        fails.zero_()
+    items = (N.qmc_batch_item * len(specs))()
+    keep = []
+    for i, (prep, dev, p, (sh, lm), (sums, fails)) in enumerate(zip(preps, devs, passes, ins, outs)):
+        buf = ctypes.create_string_buffer(prep.packed)
+        keep.append(buf)
+        items[i].packed_host = ctypes.addressof(buf)
+        items[i].packed_dev = dev.dpacked.data_ptr()
+        items[i].pass_ = p
+        items[i].shifts_dev = sh.data_ptr()
+        items[i].lambda_dev = lm.data_ptr()
+        items[i].sums_dev = sums.data_ptr()
+        items[i].fails_dev = fails.data_ptr()
+    need = N.lib().qmc_batch_scratch_bytes(items, len(specs))
+    assert need > 0
+    scratch = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    base = scratch.data_ptr() + ((-scratch.data_ptr()) % 256)
+    rc = N.lib().qmc_eval_batch(items, len(specs), base, need, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, N.strerror(rc)
+    torch.cuda.synchronize()
+    for (s_a, f_a), (sums, fails) in zip(alone, outs):
+        assert torch.equal(s_a, sums) and torch.equal(f_a, fails)
+
+
+def req_opts(prec, seed):
+    return dict(rel_tol=1e-4, n_shifts=8, seed=seed, lam=0.5, precision=prec)
+
+
+def same(r1, r2):
+    v1, e1 = api.result_arrays(r1)
+    v2, e2 = api.result_arrays(r2)
+    return (r1.status == r2.status and r1.n_final == r2.n_final and r1.passes == r2.passes and np.array_equal(v1, v2)
+            and np.array_equal(e1, e2))
+
+
+@pytest.mark.parametrize("prec", [N.QMC_PREC_FP64, N.QMC_PREC_MIXED], ids=["fp64", "mixed"])
+def test_serving_result_same_alone_and_in_the_mix(prec):
+    ctx = api.Context(0, 2 << 30)
+    ids = {c.name: ctx.load_sectors(table(c)) for c in (W.CONFIG0, W.CONFIG1, W.CONFIG2)}
+    target = (W.CONFIG1, point(W.CONFIG1, s=6.5, t=-1.0), 0, 0)
+    # alone
+    rid = ctx.submit(ids[target[0].name], target[1], target[2], target[3], **req_opts(prec, 7))
+    alone = ctx.wait(rid)
+    assert alone.status == 0
+    # the same request in a mix of uneven sector counts and dimensions, arriving while others run
+    others = [(W.CONFIG2, point(W.CONFIG2, s=7.0), -2, 0, dict(rel_tol=2e-2, n_shifts=8, seed=1, lam=0.5)),
+              (W.CONFIG0, point(W.CONFIG0, s=6.0, t=-1.2), -2, 0, req_opts(prec, 2)),
+              (W.CONFIG1, point(W.CONFIG1), 0, 0, req_opts(prec, 3)),
+              (W.CONFIG0, point(W.CONFIG0), -2, 0, req_opts(prec, 4))]
+    mix_ids = [ctx.submit(ids[c.name], kin, a, b, **o) for c, kin, a, b, o in others[:2]]
+    time.sleep(0.01)
+    rid2 = ctx.submit(ids[target[0].name], target[1], target[2], target[3], **req_opts(prec, 7))
+    mix_ids += [ctx.submit(ids[c.name], kin, a, b, **o) for c, kin, a, b, o in others[2:]]
+    in_mix = ctx.wait(rid2)
+    rest = [ctx.wait(i) for i in mix_ids]
+    assert same(alone, in_mix), (api.result_arrays(alone), api.result_arrays(in_mix))
+    assert all(r.status == 0 for r in rest), [r.status for r in rest]
+    st = ctx.serving_stats()
+    assert st.completed == 6 and st.peak_active >= 2 and st.batched_passes > st.rounds
+    # and the same as qmc_integrate with these options
+    ctx2 = api.Context(0, 1 << 30)
+    i2 = ctx2.load_sectors(table(target[0]))
+    ctx2.set_kinematics(i2, target[1], target[2], target[3])
+    direct = ctx2.integrate(i2, **req_opts(prec, 7))
+    assert same(alone, direct)
+    ctx2.close()
+    ctx.close()
+
+
+def test_serving_cancel():
+    ctx = api.Context(0, 1 << 30)
+    iid = ctx.load_sectors(table(W.CONFIG3))
+    long_id = ctx.submit(iid, point(W.CONFIG3), -2, 0, rel_tol=1e-7, n_shifts=8, seed=5, lam=0.5, max_n=1 << 20)
+    ctx.cancel(long_id)
+    r = ctx.wait(long_id, timeout=120)
+    assert r.status == N.QMC_ERR_CANCELLED, (r.status, r.n_final)
+    ctx.close()
+
+
+def test_serving_admission_by_memory():
+    """A budget that holds only a few requests at a time: the rest wait in the queue, all complete, and the
+    context never holds more device memory than its budget."""
+    budget = 24 << 20
+    ctx = api.Context(0, budget)
+    i1 = ctx.load_sectors(table(W.CONFIG1))
+    i0 = ctx.load_sectors(table(W.CONFIG0))
+    ids = []
+    for k in range(8):
+        if k % 2:
+            ids.append(ctx.submit(i1, point(W.CONFIG1, s=5.0 + 0.5 * k), 0, 0, rel_tol=1e-5, n_shifts=8, seed=k))
+        else:
+            ids.append(ctx.submit(i0, point(W.CONFIG0, s=-2.0 - k), -2, 0, rel_tol=1e-6, n_shifts=8, seed=k))
+    peak_bytes, saw_queue = 0, False
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 120:
+        st = ctx.serving_stats()
+        peak_bytes = max(peak_bytes, st.device_bytes)
+        saw_queue |= st.queued > 0 and st.active > 0
+        if st.completed == len(ids):
+            break
+        time.sleep(0.001)
+    for i in ids:
+        assert ctx.wait(i, timeout=60).status == 0
+    st = ctx.serving_stats()
+    # the budget admits only a few requests at once (each reserves room for its first pass), so some waited
+    assert peak_bytes <= budget and 1 <= st.peak_active < len(ids)
+    ctx.close()
