@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--profile-pass", action="store_true",
                     help="run two passes of the same integral at n = 1048573 and exit (small case for ncu)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="run only the serving workload with this many requests and print its JSON line")
     return ap.parse_args()
 
 
@@ -356,6 +358,7 @@ def main_ours(args):
     if not args.no_extras and rank == 0:
         extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream)
         extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, precision=N.QMC_PREC_MIXED)
+        extras["serving"] = serving_run(24, device=local)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -379,6 +382,57 @@ def main_ours(args):
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0):
+    """Config 4: Poisson arrivals of requests for random integrals (massless box, massive box, planar and
+    non-planar double box) at random s ~ U[4.5,12], t ~ U[-4,-0.5], each integrated to 1e-3 relative error with 16
+    shifts by the serving loop (continuous batching).  Latency = submission to completion."""
+    from paper_1508_02512_gb300 import api
+    from paper_1508_02512_gb300 import tables as T
+    arrivals = W.serving_arrivals(n_requests, rate, seed)
+    ctx = api.Context(device, 8 << 30)
+    ids = [ctx.load_sectors(T.compile_integral(c.topology, T.zero_invariants_of(c.topology, c.point)))
+           for c in W.CONFIGS]
+    # warm the kernels once
+    w = ctx.submit(ids[1], W.CONFIG1.kin, 0, 0, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=1, precision=precision)
+    ctx.wait(w)
+    base = ctx.serving_stats()
+    reqs = []
+    t0 = time.perf_counter()
+    k = 0
+    pending = {}
+    done = {}
+    while len(done) < n_requests:
+        now = time.perf_counter() - t0
+        while k < n_requests and arrivals[k][0] <= now:
+            at, ci, sv, tv = arrivals[k]
+            cfg = W.CONFIGS[ci]
+            kin = W.kinematics(cfg.topology, **{**cfg.point, "s": sv, "t": tv})
+            rid = ctx.submit(ids[ci], kin, cfg.order_min, cfg.order_max, rel_tol=1e-3, n_shifts=N_SHIFTS,
+                             seed=100 + k, lam=LAMBDA, precision=precision, max_seconds=300.0)
+            pending[rid] = (k, ci, time.perf_counter() - t0)
+            k += 1
+        for rid in list(pending):
+            st, r = ctx.poll(rid)
+            if st != 1:
+                done[rid] = (pending.pop(rid), r)
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    stats = ctx.serving_stats()
+    lat = sorted(r.seconds for (_, r) in done.values())
+    ok = sum(1 for (_, r) in done.values() if r.status == 0)
+    per_cfg = {}
+    for (k_, ci, _), r in done.values():
+        per_cfg.setdefault(W.CONFIGS[ci].name, []).append(r.seconds)
+    ctx.close()
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    return {"requests": n_requests, "converged": ok, "offered_rate_per_s": rate, "wall_s": wall,
+            "throughput_req_per_s": n_requests / wall, "p50_s": statistics.median(lat), "p99_s": p99,
+            "per_integral_p50_s": {k2: statistics.median(v) for k2, v in per_cfg.items()},
+            "rounds": stats.rounds - base.rounds, "batched_passes": stats.batched_passes - base.batched_passes,
+            "peak_active": stats.peak_active, "precision": "f32+f64" if precision == 1 else "f64",
+            "rel_tol": 1e-3, "shifts": N_SHIFTS}
 
 
 def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0):
@@ -425,7 +479,9 @@ def profile_pass(precision="fp64"):
 
 if __name__ == "__main__":
     a = parse()
-    if a.profile_pass:
+    if a.serving:
+        print(json.dumps({"metric": "serving time-to-1e-3", **serving_run(a.serving)}))
+    elif a.profile_pass:
         profile_pass(a.precision)
     elif a.impl == "reference":
         main_reference(a)

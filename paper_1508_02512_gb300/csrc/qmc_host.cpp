@@ -1537,6 +1537,8 @@ struct Request {
 
 struct Serving {
     std::thread th;
+    cudaStream_t stream = nullptr; /* the loop's own stream: rounds never wait for, or block, other context calls */
+    DevBuf scratch;                /* the loop's own scratch (counted in the context's budget) */
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
@@ -1565,7 +1567,7 @@ void finish(Serving *S, qmc_ctx *c, Request &r, int status) {
 }
 
 /* host preparation and device buffers of a newly admitted request (called with the context mutex held) */
-int admit(qmc_ctx *c, Request &r) {
+int admit(Serving *S, qmc_ctx *c, Request &r) {
     int rc = qmc_prepare(r.table.data(), r.table.size(), r.inv.data(), (int32_t)r.inv.size(), r.omin, r.omax, nullptr,
                          0, &r.info);
     if (rc) return rc;
@@ -1584,10 +1586,10 @@ int admit(qmc_ctx *c, Request &r) {
     if (!rc) rc = dev_reserve(c, r.dprec, ns * sizeof(int32_t));
     if (!rc) rc = dev_reserve(c, r.dprobe, (size_t)ns * h->n_slots * 4 * sizeof(double));
     if (rc) return rc;
-    rc = cuda_status(cudaMemcpyAsync(r.dpacked.p, r.packed.data(), r.packed.size(), cudaMemcpyHostToDevice, c->stream));
+    rc = cuda_status(cudaMemcpyAsync(r.dpacked.p, r.packed.data(), r.packed.size(), cudaMemcpyHostToDevice, S->stream));
     if (!rc)
         rc = cuda_status(cudaMemcpyAsync(r.dshifts.p, r.shifts.data(), r.shifts.size() * sizeof(double),
-                                         cudaMemcpyHostToDevice, c->stream));
+                                         cudaMemcpyHostToDevice, S->stream));
     r.lam.assign(ns, r.opt.lambda > 0 ? r.opt.lambda : 0.5);
     r.halv.assign(ns, 0);
     r.prec.assign(ns, 1);
@@ -1613,7 +1615,7 @@ qmc_pass pass_of(const Request &r) {
 }
 
 /* FP32 budget check of a mixed-precision request (as in qmc_integrate) */
-int probe(qmc_ctx *c, Request &r) {
+int probe(Serving *S, qmc_ctx *c, Request &r) {
     const PackedHeader *h = header_of(r.packed.data());
     const int ns = h->n_sectors;
     qmc_pass p = pass_of(r);
@@ -1621,14 +1623,14 @@ int probe(qmc_ctx *c, Request &r) {
     const double budget = (r.opt.fp32_budget > 0 ? r.opt.fp32_budget : 0.1) * r.opt.rel_tol;
     std::vector<double> pr((size_t)ns * h->n_slots * 4);
     int rc = cuda_status(cudaMemcpyAsync(r.dlambda.p, r.lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
-                                         c->stream));
+                                         S->stream));
     if (!rc)
         rc = qmc_probe_precision(r.packed.data(), r.dpacked.p, &p, (const double *)r.dshifts.p,
-                                 (const double *)r.dlambda.p, nsamp, (double *)r.dprobe.p, c->stream);
+                                 (const double *)r.dlambda.p, nsamp, (double *)r.dprobe.p, S->stream);
     if (!rc)
         rc = cuda_status(cudaMemcpyAsync(pr.data(), r.dprobe.p, pr.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                         c->stream));
-    if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+                                         S->stream));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
     if (rc) return rc;
     r.res.fp64_reruns = 0;
     for (int s2 = 0; s2 < ns; ++s2) {
@@ -1642,7 +1644,7 @@ int probe(qmc_ctx *c, Request &r) {
     }
     r.probe_due = false;
     return cuda_status(cudaMemcpyAsync(r.dprec.p, r.prec.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                       c->stream));
+                                       S->stream));
 }
 
 /* after a pass: lambda halving, combination, convergence; returns true when the request is finished */
@@ -1749,13 +1751,24 @@ void serve_loop(qmc_ctx *c) {
                 if (S->active.size() + fresh.size() >= QMC_MAX_JOBS / 4) break;
             }
         }
-        std::lock_guard<std::mutex> g(c->mu);
-        for (auto &r : cancelled) finish(S, c, *r, QMC_ERR_CANCELLED);
+        /* device buffers of cancelled and newly admitted requests: the context mutex guards the budget */
+        {
+            std::lock_guard<std::mutex> g(c->mu);
+            for (auto &r : cancelled) finish(S, c, *r, QMC_ERR_CANCELLED);
+            for (auto &r : fresh) {
+                r->t_admit = std::chrono::steady_clock::now();
+                const int rc = admit(S, c, *r);
+                if (rc) {
+                    finish(S, c, *r, rc);
+                    r.reset();
+                }
+            }
+        }
         for (auto &r : fresh) {
-            r->t_admit = std::chrono::steady_clock::now();
-            int rc = admit(c, *r);
-            if (!rc && r->probe_due) rc = probe(c, *r);
+            if (!r) continue;
+            int rc = r->probe_due ? probe(S, c, *r) : QMC_OK;
             if (rc) {
+                std::lock_guard<std::mutex> g(c->mu);
                 finish(S, c, *r, rc);
                 continue;
             }
@@ -1770,13 +1783,13 @@ void serve_loop(qmc_ctx *c) {
             batch = S->active;
         }
         if (batch.empty()) continue;
-        /* this round: one pass per active request, in shared launches */
+        /* this round: one pass per active request, in shared launches (no context lock held meanwhile) */
         int rc = QMC_OK;
         for (auto &r : batch) {
-            if (r->probe_due) rc = probe(c, *r);
+            if (r->probe_due) rc = probe(S, c, *r);
             if (rc) break;
             rc = cuda_status(cudaMemcpyAsync(r->dlambda.p, r->lam.data(), r->lam.size() * sizeof(double),
-                                             cudaMemcpyHostToDevice, c->stream));
+                                             cudaMemcpyHostToDevice, S->stream));
             if (rc) break;
         }
         std::vector<qmc_batch_item> items(batch.size());
@@ -1794,39 +1807,45 @@ void serve_loop(qmc_ctx *c) {
         }
         size_t need = rc ? 0 : qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
         if (!rc && !need) rc = QMC_ERR_ARG;
-        /* the round shrinks (later requests wait) when its scratch would not fit the budget */
-        while (!rc && items.size() > 1 && c->used - c->scratch.bytes + ((need + 4095) & ~size_t(4095)) > c->budget) {
-            items.pop_back();
-            batch.pop_back();
-            need = qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
+        if (!rc) {
+            std::lock_guard<std::mutex> g(c->mu);
+            /* the round shrinks (later requests wait) when its scratch would not fit the budget */
+            while (items.size() > 1 && c->used - S->scratch.bytes + ((need + 4095) & ~size_t(4095)) > c->budget) {
+                items.pop_back();
+                batch.pop_back();
+                need = qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
+            }
+            rc = dev_reserve(c, S->scratch, need);
         }
-        if (!rc) rc = dev_reserve(c, c->scratch, need);
-        if (!rc) rc = qmc_eval_batch(items.data(), (int32_t)items.size(), c->scratch.p, c->scratch.bytes, c->stream);
+        if (!rc) rc = qmc_eval_batch(items.data(), (int32_t)items.size(), S->scratch.p, S->scratch.bytes, S->stream);
         for (size_t i = 0; i < batch.size() && !rc; ++i) {
             Request &r = *batch[i];
             rc = cuda_status(cudaMemcpyAsync(r.sums.data(), r.dsums.p, r.sums.size() * sizeof(double),
-                                             cudaMemcpyDeviceToHost, c->stream));
+                                             cudaMemcpyDeviceToHost, S->stream));
             if (!rc)
                 rc = cuda_status(cudaMemcpyAsync(r.fails.data(), r.dfails.p, r.fails.size() * sizeof(int64_t),
-                                                 cudaMemcpyDeviceToHost, c->stream));
+                                                 cudaMemcpyDeviceToHost, S->stream));
         }
-        if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
         {
             std::lock_guard<std::mutex> g2(S->mu);
             S->stats.rounds += 1;
             S->stats.batched_passes += (int64_t)batch.size();
         }
         std::vector<std::shared_ptr<Request>> done;
-        for (auto &rp : batch) {
-            Request &r = *rp;
-            if (rc) {
-                finish(S, c, r, rc);
-                done.push_back(rp);
-                continue;
+        {
+            std::lock_guard<std::mutex> g(c->mu);
+            for (auto &rp : batch) {
+                Request &r = *rp;
+                if (rc) {
+                    finish(S, c, r, rc);
+                    done.push_back(rp);
+                    continue;
+                }
+                r.res.passes += 1;
+                r.res.evals += (int64_t)r.info.n_sectors * (int64_t)(r.shifts.size() / 6) * r.ladder[r.rung].n;
+                if (advance(S, c, r)) done.push_back(rp);
             }
-            r.res.passes += 1;
-            r.res.evals += (int64_t)r.info.n_sectors * (int64_t)(r.shifts.size() / 6) * r.ladder[r.rung].n;
-            if (advance(S, c, r)) done.push_back(rp);
         }
         std::lock_guard<std::mutex> g2(S->mu);
         for (auto &d : done) S->active.erase(std::remove(S->active.begin(), S->active.end(), d), S->active.end());
@@ -1843,7 +1862,11 @@ void serving_shutdown(qmc_ctx *c) {
     }
     c->serving->cv.notify_all();
     if (c->serving->th.joinable()) c->serving->th.join();
+    cudaSetDevice(c->device);
+    if (c->serving->stream) cudaStreamSynchronize(c->serving->stream);
     for (auto &kv : c->serving->all) release_request(c, *kv.second);
+    dev_release(c, c->serving->scratch);
+    if (c->serving->stream) cudaStreamDestroy(c->serving->stream);
     delete c->serving;
     c->serving = nullptr;
 }
@@ -1887,9 +1910,15 @@ int qmc_submit(qmc_ctx *c, int32_t integral_id, const double *invariants, int32_
     {
         std::lock_guard<std::mutex> g(c->mu);
         if (!c->serving) {
-            c->serving = new Serving();
-            std::memset(&c->serving->stats, 0, sizeof(qmc_serving_stats));
-            c->serving->th = std::thread(serve_loop, c);
+            Serving *S = new Serving();
+            std::memset(&S->stats, 0, sizeof(qmc_serving_stats));
+            cudaSetDevice(c->device);
+            if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+                delete S;
+                return QMC_ERR_CUDA;
+            }
+            c->serving = S;
+            S->th = std::thread(serve_loop, c);
         }
     }
     Serving *S = c->serving;
