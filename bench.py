@@ -14,6 +14,9 @@ derived from the SM count, FP64 units and clock; `cpu_baseline` = the oracle (pl
 bounded sample of the same workload; `time_to_1e-3` = qmc_integrate to 1e-3 relative error over 32 seeds.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --integral planar_dbox|nonplanar_dbox [--log2n 18]   the same measurement on a two-loop
+        double box (46/48 six-dimensional sectors, eps^-2..eps^0, lambda adapted per sector beforehand)
+    python bench.py --serving N   the serving workload: N Poisson arrivals of random integrals
 Multi-GPU (torchrun, one rank per GPU): every rank integrates its own replica with its own shifts (weak
 scaling, no data-path collective); the barrier and max-over-ranks timing use torch.distributed.
 """
@@ -51,9 +54,12 @@ TRAFFIC_BYTES = None
 KERNEL_HASH = None
 
 
+INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3}
+
+
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("qmc_device.cuh", "qmc_kern_d3.cu"):
+    for f in ("qmc_dev.cuh", "qmc_kern_d3.cu"):
         with open(os.path.join(ROOT, "paper_1508_02512_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -66,6 +72,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-accuracy and CPU baseline")
+    ap.add_argument("--integral", choices=sorted(INTEGRALS), default="massive_box",
+                    help="integral of the timed pass (default: the massive one-loop box)")
+    ap.add_argument("--log2n", type=int, default=0, help="lattice size: largest prime below 2^log2n (default "
+                                                         "24 one-loop, 18 two-loop)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="run two passes of the same integral at n = 1048573 and exit (small case for ncu)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
@@ -74,12 +84,16 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(n):
-    return {"workload": f"massive one-loop box, physical s=5 t=-1.5 m^2=1, lambda={LAMBDA}, 4 sectors x "
-                        f"{N_SHIFTS} shifts x n={n} rank-1 lattice, Korobov r=3",
-            "integral": W.CONFIG1.name, "sectors": 4, "shifts": N_SHIFTS, "lattice_n": n,
-            "l2": "inputs (a 3 KB table, shifts) live in shared memory; a 256 MiB buffer is written between steps "
-                  "to flush L2"}
+def workload_config(cfg, n, ns, lam_desc):
+    if cfg is W.CONFIG1:
+        what = f"massive one-loop box, physical s=5 t=-1.5 m^2=1, lambda={lam_desc}, {ns} sectors"
+    else:
+        what = (f"{'planar' if cfg is W.CONFIG2 else 'non-planar'} two-loop double box, physical s=6 t=-2, "
+                f"m^2=1 on four lines, eps^-2..eps^0, lambda={lam_desc}, {ns} six-dimensional sectors")
+    return {"workload": f"{what} x {N_SHIFTS} shifts x n={n} rank-1 lattice, Korobov r=3",
+            "integral": cfg.name, "sectors": ns, "shifts": N_SHIFTS, "lattice_n": n,
+            "l2": "inputs (the sector table, shifts) live in shared memory; a 256 MiB buffer is written between "
+                  "steps to flush L2"}
 
 
 class ClockSampler:
@@ -213,12 +227,13 @@ def main_ours(args):
     world, rank, local, dist = dist_setup(args)
     torch.cuda.set_device(local)
     dev_name = f"cuda:{local}"
-    cfg = W.CONFIG1
+    cfg = INTEGRALS[args.integral]
     blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
-    prep = api.prepare(blob, cfg.kin, 0, 0)
+    prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
     di = api.DeviceIntegral(prep, dev_name)
     lat = dict(api.builtin_lattices())
-    n = max(k for k in lat if k < (1 << LOG2_N))
+    log2n = args.log2n or (LOG2_N if cfg.topology.loops == 1 else 18)
+    n = max(k for k in lat if k < (1 << log2n))
     z = lat[n]
     shifts = W.shifts(cfg.seed + rank, N_SHIFTS)
     p = api.make_pass(n, z, N_SHIFTS, 3)
@@ -228,6 +243,16 @@ def main_ours(args):
     lam = torch.full((ns,), LAMBDA, dtype=torch.float64, device=dev_name)
     sums, fails = di.outputs(p)
     scr, scr_bytes = di.scratch(p)
+    # lambda per sector: halved where the sign check of Eq. 14 fails on this workload (as qmc_integrate does)
+    halvings = 0
+    for _ in range(6):
+        di.eval_sums(p, sh, lam, sums, fails)
+        bad = fails.sum(dim=1) > 0
+        if not bool(bad.any()):
+            break
+        lam[bad] *= 0.5
+        halvings += int(bad.sum().item())
+    lam_desc = f"{LAMBDA}" if halvings == 0 else f"{LAMBDA} halved per failing sector ({halvings} halvings)"
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev_name)
     L = N.lib()
     evals_per_step = ns * N_SHIFTS * n
@@ -271,15 +296,17 @@ def main_ours(args):
         elapsed = float(t.item())
     eval_ms = [a.elapsed_time(b) for a, b, c in evs]
     pass_ms = [a.elapsed_time(c) for a, b, c in evs]
-    assert int(fails.sum().item()) == 0, "sign check of the deformation failed in the benchmark workload"
+    sign_failures = int(fails.sum().item())
     value = world * evals_per_step * args.steps / elapsed
     flops_launch = prep.info.flops_per_eval * evals_per_step
     achieved = flops_launch / (statistics.mean(eval_ms) * 1e-3) / 1e12
     kh = kernel_hash()
     traffic = TRAFFIC_BYTES if (TRAFFIC_BYTES is not None and kh == KERNEL_HASH) else None
 
-    # the same pass in mixed precision (FP32 evaluation, FP64 lattice arithmetic and accumulation)
-    pm = api.make_pass(n, z, N_SHIFTS, 3, precision=N.QMC_PREC_MIXED)
+    # the same pass in mixed precision (FP32 evaluation, FP64 lattice arithmetic and accumulation), with the
+    # evaluator generated for this family (compiled here, before any timing) and with the table evaluator
+    gen_info = api.gen_compile(prep)
+    pm = api.make_pass(n, z, N_SHIFTS, 3, precision=N.QMC_PREC_MIXED, evaluator=N.QMC_EVAL_GENERATED)
     scr_m, scr_m_bytes = di.scratch(pm)
     sums_m, fails_m = di.outputs(pm)
 
@@ -316,7 +343,25 @@ def main_ours(args):
     s64 = sums.cpu().numpy()
     s32 = sums_m.cpu().numpy()
     mixed_dev = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
+    # table evaluator on the same pass (for comparison; fewer steps)
+    pt = api.make_pass(n, z, N_SHIFTS, 3, precision=N.QMC_PREC_MIXED, evaluator=N.QMC_EVAL_TABLE)
+    evs_t = []
+    for i in range(2 + max(1, args.steps // 2)):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), pt, sh.data_ptr(), lam.data_ptr(), scr_m,
+                                        scr_m_bytes, stream.cuda_stream), "qmc_eval_partials")
+            e1.record(stream)
+            if i >= 2:
+                evs_t.append((e0, e1))
+    torch.cuda.synchronize()
+    tab_eval_ms = statistics.mean(a.elapsed_time(b) for a, b in evs_t)
     mixed = {"value": world * evals_per_step * args.steps / tmix, "unit": "evals/s", "dtype": "f32+f64",
+             "evaluator": "generated", "codegen_compile_ms": gen_info.compile_ms,
+             "table_evaluator": {"eval_kernel_ms": tab_eval_ms, "evals_per_s_kernel": evals_per_step / (tab_eval_ms * 1e-3),
+                                 "frac": flops_launch / (tab_eval_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
              "ms_per_step": 1e3 * tmix / args.steps, "eval_kernel_ms": mix_eval_ms,
              "roofline": {"bound": "alu", "achieved": flops_launch / (mix_eval_ms * 1e-3) / 1e12,
                           "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -358,19 +403,19 @@ def main_ours(args):
     if not args.no_extras and rank == 0:
         extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream)
         extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, precision=N.QMC_PREC_MIXED)
-        extras["serving"] = serving_run(24, device=local)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(n),
+            "config": workload_config(cfg, n, ns, lam_desc),
             "e2e": {"value": world * evals_per_step * args.steps / te, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,  # per step: qmc_eval_kernel + qmc_finalize_kernel
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "kernel": "qmc_eval_kernel<3,deform,0>", "flops_per_eval": prep.info.flops_per_eval,
+                         "kernel": f"qmc_eval_kernel<{prep.info.dim},deform,{maxm_of(prep)}>",
+                         "flops_per_eval": prep.info.flops_per_eval, "sign_failures": sign_failures,
                          "eval_kernel_ms": statistics.mean(eval_ms), "pass_ms": statistics.mean(pass_ms),
                          "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz (recipe FP64 1.25 TFLOP/s)",
                          "kernel_hash": kh},
@@ -384,6 +429,11 @@ def main_ours(args):
         dist.destroy_process_group()
 
 
+def maxm_of(prep):
+    k = prep.info.n_slots - 1
+    return 0 if k == 0 else (2 if k <= 2 else 4)
+
+
 def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0):
     """Config 4: Poisson arrivals of requests for random integrals (massless box, massive box, planar and
     non-planar double box) at random s ~ U[4.5,12], t ~ U[-4,-0.5], each integrated to 1e-3 relative error with 16
@@ -392,8 +442,11 @@ def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0):
     from paper_1508_02512_gb300 import tables as T
     arrivals = W.serving_arrivals(n_requests, rate, seed)
     ctx = api.Context(device, 8 << 30)
-    ids = [ctx.load_sectors(T.compile_integral(c.topology, T.zero_invariants_of(c.topology, c.point)))
-           for c in W.CONFIGS]
+    blobs = [T.compile_integral(c.topology, T.zero_invariants_of(c.topology, c.point)) for c in W.CONFIGS]
+    ids = [ctx.load_sectors(b) for b in blobs]
+    # generated evaluators of the four families, compiled before the arrivals start
+    compile_ms = {c.name: api.gen_compile(api.prepare(b, c.kin, c.order_min, c.order_max)).compile_ms
+                  for c, b in zip(W.CONFIGS, blobs)}
     # warm the kernels once
     w = ctx.submit(ids[1], W.CONFIG1.kin, 0, 0, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=1, precision=precision)
     ctx.wait(w)
@@ -432,6 +485,7 @@ def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0):
             "per_integral_p50_s": {k2: statistics.median(v) for k2, v in per_cfg.items()},
             "rounds": stats.rounds - base.rounds, "batched_passes": stats.batched_passes - base.batched_passes,
             "peak_active": stats.peak_active, "precision": "f32+f64" if precision == 1 else "f64",
+            "codegen_compile_ms": compile_ms,
             "rel_tol": 1e-3, "shifts": N_SHIFTS}
 
 

@@ -43,12 +43,21 @@ extern "C" {
 #define QMC_ERR_NOT_FOUND (-10)   /* unknown integral or request id */
 #define QMC_ERR_NO_DEVICE (-11)   /* no usable CUDA device */
 #define QMC_ERR_NOT_CONVERGED (-12) /* lattice ladder exhausted before the requested accuracy */
+#define QMC_ERR_CODEGEN (-13)     /* run-time compilation of a generated evaluator failed (NVRTC) */
 
 #define QMC_MAX_DIM 6             /* sector dimension (7 propagators) */
 #define QMC_MAX_SLOTS 5           /* series slots per sector */
 #define QMC_MAX_ORDERS 8          /* Laurent orders of a result */
 
 enum { QMC_PREC_FP64 = 0, QMC_PREC_MIXED = 1 };
+
+/* Polynomial evaluator of the FP32 evaluation (QMC_PREC_MIXED passes; FP64 evaluation always reads the table):
+ *   QMC_EVAL_AUTO (0)      = QMC_EVAL_GENERATED
+ *   QMC_EVAL_TABLE         the kernels walk each sector's staged term table and decode its exponents per point
+ *   QMC_EVAL_GENERATED     straight-line code generated for the family of sector tables (same exponents) and
+ *                          compiled at run time with NVRTC on first use (qmc_gen_compile); the coefficients
+ *                          are still read from the staged table, so kinematic points of one family share it. */
+enum { QMC_EVAL_AUTO = 0, QMC_EVAL_TABLE = 1, QMC_EVAL_GENERATED = 2 };
 
 /* A rank-1 lattice (Eq. 17): prime size n and generating vector z (a dim-d sector uses z[0..d-1]). */
 typedef struct {
@@ -90,6 +99,8 @@ typedef struct {
     int32_t block;             /* threads per block: 0 = default, else 64..512 and a multiple of 32 */
     int32_t points_per_thread; /* 0 = default, else 1..64 */
     int32_t grid;              /* blocks of the persistent kernel: 0 = one wave on the device */
+    int32_t evaluator;         /* QMC_EVAL_* of the FP32 evaluation */
+    int32_t reserved;
     const int32_t *sector_precision; /* QMC_PREC_MIXED only: device array, one entry per sector (table order),
                                         1 = evaluate in FP32, anything else = FP64; NULL = every sector FP32 */
 } qmc_pass;
@@ -175,11 +186,64 @@ int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const q
  * asynchronous on `stream`.  For each sector s, a strided sample of n_sample lattice points i = k * (n / n_sample)
  * of the shift shift_dev[0..5] is evaluated by both the FP32 and the FP64 device code; per slot it writes
  *   out[(s * n_slots + slot) * 4 + {0,1,2,3}] = sum |v64|, sum |v32 - v64|, sum (v32 - v64) re, im.
+ * The FP32 values come from the table evaluator whatever pass->evaluator says (the generated evaluator performs
+ * the same products and FMAs, summed in another order).
  * The paper evaluates in one precision; the split into an FP32 path with FP64 re-runs of sectors whose FP32
  * error exceeds a budget is this library's (Sec. II, after Eq. 12, motivates FP64 where cancellation is large).
  */
 int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
                         const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream);
+
+/*
+ * Generated evaluators (the paper evaluates a fixed, hand-written integrand per sector; this is the
+ * library's way of getting the same straight-line arithmetic for any table).  A family = the sector tables
+ * with identical exponent structure (same topology and kinematic class, any kinematic point).
+ * qmc_gen_source: writes the CUDA source generated for the family of `packed_host` (an image from qmc_prepare)
+ *   into buf (cap bytes, NUL-terminated); *len receives the size needed (call with buf = NULL to query).
+ *   Host only.  Errors: QMC_ERR_ARG, QMC_ERR_MEMORY (cap too small).
+ * qmc_gen_compile: compiles that source with NVRTC for sm_103a.  load = 0: compile only (no CUDA device needed;
+ *   nothing cached).  load != 0: compile unless the family is cached, load the module on the current device
+ *   and keep it for the life of the process (the FP32 passes of QMC_EVAL_GENERATED do this on first use; call
+ *   it beforehand to keep compilation out of a timed region).  info (may be NULL) receives the family key,
+ *   compilation time (of the cached compilation when cached = 1), source and cubin sizes.
+ *   Errors: QMC_ERR_ARG, QMC_ERR_CODEGEN (NVRTC failed; its log goes to stderr), QMC_ERR_CUDA (load failed).
+ */
+typedef struct {
+    uint64_t family;
+    double compile_ms;
+    int64_t source_bytes, cubin_bytes;
+    int32_t cached, reserved;
+} qmc_gen_info;
+
+int qmc_gen_source(const void *packed_host, char *buf, size_t cap, size_t *len);
+int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info);
+
+/*
+ * Launch-shape autotuner (the paper fixes no launch shape; this is the library's).  qmc_autotune runs the
+ * evaluation launch of `pass` (qmc_eval_partials semantics, synchronous on `stream`) once per candidate shape,
+ * block in {64, 128, 256} threads x points_per_thread in {4, 8, 16, 32}, times each with CUDA events (one
+ * untimed launch first), returns the timings and the fastest shape in *out, and records that shape for the
+ * family of the image, the pass's precision and evaluator and the lattice-size bucket (smallest 2^k >= n).
+ * From then on, in this process, passes of that key whose block and points_per_thread are both 0 use the
+ * recorded shape: qmc_scratch_bytes, qmc_eval_sums, qmc_integrate and the serving loop included.  Results
+ * depend on the shape only through the summation order.  pass->block/points_per_thread are ignored.
+ * scratch: at least qmc_autotune_scratch_bytes(packed_host, pass) bytes (the largest candidate's need).
+ * qmc_autotune_clear forgets every recorded shape.
+ * Errors: QMC_ERR_ARG, QMC_ERR_MEMORY (scratch too small), QMC_ERR_CUDA, and those of qmc_eval_partials.
+ */
+typedef struct {
+    int32_t block, points_per_thread;  /* the fastest candidate */
+    float ms;                          /* its evaluation-launch time */
+    int32_t n_candidates;
+    int32_t candidate_block[16], candidate_points_per_thread[16];
+    float candidate_ms[16];
+} qmc_tune_result;
+
+size_t qmc_autotune_scratch_bytes(const void *packed_host, const qmc_pass *pass);
+int qmc_autotune(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shifts_dev,
+                 const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, qmc_tune_result *out,
+                 void *stream);
+int qmc_autotune_clear(void);
 
 /*
  * qmc_eval_sums_noalloc -- qmc_eval_sums without a caller-provided scratch buffer, for callers that cannot
@@ -240,6 +304,8 @@ typedef struct {
     int64_t probe_samples;   /* QMC_PREC_MIXED: points per sector of the FP32/FP64 probe (0 = 4096) */
     double fp32_budget;      /* QMC_PREC_MIXED: a sector runs in FP64 when its probe's sum|v32-v64| exceeds
                                 fp32_budget * rel_tol * sum|v64| in any order (0 = 0.1) */
+    int32_t evaluator;       /* QMC_EVAL_* of the FP32 evaluation (passes and probe) */
+    int32_t reserved;
 } qmc_options;
 
 typedef struct {

@@ -25,12 +25,16 @@ QMC_ERR_CANCELLED = -9
 QMC_ERR_NOT_FOUND = -10
 QMC_ERR_NO_DEVICE = -11
 QMC_ERR_NOT_CONVERGED = -12
+QMC_ERR_CODEGEN = -13
 
 QMC_MAX_DIM = 6
 QMC_MAX_SLOTS = 5
 QMC_MAX_ORDERS = 8
 QMC_PREC_FP64 = 0
 QMC_PREC_MIXED = 1
+QMC_EVAL_AUTO = 0
+QMC_EVAL_TABLE = 1
+QMC_EVAL_GENERATED = 2
 
 
 class qmc_lattice(ctypes.Structure):
@@ -52,8 +56,8 @@ class qmc_sector_desc(ctypes.Structure):
 
 class qmc_pass(ctypes.Structure):
     _fields_ = [("lattice", qmc_lattice), ("n_shifts", c_int32), ("transform_r", c_int32), ("precision", c_int32),
-                ("block", c_int32), ("points_per_thread", c_int32), ("grid", c_int32),
-                ("sector_precision", c_void_p)]
+                ("block", c_int32), ("points_per_thread", c_int32), ("grid", c_int32), ("evaluator", c_int32),
+                ("reserved", c_int32), ("sector_precision", c_void_p)]
 
 
 class qmc_batch_item(ctypes.Structure):
@@ -66,7 +70,8 @@ class qmc_options(ctypes.Structure):
                 ("seed", c_uint64), ("lambda_", c_double), ("max_halvings", c_int32), ("transform_r", c_int32),
                 ("ladder_start", c_int32), ("n_lattices", c_int32), ("lattices", POINTER(qmc_lattice)),
                 ("shifts", POINTER(c_double)), ("max_n", c_int64), ("max_seconds", c_double), ("block", c_int32),
-                ("points_per_thread", c_int32), ("probe_samples", c_int64), ("fp32_budget", c_double)]
+                ("points_per_thread", c_int32), ("probe_samples", c_int64), ("fp32_budget", c_double),
+                ("evaluator", c_int32), ("reserved", c_int32)]
 
 
 class qmc_result(ctypes.Structure):
@@ -84,6 +89,17 @@ class qmc_serving_stats(ctypes.Structure):
 
 
 # name -> (restype, argtypes); every symbol declared in include/qmcfi.h
+class qmc_gen_info(ctypes.Structure):
+    _fields_ = [("family", c_uint64), ("compile_ms", c_double), ("source_bytes", c_int64), ("cubin_bytes", c_int64),
+                ("cached", c_int32), ("reserved", c_int32)]
+
+
+class qmc_tune_result(ctypes.Structure):
+    _fields_ = [("block", c_int32), ("points_per_thread", c_int32), ("ms", ctypes.c_float),
+                ("n_candidates", c_int32), ("candidate_block", c_int32 * 16),
+                ("candidate_points_per_thread", c_int32 * 16), ("candidate_ms", ctypes.c_float * 16)]
+
+
 PROTOTYPES = {
     "qmc_strerror": (c_char_p, [c_int]),
     "qmc_version": (c_int, []),
@@ -103,6 +119,12 @@ PROTOTYPES = {
                                     c_void_p]),
     "qmc_eval_sums_noalloc": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
+    "qmc_autotune_scratch_bytes": (c_size_t, [c_void_p, POINTER(qmc_pass)]),
+    "qmc_autotune": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_size_t,
+                             POINTER(qmc_tune_result), c_void_p]),
+    "qmc_autotune_clear": (c_int, []),
+    "qmc_gen_source": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "qmc_gen_compile": (c_int, [c_void_p, c_int32, POINTER(qmc_gen_info)]),
     "qmc_eval_points": (c_int, [c_void_p, c_void_p, c_int32, POINTER(qmc_pass), c_void_p, c_double, c_void_p,
                                 c_int64, c_void_p, c_void_p, c_void_p]),
     "qmc_builtin_lattices": (c_int, [POINTER(qmc_lattice), c_int32]),

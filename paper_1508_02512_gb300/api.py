@@ -35,7 +35,7 @@ def builtin_lattices():
 
 
 def make_pass(n: int, z, n_shifts: int, transform_r: int = 3, precision: int = N.QMC_PREC_FP64, block: int = 0,
-              points_per_thread: int = 0, grid: int = 0) -> N.qmc_pass:
+              points_per_thread: int = 0, grid: int = 0, evaluator: int = N.QMC_EVAL_AUTO) -> N.qmc_pass:
     p = N.qmc_pass()
     p.lattice = make_lattice(n, z)
     p.n_shifts = n_shifts
@@ -44,7 +44,24 @@ def make_pass(n: int, z, n_shifts: int, transform_r: int = 3, precision: int = N
     p.block = block
     p.points_per_thread = points_per_thread
     p.grid = grid
+    p.evaluator = evaluator
     return p
+
+
+def gen_source(prep) -> str:
+    """qmc_gen_source: the CUDA source generated for the family of a prepared integral."""
+    n = ctypes.c_size_t()
+    N.check(N.lib().qmc_gen_source(prep.packed, None, 0, ctypes.byref(n)), "qmc_gen_source")
+    buf = ctypes.create_string_buffer(n.value)
+    N.check(N.lib().qmc_gen_source(prep.packed, buf, n.value, ctypes.byref(n)), "qmc_gen_source")
+    return buf.value.decode()
+
+
+def gen_compile(prep, load: bool = True) -> N.qmc_gen_info:
+    """qmc_gen_compile: compile (load=False: compile only, no device) or compile-and-cache the family's module."""
+    info = N.qmc_gen_info()
+    N.check(N.lib().qmc_gen_compile(prep.packed, 1 if load else 0, ctypes.byref(info)), "qmc_gen_compile")
+    return info
 
 
 @dataclass
@@ -129,6 +146,20 @@ class DeviceIntegral:
                                       lam.data_ptr(), scr, nbytes, sums.data_ptr(), fails.data_ptr(),
                                       st.cuda_stream), "qmc_eval_sums")
 
+    def autotune(self, p: N.qmc_pass, shifts, lam, stream=None) -> N.qmc_tune_result:
+        """qmc_autotune: time the candidate launch shapes of pass p and record the fastest (synchronous)."""
+        t = self.torch
+        st = stream if stream is not None else t.cuda.current_stream(self.device)
+        need = int(N.lib().qmc_autotune_scratch_bytes(self.prep.packed, ctypes.byref(p)))
+        if need == 0:
+            raise N.QMCError(N.QMC_ERR_ARG, "qmc_autotune_scratch_bytes")
+        buf = t.empty(need + 256, dtype=t.uint8, device=self.device)
+        base = buf.data_ptr() + (-buf.data_ptr()) % 256
+        r = N.qmc_tune_result()
+        N.check(N.lib().qmc_autotune(self.prep.packed, self.dpacked.data_ptr(), ctypes.byref(p), shifts.data_ptr(),
+                                     lam.data_ptr(), base, need, ctypes.byref(r), st.cuda_stream), "qmc_autotune")
+        return r
+
     def eval_points(self, sector: int, p: N.qmc_pass, shift, lam: float, idx, out, fails, stream=None):
         t = self.torch
         st = stream if stream is not None else t.cuda.current_stream(self.device)
@@ -170,12 +201,13 @@ class Context:
     @staticmethod
     def options(rel_tol=1e-3, abs_tol=0.0, precision=N.QMC_PREC_FP64, n_shifts=16, seed=0, lam=0.5, transform_r=3,
                 ladder_start=0, lattices=None, shifts=None, max_n=0, max_seconds=0.0, max_halvings=6, block=0,
-                points_per_thread=0):
+                points_per_thread=0, evaluator=N.QMC_EVAL_AUTO, probe_samples=0, fp32_budget=0.0):
         """qmc_options and the Python objects that must outlive the call that uses them."""
         o = N.qmc_options()
         o.rel_tol, o.abs_tol, o.precision, o.n_shifts, o.seed = rel_tol, abs_tol, precision, n_shifts, seed
         o.lambda_, o.max_halvings, o.transform_r, o.ladder_start = lam, max_halvings, transform_r, ladder_start
         o.max_n, o.max_seconds, o.block, o.points_per_thread = max_n, max_seconds, block, points_per_thread
+        o.evaluator, o.probe_samples, o.fp32_budget = evaluator, probe_samples, fp32_budget
         keep = []
         if lattices is not None:
             arr = (N.qmc_lattice * len(lattices))(*[make_lattice(n, z) for n, z in lattices])
@@ -224,23 +256,9 @@ class Context:
         N.check(N.lib().qmc_serving_stats_get(self._c, ctypes.byref(st)), "qmc_serving_stats_get")
         return st
 
-    def integrate(self, integral_id: int, rel_tol=1e-3, abs_tol=0.0, precision=N.QMC_PREC_FP64, n_shifts=16, seed=0,
-                  lam=0.5, transform_r=3, ladder_start=0, lattices=None, shifts=None, max_n=0, max_seconds=0.0,
-                  max_halvings=6, block=0, points_per_thread=0) -> N.qmc_result:
-        o = N.qmc_options()
-        o.rel_tol, o.abs_tol, o.precision, o.n_shifts, o.seed = rel_tol, abs_tol, precision, n_shifts, seed
-        o.lambda_, o.max_halvings, o.transform_r, o.ladder_start = lam, max_halvings, transform_r, ladder_start
-        o.max_n, o.max_seconds, o.block, o.points_per_thread = max_n, max_seconds, block, points_per_thread
-        keep = []
-        if lattices is not None:
-            arr = (N.qmc_lattice * len(lattices))(*[make_lattice(n, z) for n, z in lattices])
-            keep.append(arr)
-            o.n_lattices = len(lattices)
-            o.lattices = arr
-        if shifts is not None:
-            sh = np.ascontiguousarray(np.asarray(shifts, dtype=np.float64))
-            keep.append(sh)
-            o.shifts = _dptr(sh)
+    def integrate(self, integral_id: int, rel_tol=1e-3, **kw) -> N.qmc_result:
+        """qmc_integrate (blocking); keyword arguments as in options()."""
+        o, keep = self.options(rel_tol=rel_tol, **kw)
         r = N.qmc_result()
         st = N.lib().qmc_integrate(self._c, integral_id, ctypes.byref(o), ctypes.byref(r))
         if st < 0 and st not in (N.QMC_ERR_NOT_CONVERGED, N.QMC_ERR_TIMEOUT):

@@ -2,8 +2,10 @@
 
     python -m paper_1508_02512_gb300.build
 
-compiles csrc/qmc_kernels.cu and csrc/qmc_host.cpp in parallel with nvcc and links
-paper_1508_02512_gb300/_build/libqmcfi.so against the shared CUDA runtime.
+compiles the csrc/ translation units in parallel with nvcc and links paper_1508_02512_gb300/_build/libqmcfi.so
+against the shared CUDA runtime and NVRTC.  The device headers are also embedded into the library as string
+literals (_build/qmc_jit_sources.h), because the generated evaluators (qmc_jit.cpp) are compiled at run time
+together with them.
 """
 from __future__ import annotations
 
@@ -19,7 +21,11 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmcfi.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_host.cpp", "qmc_noalloc.cu"] + [f"qmc_kern_d{d}.cu" for d in range(1, 7)]
+SOURCES = ["qmc_kernels.cu", "qmc_host.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"] + [f"qmc_kern_d{d}.cu" for d in range(1, 7)]
+# device headers compiled again at run time with the generated evaluators: (C identifier, file)
+EMBEDDED = [("qmc_src_qmcfi_h", os.path.join(ROOT, "include", "qmcfi.h")),
+            ("qmc_src_qmc_internal_h", os.path.join(CSRC, "qmc_internal.h")),
+            ("qmc_src_qmc_dev_cuh", os.path.join(CSRC, "qmc_dev.cuh"))]
 
 
 def nvcc() -> str:
@@ -34,9 +40,23 @@ def _cuda_lib_dir(nv: str) -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in SOURCES + ["qmc_internal.h", "qmc_device.cuh", "lattice_table.h"]]
+    files = [os.path.join(CSRC, f) for f in SOURCES + ["qmc_internal.h", "qmc_device.cuh", "qmc_dev.cuh", "lattice_table.h"]]
     files.append(os.path.join(ROOT, "include", "qmcfi.h"))
     return files
+
+
+def write_embedded(path: str) -> None:
+    """C++ header holding each file of EMBEDDED as a raw string literal."""
+    out = ["/* generated by paper_1508_02512_gb300/build.py: device headers for run-time compilation */", "#pragma once"]
+    for name, f in EMBEDDED:
+        text = open(f).read()
+        if ')QMCSRC"' in text:
+            raise RuntimeError(f"{f} contains the raw-string delimiter")
+        out.append(f'static const char {name}[] = R"QMCSRC({text})QMCSRC";')
+    tmp = path + f".{os.getpid()}.tmp"
+    with open(tmp, "w") as fh:
+        fh.write("\n".join(out) + "\n")
+    os.replace(tmp, path)
 
 
 def up_to_date() -> bool:
@@ -51,7 +71,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nv = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC,
+    write_embedded(os.path.join(OUT, "qmc_jit_sources.h"))
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", OUT,
                      "-I", os.path.join(ROOT, "include")] + list(extra)
     tag = f"{os.getpid()}"
     objs = []
@@ -73,7 +94,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         list(ex.map(run, cmds))
     tmp = LIB + f".{tag}.tmp"
     libdir = _cuda_lib_dir(nv)
-    run([nv, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-L", libdir,
+    run([nv, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-L", libdir, "-lnvrtc",
                                                      "-Xlinker", f"-rpath={libdir}"])
     os.replace(tmp, LIB)
     for o in objs:

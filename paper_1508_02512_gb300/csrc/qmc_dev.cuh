@@ -1,0 +1,1221 @@
+#pragma once
+/*
+ * GB300 (sm_103a) kernels of the quasi-Monte Carlo sector integrator.
+ *
+ * Li, Wang, Yan, Zhao, "Efficient Numerical Evaluation of Feynman Integrals", Chin. Phys. C 40 (2016) 033103.
+ *
+ * qmc_eval_kernel (persistent, one launch per sector class): blocks take work items from an atomic counter;
+ *   an item is (sector, shift, chunk of blockDim * P consecutive lattice indices).  The block stages the
+ *   sector's polynomial terms into shared memory (one copy per sector change), each thread walks P lattice
+ *   points i = i0 + p * blockDim with integer index arithmetic (Eq. 17: x = {i z / n + Delta}), evaluates
+ *   the sector integrand series (periodising transform Eq. 21, contour deformation Eq. 14 with its Jacobian,
+ *   endpoint subtraction Eqs. 10-12, eps expansion) and accumulates it with Kahan compensation; the block
+ *   reduces with warp shuffles and writes one partial per item and slot.
+ * qmc_finalize_kernel: one warp per (sector, shift) sums that pair's item partials in a fixed order
+ *   (compensated), so results do not depend on which block ran which item (Eqs. 16 and 18).
+ * qmc_points_kernel: the same per-point device code on explicit lattice indices (sampled checks).
+ *
+ * The path is bound by FP64 arithmetic (no dense contraction, nothing streamed from HBM), so no tensor cores
+ * or TMA are used: tables live in shared memory, points are generated, outputs are a few KB.
+ *
+ * This header holds device code only, so that it also compiles at run time (NVRTC) together with the
+ * polynomial code generated for one family of sector tables; the host launchers are in qmc_device.cuh.
+ */
+#ifndef __CUDACC_RTC__
+#include <math.h>
+#include <stdint.h>
+#endif
+
+#include "qmc_internal.h"
+
+#define DEV __device__ __forceinline__
+#define QMC_PI 3.141592653589793
+
+/* ------------------------------------------------------------------ complex double */
+struct cd {
+    double x, y;
+};
+DEV cd mk(double x, double y) { return cd{x, y}; }
+DEV cd cadd(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+DEV cd csub(cd a, cd b) { return cd{a.x - b.x, a.y - b.y}; }
+DEV cd cscale(cd a, double s) { return cd{a.x * s, a.y * s}; }
+DEV cd cmul(cd a, cd b) { return cd{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)}; }
+DEV cd cinv(cd a) {
+    const double d = __drcp_rn(fma(a.x, a.x, a.y * a.y));
+    return cd{a.x * d, -a.y * d};
+}
+DEV cd cdiv(cd a, cd b) { return cmul(a, cinv(b)); }
+DEV cd cipow(cd z, int e) {
+    cd r = mk(1.0, 0.0);
+    int k = e < 0 ? -e : e;
+    for (int i = 0; i < k; ++i) r = cmul(r, z);
+    return e < 0 ? cinv(r) : r;
+}
+DEV double ipow(double v, int e) {
+    double r = 1.0;
+    int k = e < 0 ? -e : e;
+    for (int i = 0; i < k; ++i) r *= v;
+    return e < 0 ? __drcp_rn(r) : r;
+}
+/* principal log */
+DEV cd clog_p(cd z) { return cd{0.5 * log(fma(z.x, z.x, z.y * z.y)), atan2(z.y, z.x)}; }
+/* log(F - i0): a negative real F lies at arg -pi */
+DEV cd clog_mi0(cd z) {
+    double arg = (z.y == 0.0) ? (z.x < 0.0 ? -QMC_PI : 0.0) : atan2(z.y, z.x);
+    return cd{0.5 * log(fma(z.x, z.x, z.y * z.y)), arg};
+}
+
+/* ------------------------------------------------------------------ periodising transform (Eq. 21, order r) */
+/* t = phi_r(x), tm = phi_r(1-x) = 1 - t, w = phi_r'(x); phi_r' = c_r x^r (1-x)^r, c_r = (2r+1)!/(r!)^2 */
+DEV double phi_poly(int r, double x) {
+    switch (r) {
+        case 0: return x;
+        case 1: return x * x * fma(-2.0, x, 3.0);
+        case 2: return x * x * x * fma(x, fma(6.0, x, -15.0), 10.0);
+        default: {
+            const double x2 = x * x;
+            return x2 * x2 * fma(x, fma(x, fma(-20.0, x, 70.0), -84.0), 35.0);
+        }
+    }
+}
+/* phi is evaluated on the smaller of x and 1-x only; phi_r(1-x) = 1 - phi_r(x) gives the other side, which is
+   >= 1/2 and therefore exact to rounding */
+DEV void transform(int r, double x, double &t, double &tm, double &w) {
+    const double y = 1.0 - x;
+    const bool lo = x <= 0.5;
+    const double p = phi_poly(r, lo ? x : y);
+    const double q = 1.0 - p;
+    t = lo ? p : q;
+    tm = lo ? q : p;
+    const double xy = x * y;
+    switch (r) {
+        case 0: w = 1.0; break;
+        case 1: w = 6.0 * xy; break;
+        case 2: w = 30.0 * xy * xy; break;
+        default: w = 140.0 * xy * xy * xy; break;
+    }
+}
+
+/* ------------------------------------------------------------------ polynomials from shared memory */
+DEV uint64_t term_exps(const PackedTerm &T) { return *reinterpret_cast<const uint64_t *>(T.e); }
+
+/* sum_a c_a prod_j t_j^{e_aj}: the monomial starts from its first factor and the coefficient enters through
+   one FMA into the accumulator; exponents are warp-uniform (every lane reads the same term) */
+template <int S>
+DEV double poly_r(const PackedTerm *__restrict__ T, int n, const double *t) {
+    double acc = 0.0;
+    for (int a = 0; a < n; ++a) {
+        const double c = T[a].c;
+        const uint64_t ew = term_exps(T[a]);
+        if (ew == 0) {
+            acc += c;
+            continue;
+        }
+        double m = 1.0;
+        bool have = false;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            int e = (int)((ew >> (8 * j)) & 0xffu);
+            if (e > 0) {
+                if (!have) {
+                    m = t[j];
+                    have = true;
+                    --e;
+                }
+                for (int k = 0; k < e; ++k) m *= t[j];
+            }
+        }
+        acc = fma(c, m, acc);
+    }
+    return acc;
+}
+
+template <int S>
+DEV cd poly_c(const PackedTerm *__restrict__ T, int n, const cd *z) {
+    cd acc = mk(0.0, 0.0);
+    for (int a = 0; a < n; ++a) {
+        const double c = T[a].c;
+        const uint64_t ew = term_exps(T[a]);
+        if (ew == 0) {
+            acc.x += c;
+            continue;
+        }
+        cd m = mk(1.0, 0.0);
+        bool have = false;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            int e = (int)((ew >> (8 * j)) & 0xffu);
+            if (e > 0) {
+                if (!have) {
+                    m = z[j];
+                    have = true;
+                    --e;
+                }
+                for (int k = 0; k < e; ++k) m = cmul(m, z[j]);
+            }
+        }
+        acc.x = fma(c, m.x, acc.x);
+        acc.y = fma(c, m.y, acc.y);
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------ det(I - i lam A), A real S x S */
+template <int S>
+DEV cd det_deform(const double (&A)[S][S], double lam) {
+    if constexpr (S == 1) {
+        return mk(1.0, -lam * A[0][0]);
+    } else if constexpr (S == 2) {
+        const double tr = A[0][0] + A[1][1];
+        const double dt = fma(A[0][0], A[1][1], -A[0][1] * A[1][0]);
+        return mk(fma(-lam * lam, dt, 1.0), -lam * tr);
+    } else if constexpr (S == 3) {
+        /* det(I + cA) = 1 + c tr A + c^2 E2(A) + c^3 det A with c = -i lam */
+        const double tr = A[0][0] + A[1][1] + A[2][2];
+        const double e2 = fma(A[0][0], A[1][1], -A[0][1] * A[1][0]) + fma(A[0][0], A[2][2], -A[0][2] * A[2][0]) +
+                          fma(A[1][1], A[2][2], -A[1][2] * A[2][1]);
+        const double dt = A[0][0] * fma(A[1][1], A[2][2], -A[1][2] * A[2][1]) -
+                          A[0][1] * fma(A[1][0], A[2][2], -A[1][2] * A[2][0]) +
+                          A[0][2] * fma(A[1][0], A[2][1], -A[1][1] * A[2][0]);
+        const double l2 = lam * lam;
+        return mk(fma(-l2, e2, 1.0), fma(l2 * lam, dt, -lam * tr));
+    } else {
+        /* Gaussian elimination with partial pivoting on J = I - i lam A */
+        cd J[S][S];
+#pragma unroll
+        for (int r = 0; r < S; ++r)
+#pragma unroll
+            for (int c = 0; c < S; ++c) J[r][c] = mk(r == c ? 1.0 : 0.0, -lam * A[r][c]);
+        cd det = mk(1.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            int p = c;
+            double best = fabs(J[c][c].x) + fabs(J[c][c].y);
+#pragma unroll
+            for (int r = c + 1; r < S; ++r) {
+                const double v = fabs(J[r][c].x) + fabs(J[r][c].y);
+                if (v > best) {
+                    best = v;
+                    p = r;
+                }
+            }
+            if (p != c) {
+                det = cscale(det, -1.0);
+#pragma unroll
+                for (int r = c + 1; r < S; ++r) {
+                    if (r == p) {
+#pragma unroll
+                        for (int k = c; k < S; ++k) {
+                            const cd tmp = J[c][k];
+                            J[c][k] = J[r][k];
+                            J[r][k] = tmp;
+                        }
+                    }
+                }
+            }
+            det = cmul(det, J[c][c]);
+            const cd inv = cinv(J[c][c]);
+#pragma unroll
+            for (int r = c + 1; r < S; ++r) {
+                const cd f = cmul(J[r][c], inv);
+#pragma unroll
+                for (int k = c + 1; k < S; ++k) J[r][k] = csub(J[r][k], cmul(f, J[c][k]));
+            }
+        }
+        return det;
+    }
+}
+
+/* ------------------------------------------------------------------ sector integrand */
+struct Exps {
+    int eU0, eU1, eF0, eF1;
+};
+
+/* G at the point tt (t with the subset Y zeroed): returns its eps^0 value G0 and the eps-coefficient X of
+   its logarithm, so that G(eps) = G0 exp(X eps) (Sec. II, Eq. 9 with the deformation of Eq. 14). */
+template <int S, bool DEF, int MAXM>
+DEV void eval_G(const PackedSector &s, const PackedTerm *__restrict__ T, const double *tt, const double *ttm,
+                const double *Lt, double lam, int M, const Exps &ex, cd &G0, cd &X, uint32_t &fails) {
+    const PackedTerm *TU = T;
+    const PackedTerm *TF = T + s.nU;
+    if constexpr (!DEF) {
+        const double U = poly_r<S>(TU, s.nU, tt);
+        double F = poly_r<S>(TF, s.nF, tt);
+        if (s.kind == 1) F = -F;
+        double g = s.D * ipow(U, ex.eU0) * ipow(F, -ex.eF0);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < s.A[j]; ++k) g *= tt[j];
+        G0 = mk(g, 0.0);
+        X = mk(0.0, 0.0);
+        if (MAXM > 0 && M > 0) {
+            /* eU1 log U - eF1 log F as one logarithm: both are real and positive on this path */
+            double x = log(ipow(U, ex.eU1) * ipow(F, -ex.eF1));
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+                if (s.A[j] != -1 && s.B[j] != 0) x = fma((double)s.B[j], Lt[j], x);
+            X = mk(x, 0.0);
+        }
+    } else {
+        const PackedTerm *TG = TF + s.nF;
+        const PackedTerm *TH = TG + s.nG;
+        double g[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) g[j] = poly_r<S>(TG + s.gstart[j], s.gstart[j + 1] - s.gstart[j], tt);
+        double A[S][S];
+        int p = 0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+#pragma unroll
+            for (int k = j; k < S; ++k) {
+                const double h = poly_r<S>(TH + s.hstart[p], s.hstart[p + 1] - s.hstart[p], tt);
+                ++p;
+                A[j][k] = tt[j] * ttm[j] * h;
+                if (k != j) A[k][j] = tt[k] * ttm[k] * h;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) A[j][j] = fma(ttm[j] - tt[j], g[j], A[j][j]);
+        const cd detJ = det_deform<S>(A, lam);
+        cd z[S], q[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const double d = lam * ttm[j] * g[j];
+            z[j] = mk(tt[j], -tt[j] * d);
+            q[j] = mk(1.0, -d);
+        }
+        const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
+        const cd U = needU ? poly_c<S>(TU, s.nU, z) : mk(1.0, 0.0);
+        const cd F = poly_c<S>(TF, s.nF, z);
+        fails += (F.y > 0.0) ? 1u : 0u;
+        cd G = cscale(detJ, s.D);
+        if (ex.eU0 != 0) G = cmul(G, cipow(U, ex.eU0));
+        G = cmul(G, cipow(F, -ex.eF0));
+        bool any_mono = false;
+        double mono = 1.0;
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < s.A[j]; ++k) {
+                mono *= tt[j];
+                any_mono = true;
+            }
+        if (any_mono) G = cscale(G, mono);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (s.A[j] != 0) G = cmul(G, cipow(q[j], s.A[j]));
+        G0 = G;
+        X = mk(0.0, 0.0);
+        if (MAXM > 0 && M > 0) {
+            cd x = csub(cscale(clog_p(U), (double)ex.eU1), cscale(clog_mi0(F), (double)ex.eF1));
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                if (s.B[j] != 0) {
+                    if (s.A[j] != -1) x.x = fma((double)s.B[j], Lt[j], x.x);
+                    x = cadd(x, cscale(clog_p(q[j]), (double)s.B[j]));
+                }
+            }
+            X = x;
+        }
+    }
+}
+
+/* w(x) * (sector integrand) at x, as series slots 0..M (slot n = coefficient of eps^(n - sigma)).
+   Subtraction of Eq. (11) with alpha = -1, regrouped over the zeroed subsets Y of the singular set S:
+   eps^sigma I = sum_Y G_Y(eps) V_Y(eps),  V_Y = prod_{j in S\Y} eps t_j^{-1+B eps} prod_{j in Y} (1/B_j - eps t_j^{-1+B eps}). */
+template <int S, bool DEF, int MAXM>
+DEV void point_integrand(const PackedSector &s, const PackedTerm *__restrict__ T, const double *x, int r, double lam,
+                         const Exps &ex, cd (&out)[MAXM + 1], uint32_t &fails) {
+    double t[S], tm[S], w = 1.0;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        double wj;
+        transform(r, x[j], t[j], tm[j], wj);
+        w *= wj;
+        bad |= x[j] == 0.0; /* the weight and t vanish only there: x < 1 after the wrap */
+    }
+#pragma unroll
+    for (int n = 0; n <= MAXM; ++n) out[n] = mk(0.0, 0.0);
+    if (bad) return;
+    const int M = s.M;
+    const unsigned smask = (unsigned)s.sing_mask;
+    double Lt[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) Lt[j] = 0.0;
+    if (MAXM > 0 && M > 0) {
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (((smask >> j) & 1u) || s.B[j] != 0) Lt[j] = log(t[j]);
+    }
+    unsigned Y = 0;
+    do {
+        double tt[S], ttm[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const bool zj = (Y >> j) & 1u;
+            tt[j] = zj ? 0.0 : t[j];
+            ttm[j] = zj ? 1.0 : tm[j];
+        }
+        cd G0, X;
+        eval_G<S, DEF, MAXM>(s, T, tt, ttm, Lt, lam, M, ex, G0, X, fails);
+        double V[MAXM + 1];
+        V[0] = 1.0;
+#pragma unroll
+        for (int n = 1; n <= MAXM; ++n) V[n] = 0.0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            if ((smask >> j) & 1u) {
+                const bool inY = (Y >> j) & 1u;
+                const double Bj = (double)s.B[j];
+                double f[MAXM + 1];
+                f[0] = inY ? 1.0 / Bj : 0.0;
+                double c = 1.0 / t[j];
+#pragma unroll
+                for (int n = 1; n <= MAXM; ++n) {
+                    f[n] = inY ? -c : c;
+                    c *= Bj * Lt[j] / n;
+                }
+#pragma unroll
+                for (int n = MAXM; n >= 0; --n) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int k = 0; k <= n; ++k) acc = fma(V[k], f[n - k], acc);
+                    V[n] = acc;
+                }
+            }
+        }
+        cd g = G0;
+#pragma unroll
+        for (int n = 0; n <= MAXM; ++n) {
+            if (n <= M) {
+#pragma unroll
+                for (int k = 0; k + n <= MAXM; ++k)
+                    if (n + k <= M) out[n + k] = cadd(out[n + k], cscale(g, V[k]));
+                g = cscale(cmul(g, X), 1.0 / (n + 1));
+            }
+        }
+        Y = (Y - smask) & smask;
+    } while (Y != 0);
+#pragma unroll
+    for (int n = 0; n <= MAXM; ++n) out[n] = cscale(out[n], w);
+}
+
+/* ------------------------------------------------------------------ staging a sector into shared memory */
+DEV void stage_sector(const unsigned char *packed, int64_t sectors_off, int64_t terms_off, int psec,
+                      unsigned char *smem) {
+    const PackedSector *ps = reinterpret_cast<const PackedSector *>(packed + sectors_off) + psec;
+    const int4 *src = reinterpret_cast<const int4 *>(ps);
+    int4 *dst = reinterpret_cast<int4 *>(smem);
+    constexpr int NS = (int)(sizeof(PackedSector) / 16);
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = src[k];
+    const int nt = ps->n_terms;
+    const int4 *tsrc = reinterpret_cast<const int4 *>(packed + terms_off) + ps->term0;
+    int4 *tdst = dst + NS;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) tdst[k] = tsrc[k];
+}
+
+/* Smallest integer r with fma(r, 1/n, delta) >= 1: the lattice point x = {r/n + delta} wraps exactly for
+   r >= R, so the per-point wrap test is an integer compare (evaluated once per item and shift). */
+DEV uint32_t wrap_threshold(double delta, uint32_t n, double invn) {
+    double g = ceil((1.0 - delta) * (double)n);
+    uint32_t R = g <= 0.0 ? 0u : (g >= (double)n ? n : (uint32_t)g);
+    while (R > 0 && fma((double)(R - 1), invn, delta) >= 1.0) --R;
+    while (R < n && fma((double)R, invn, delta) < 1.0) ++R;
+    return R;
+}
+
+DEV void kahan_add(double &s, double &c, double v) {
+    const double y = v - c;
+    const double t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+/* ------------------------------------------------------------------ job lookup */
+/* the job whose item range contains `item` (jobs are in increasing item_begin) */
+DEV int find_job(const JobTable &jt, long long item) {
+    int lo = 0, hi = jt.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jt.jobs[mid].item_begin <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+/* ------------------------------------------------------------------ K1: persistent FP64 evaluation */
+template <int S, bool DEF, int MAXM>
+__global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ JobTable jt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_job;
+    __shared__ double s_red[16][2 * (MAXM + 1)];
+    __shared__ uint32_t s_fail[16];
+    const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
+    const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int cur = -1, cur_job = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(jt.counter, 1ull);
+            s_item = it;
+            s_job = it < jt.total_items ? find_job(jt, it) : 0;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= jt.total_items) break;
+        const int jb = s_job;
+        const Job &J = jt.jobs[jb];
+        const long long local = item - J.item_begin;
+        const long long per_sector = (long long)J.m * J.chunks;
+        const int ls = (int)(local / per_sector);
+        const long long rem = local - (long long)ls * per_sector;
+        const int shift = (int)(rem / J.chunks);
+        const long long chunk = rem - (long long)shift * J.chunks;
+        const int psec = J.sector_begin + ls;
+        if (J.sector_prec) {
+            /* mixed pass: items of sectors evaluated in FP32 belong to the other kernel */
+            const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
+            if (J.sector_prec[gps->orig_index] == 1) {
+                __syncthreads();
+                continue;
+            }
+        }
+        if (psec != cur || jb != cur_job) {
+            stage_sector(J.packed, J.sectors_off, J.terms_off, psec, smem);
+            __syncthreads();
+            cur = psec;
+            cur_job = jb;
+        }
+        const Exps ex{J.eU0, J.eU1, J.eF0, J.eF1};
+        const uint32_t n = J.n;
+        const double invn = J.invn;
+        const double lam = J.lambda[sec.orig_index];
+        double delta[S];
+        uint32_t rj[S], Rj[S], zs[S];
+        const long long i0 = chunk * (long long)blockDim.x * jt.P + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            delta[j] = J.shifts[6 * shift + j];
+            rj[j] = (uint32_t)(((unsigned long long)i0 * J.z[j]) % n);
+            Rj[j] = wrap_threshold(delta[j], n, invn);
+            zs[j] = J.zstep[j];
+        }
+        /* a thread sums its P points plainly; the block combines threads by a shuffle tree, warps and items
+           with compensated (Kahan) sums */
+        double acc[2 * (MAXM + 1)];
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = 0.0;
+        uint32_t fails = 0;
+        for (int p = 0; p < jt.P; ++p) {
+            const long long i = i0 + (long long)p * blockDim.x;
+            if (i < (long long)n) {
+                double x[S];
+#pragma unroll
+                for (int j = 0; j < S; ++j) x[j] = fma((double)rj[j], invn, delta[j]) - (rj[j] >= Rj[j] ? 1.0 : 0.0);
+                cd val[MAXM + 1];
+                point_integrand<S, DEF, MAXM>(sec, T, x, jt.r, lam, ex, val, fails);
+#pragma unroll
+                for (int m = 0; m <= MAXM; ++m) {
+                    acc[2 * m] += val[m].x;
+                    acc[2 * m + 1] += val[m].y;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const uint32_t v = rj[j] + zs[j];
+                rj[j] = v >= n ? v - n : v;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) {
+            double v = acc[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) s_red[warp][q] = v;
+        }
+        uint32_t f = fails;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+        if (lane == 0) s_fail[warp] = f;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            if (q < J.n_slots * 2) {
+                double s2 = 0.0, c2 = 0.0;
+                if (q < 2 * (MAXM + 1))
+                    for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
+                J.partials[local * J.n_slots * 2 + q] = s2 - c2;
+            }
+            if (q == 0) {
+                uint32_t tf = 0;
+                for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
+                J.part_fails[local] = tf;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+/* ================================================================== FP32 path of the mixed-precision pass
+ * The integrand is evaluated in FP32: GB300 issues ~58x more FP32 than FP64 operations.  What stays exact or
+ * FP64: the lattice index arithmetic (integers), 1 - x (formed from integers, never by subtraction), the
+ * accumulation of the point values (double-float per thread, FP64 per work item and across items). */
+struct cf {
+    float x, y;
+};
+DEV cf mkf(float x, float y) { return cf{x, y}; }
+DEV cf caddf(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+DEV cf csubf(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
+DEV cf cscalef(cf a, float s) { return cf{a.x * s, a.y * s}; }
+DEV cf cmulf(cf a, cf b) { return cf{fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
+DEV cf cinvf(cf a) {
+    const float d = __frcp_rn(fmaf(a.x, a.x, a.y * a.y));
+    return cf{a.x * d, -a.y * d};
+}
+DEV cf cipowf(cf z, int e) {
+    cf r = mkf(1.f, 0.f);
+    int k = e < 0 ? -e : e;
+    for (int i = 0; i < k; ++i) r = cmulf(r, z);
+    return e < 0 ? cinvf(r) : r;
+}
+DEV float ipowf_(float v, int e) {
+    float r = 1.f;
+    int k = e < 0 ? -e : e;
+    for (int i = 0; i < k; ++i) r *= v;
+    return e < 0 ? __frcp_rn(r) : r;
+}
+DEV cf clogf_p(cf z) { return cf{0.5f * __logf(fmaf(z.x, z.x, z.y * z.y)), atan2f(z.y, z.x)}; }
+DEV cf clogf_mi0(cf z) {
+    const float arg = (z.y == 0.f) ? (z.x < 0.f ? -3.14159265358979f : 0.f) : atan2f(z.y, z.x);
+    return cf{0.5f * __logf(fmaf(z.x, z.x, z.y * z.y)), arg};
+}
+
+DEV float phi_poly_f(int r, float x) {
+    switch (r) {
+        case 0: return x;
+        case 1: return x * x * fmaf(-2.f, x, 3.f);
+        case 2: return x * x * x * fmaf(x, fmaf(6.f, x, -15.f), 10.f);
+        default: {
+            const float x2 = x * x;
+            return x2 * x2 * fmaf(x, fmaf(x, fmaf(-20.f, x, 70.f), -84.f), 35.f);
+        }
+    }
+}
+/* x and y = 1 - x are both given (each accurate relative to itself) */
+DEV void transform_f(int r, float x, float y, float &t, float &tm, float &w) {
+    const bool lo = x <= y;
+    const float p = phi_poly_f(r, lo ? x : y);
+    const float q = 1.f - p;
+    t = lo ? p : q;
+    tm = lo ? q : p;
+    const float xy = x * y;
+    switch (r) {
+        case 0: w = 1.f; break;
+        case 1: w = 6.f * xy; break;
+        case 2: w = 30.f * xy * xy; break;
+        default: w = 140.f * xy * xy * xy; break;
+    }
+}
+
+DEV uint64_t term_exps_f(const PackedTermF &T) { return *reinterpret_cast<const uint64_t *>(T.e); }
+
+/* Term table of the FP32 path in shared memory (every lane of a warp reads the same term: a broadcast). */
+struct SmemTabF {
+    const PackedTermF *T;
+    DEV float hi(int i) const { return T[i].hi; }
+    DEV float lo(int i) const { return T[i].lo; }
+    DEV uint64_t ex(int i) const { return term_exps_f(T[i]); }
+};
+
+/* coefficient as hi + lo float pair: two FMAs per term keep the coefficient exact to ~2^-48 */
+template <int S, class Tab>
+DEV float poly_rf(const Tab &T, int base, int n, const float *t) {
+    float acc = 0.f;
+    for (int a = base; a < base + n; ++a) {
+        const uint64_t ew = T.ex(a);
+        const float hi = T.hi(a), lo = T.lo(a);
+        if (ew == 0) {
+            acc += hi + lo;
+            continue;
+        }
+        float m = 1.f;
+        bool have = false;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            int e = (int)((ew >> (8 * j)) & 0xffu);
+            if (e > 0) {
+                if (!have) {
+                    m = t[j];
+                    have = true;
+                    --e;
+                }
+                for (int k = 0; k < e; ++k) m *= t[j];
+            }
+        }
+        acc = fmaf(hi, m, fmaf(lo, m, acc));
+    }
+    return acc;
+}
+
+template <int S, class Tab>
+DEV cf poly_cf(const Tab &T, int base, int n, const cf *z) {
+    cf acc = mkf(0.f, 0.f);
+    for (int a = base; a < base + n; ++a) {
+        const uint64_t ew = T.ex(a);
+        const float hi = T.hi(a), lo = T.lo(a);
+        if (ew == 0) {
+            acc.x += hi + lo;
+            continue;
+        }
+        cf m = mkf(1.f, 0.f);
+        bool have = false;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            int e = (int)((ew >> (8 * j)) & 0xffu);
+            if (e > 0) {
+                if (!have) {
+                    m = z[j];
+                    have = true;
+                    --e;
+                }
+                for (int k = 0; k < e; ++k) m = cmulf(m, z[j]);
+            }
+        }
+        acc.x = fmaf(hi, m.x, fmaf(lo, m.x, acc.x));
+        acc.y = fmaf(hi, m.y, fmaf(lo, m.y, acc.y));
+    }
+    return acc;
+}
+
+/* Polynomial evaluators of the FP32 path.  The integrand code below asks an evaluator for
+     UFr(t, U, F)          U~ and F~ at real t (undeformed sectors, Eqs. 7-8),
+     GH(t, g, h)           g_j = dF~/dt_j and h_p = d2F~/dt_j dt_k (p runs over j <= k, row-major upper
+                           triangle) at real t, the inputs of the deformation of Eq. 14,
+     UFc(z, needU, U, F)   U~ (1 when needU is false) and F~ at the deformed complex point z.
+   TabPolF walks the staged term table and decodes each term's exponent bytes.  A generated evaluator
+   (compiled at run time for one family of sector tables) holds every sector's monomials as straight-line code
+   with shared sub-products and reads only the coefficients (hi + lo) from the same staged table. */
+template <int S>
+struct TabPolF {
+    const PackedTermF *T;
+    const PackedSector *s;
+    DEV static TabPolF make(const PackedTermF *T, const PackedSector &s, int) { return TabPolF{T, &s}; }
+    DEV void UFr(const float *t, float &U, float &F) const {
+        const SmemTabF tab{T};
+        U = poly_rf<S>(tab, 0, s->nU, t);
+        F = poly_rf<S>(tab, s->nU, s->nF, t);
+    }
+    DEV void GH(const float *t, float *g, float *h) const {
+        const SmemTabF tab{T};
+        const int bG = s->nU + s->nF, bH = bG + s->nG;
+#pragma unroll
+        for (int j = 0; j < S; ++j) g[j] = poly_rf<S>(tab, bG + s->gstart[j], s->gstart[j + 1] - s->gstart[j], t);
+#pragma unroll
+        for (int p = 0; p < S * (S + 1) / 2; ++p)
+            h[p] = poly_rf<S>(tab, bH + s->hstart[p], s->hstart[p + 1] - s->hstart[p], t);
+    }
+    DEV void UFc(const cf *z, bool needU, cf &U, cf &F) const {
+        const SmemTabF tab{T};
+        U = needU ? poly_cf<S>(tab, 0, s->nU, z) : mkf(1.f, 0.f);
+        F = poly_cf<S>(tab, s->nU, s->nF, z);
+    }
+};
+
+template <int S>
+DEV cf det_deform_f(const float (&A)[S][S], float lam) {
+    if constexpr (S == 1) {
+        return mkf(1.f, -lam * A[0][0]);
+    } else if constexpr (S == 2) {
+        const float tr = A[0][0] + A[1][1];
+        const float dt = fmaf(A[0][0], A[1][1], -A[0][1] * A[1][0]);
+        return mkf(fmaf(-lam * lam, dt, 1.f), -lam * tr);
+    } else if constexpr (S == 3) {
+        const float tr = A[0][0] + A[1][1] + A[2][2];
+        const float e2 = fmaf(A[0][0], A[1][1], -A[0][1] * A[1][0]) + fmaf(A[0][0], A[2][2], -A[0][2] * A[2][0]) +
+                         fmaf(A[1][1], A[2][2], -A[1][2] * A[2][1]);
+        const float dt = A[0][0] * fmaf(A[1][1], A[2][2], -A[1][2] * A[2][1]) -
+                         A[0][1] * fmaf(A[1][0], A[2][2], -A[1][2] * A[2][0]) +
+                         A[0][2] * fmaf(A[1][0], A[2][1], -A[1][1] * A[2][0]);
+        const float l2 = lam * lam;
+        return mkf(fmaf(-l2, e2, 1.f), fmaf(l2 * lam, dt, -lam * tr));
+    } else {
+        cf J[S][S];
+#pragma unroll
+        for (int r = 0; r < S; ++r)
+#pragma unroll
+            for (int c = 0; c < S; ++c) J[r][c] = mkf(r == c ? 1.f : 0.f, -lam * A[r][c]);
+        cf det = mkf(1.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+            int p = c;
+            float best = fabsf(J[c][c].x) + fabsf(J[c][c].y);
+#pragma unroll
+            for (int r = c + 1; r < S; ++r) {
+                const float v = fabsf(J[r][c].x) + fabsf(J[r][c].y);
+                if (v > best) {
+                    best = v;
+                    p = r;
+                }
+            }
+            if (p != c) {
+                det = cscalef(det, -1.f);
+#pragma unroll
+                for (int r = c + 1; r < S; ++r) {
+                    if (r == p) {
+#pragma unroll
+                        for (int k = c; k < S; ++k) {
+                            const cf tmp = J[c][k];
+                            J[c][k] = J[r][k];
+                            J[r][k] = tmp;
+                        }
+                    }
+                }
+            }
+            det = cmulf(det, J[c][c]);
+            const cf inv = cinvf(J[c][c]);
+#pragma unroll
+            for (int r = c + 1; r < S; ++r) {
+                const cf f = cmulf(J[r][c], inv);
+#pragma unroll
+                for (int k = c + 1; k < S; ++k) J[r][k] = csubf(J[r][k], cmulf(f, J[c][k]));
+            }
+        }
+        return det;
+    }
+}
+
+/* FP32 sign check: rounding leaves |Im F| ~ 1e-7 |F| where the deformation vanishes; a point fails when
+   Im F(z) exceeds that noise */
+#define QMC_F32_SIGN_NOISE 4e-6f
+
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void eval_G_f(const PackedSector &s, const Pol &P, const float *tt, const float *ttm, const float *Lt, float lam,
+                  int M, const Exps &ex, cf &G0, cf &X, uint32_t &fails) {
+    const float D = s.Df;
+    if constexpr (!DEF) {
+        float U, F;
+        P.UFr(tt, U, F);
+        if (s.kind == 1) F = -F;
+        float g = D * ipowf_(U, ex.eU0) * ipowf_(F, -ex.eF0);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < s.A[j]; ++k) g *= tt[j];
+        G0 = mkf(g, 0.f);
+        X = mkf(0.f, 0.f);
+        if (MAXM > 0 && M > 0) {
+            float x = __logf(ipowf_(U, ex.eU1) * ipowf_(F, -ex.eF1));
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+                if (s.A[j] != -1 && s.B[j] != 0) x = fmaf((float)s.B[j], Lt[j], x);
+            X = mkf(x, 0.f);
+        }
+    } else {
+        float g[S], h[S * (S + 1) / 2];
+        P.GH(tt, g, h);
+        float A[S][S];
+        int p = 0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+#pragma unroll
+            for (int k = j; k < S; ++k) {
+                A[j][k] = tt[j] * ttm[j] * h[p];
+                if (k != j) A[k][j] = tt[k] * ttm[k] * h[p];
+                ++p;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) A[j][j] = fmaf(ttm[j] - tt[j], g[j], A[j][j]);
+        const cf detJ = det_deform_f<S>(A, lam);
+        cf z[S], q[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float d = lam * ttm[j] * g[j];
+            z[j] = mkf(tt[j], -tt[j] * d);
+            q[j] = mkf(1.f, -d);
+        }
+        const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
+        cf U, F;
+        P.UFc(z, needU, U, F);
+        fails += (F.y > QMC_F32_SIGN_NOISE * (fabsf(F.x) + fabsf(F.y))) ? 1u : 0u;
+        cf G = cscalef(detJ, D);
+        if (ex.eU0 != 0) G = cmulf(G, cipowf(U, ex.eU0));
+        G = cmulf(G, cipowf(F, -ex.eF0));
+        bool any_mono = false;
+        float mono = 1.f;
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < s.A[j]; ++k) {
+                mono *= tt[j];
+                any_mono = true;
+            }
+        if (any_mono) G = cscalef(G, mono);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (s.A[j] != 0) G = cmulf(G, cipowf(q[j], s.A[j]));
+        G0 = G;
+        X = mkf(0.f, 0.f);
+        if (MAXM > 0 && M > 0) {
+            cf x = csubf(cscalef(clogf_p(U), (float)ex.eU1), cscalef(clogf_mi0(F), (float)ex.eF1));
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                if (s.B[j] != 0) {
+                    if (s.A[j] != -1) x.x = fmaf((float)s.B[j], Lt[j], x.x);
+                    x = caddf(x, cscalef(clogf_p(q[j]), (float)s.B[j]));
+                }
+            }
+            X = x;
+        }
+    }
+}
+
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void point_integrand_f(const PackedSector &s, const Pol &P, const float *x, const float *y, int r, float lam,
+                           const Exps &ex, cf (&out)[MAXM + 1], uint32_t &fails) {
+    float t[S], tm[S], w = 1.f;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        float wj;
+        transform_f(r, x[j], y[j], t[j], tm[j], wj);
+        w *= wj;
+        bad |= !(t[j] > 0.f) || !(tm[j] > 0.f);
+    }
+#pragma unroll
+    for (int n = 0; n <= MAXM; ++n) out[n] = mkf(0.f, 0.f);
+    if (bad || !(w > 0.f)) return;
+    const int M = s.M;
+    const unsigned smask = (unsigned)s.sing_mask;
+    float Lt[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) Lt[j] = 0.f;
+    if (MAXM > 0 && M > 0) {
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (((smask >> j) & 1u) || s.B[j] != 0) Lt[j] = __logf(t[j]);
+    }
+    unsigned Y = 0;
+    do {
+        float tt[S], ttm[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const bool zj = (Y >> j) & 1u;
+            tt[j] = zj ? 0.f : t[j];
+            ttm[j] = zj ? 1.f : tm[j];
+        }
+        cf G0, X;
+        eval_G_f<S, DEF, MAXM>(s, P, tt, ttm, Lt, lam, M, ex, G0, X, fails);
+        float V[MAXM + 1];
+        V[0] = 1.f;
+#pragma unroll
+        for (int n = 1; n <= MAXM; ++n) V[n] = 0.f;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            if ((smask >> j) & 1u) {
+                const bool inY = (Y >> j) & 1u;
+                const float Bj = (float)s.B[j];
+                float f[MAXM + 1];
+                f[0] = inY ? 1.f / Bj : 0.f;
+                float c = __frcp_rn(t[j]);
+#pragma unroll
+                for (int n = 1; n <= MAXM; ++n) {
+                    f[n] = inY ? -c : c;
+                    c *= Bj * Lt[j] / n;
+                }
+#pragma unroll
+                for (int n = MAXM; n >= 0; --n) {
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k <= n; ++k) acc = fmaf(V[k], f[n - k], acc);
+                    V[n] = acc;
+                }
+            }
+        }
+        cf g = G0;
+#pragma unroll
+        for (int n = 0; n <= MAXM; ++n) {
+            if (n <= M) {
+#pragma unroll
+                for (int k = 0; k + n <= MAXM; ++k)
+                    if (n + k <= M) out[n + k] = caddf(out[n + k], cscalef(g, V[k]));
+                g = cscalef(cmulf(g, X), 1.f / (n + 1));
+            }
+        }
+        Y = (Y - smask) & smask;
+    } while (Y != 0);
+#pragma unroll
+    for (int n = 0; n <= MAXM; ++n) out[n] = cscalef(out[n], w);
+}
+
+/* x = ((r + a) mod n + b)/n and 1 - x = ((n - 1 - (r + a) mod n) + (1 - b))/n, with delta * n = a + b */
+DEV void lattice_f32(uint32_t r, uint32_t a, float b, uint32_t n, float invnf, float &x, float &y) {
+    uint32_t k = r + a;
+    k = k >= n ? k - n : k;
+    x = ((float)k + b) * invnf;
+    y = ((float)(n - 1u - k) + (1.f - b)) * invnf;
+}
+
+DEV void split_shift(double delta, uint32_t n, uint32_t &a, float &b) {
+    const double dn = delta * (double)n;
+    double fl = floor(dn);
+    if (fl >= (double)n) fl = (double)(n - 1u);
+    a = (uint32_t)fl;
+    b = (float)(dn - fl);
+}
+
+/* TwoSum: s + v = (s') + err exactly; the error goes into the compensation term */
+DEV void two_sum_acc(float &s, float &c, float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
+DEV void stage_sector_f(const unsigned char *packed, int64_t sectors_off, int64_t termsf_off, int psec,
+                        unsigned char *smem) {
+    const PackedSector *ps = reinterpret_cast<const PackedSector *>(packed + sectors_off) + psec;
+    const int4 *src = reinterpret_cast<const int4 *>(ps);
+    int4 *dst = reinterpret_cast<int4 *>(smem);
+    constexpr int NS = (int)(sizeof(PackedSector) / 16);
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = src[k];
+    const int nt = ps->n_terms;
+    const int4 *tsrc = reinterpret_cast<const int4 *>(packed + termsf_off) + ps->term0;
+    int4 *tdst = dst + NS;
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) tdst[k] = tsrc[k];
+}
+
+/* ------------------------------------------------------------------ K2: persistent FP32 evaluation */
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void eval_f32_body(const JobTable &jt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_job;
+    __shared__ double s_red[16][2 * (MAXM + 1)];
+    __shared__ uint32_t s_fail[16];
+    const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
+    const PackedTermF *T = reinterpret_cast<const PackedTermF *>(smem + sizeof(PackedSector));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int cur = -1, cur_job = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(jt.counter, 1ull);
+            s_item = it;
+            s_job = it < jt.total_items ? find_job(jt, it) : 0;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= jt.total_items) break;
+        const int jb = s_job;
+        const Job &J = jt.jobs[jb];
+        const long long local = item - J.item_begin;
+        const long long per_sector = (long long)J.m * J.chunks;
+        const int ls = (int)(local / per_sector);
+        const long long rem = local - (long long)ls * per_sector;
+        const int shift = (int)(rem / J.chunks);
+        const long long chunk = rem - (long long)shift * J.chunks;
+        const int psec = J.sector_begin + ls;
+        if (J.sector_prec) {
+            /* mixed pass: items of sectors evaluated in FP64 belong to the other kernel */
+            const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
+            if (J.sector_prec[gps->orig_index] != 1) {
+                __syncthreads();
+                continue;
+            }
+        }
+        if (psec != cur || jb != cur_job) {
+            stage_sector_f(J.packed, J.sectors_off, J.termsf_off, psec, smem);
+            __syncthreads();
+            cur = psec;
+            cur_job = jb;
+        }
+        const Exps ex{J.eU0, J.eU1, J.eF0, J.eF1};
+        const Pol pol = Pol::make(T, sec, psec);
+        const uint32_t n = J.n;
+        const float invnf = 1.f / (float)n;
+        const float lam = (float)J.lambda[sec.orig_index];
+        uint32_t rj[S], aj[S], zs[S];
+        float bj[S];
+        const long long i0 = chunk * (long long)blockDim.x * jt.P + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            split_shift(J.shifts[6 * shift + j], n, aj[j], bj[j]);
+            rj[j] = (uint32_t)(((unsigned long long)i0 * J.z[j]) % n);
+            zs[j] = J.zstep[j];
+        }
+        float acc[2 * (MAXM + 1)], cmp[2 * (MAXM + 1)];
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
+        uint32_t fails = 0;
+        for (int p = 0; p < jt.P; ++p) {
+            const long long i = i0 + (long long)p * blockDim.x;
+            if (i < (long long)n) {
+                float x[S], y[S];
+#pragma unroll
+                for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], n, invnf, x[j], y[j]);
+                cf val[MAXM + 1];
+                point_integrand_f<S, DEF, MAXM>(sec, pol, x, y, jt.r, lam, ex, val, fails);
+#pragma unroll
+                for (int m = 0; m <= MAXM; ++m) {
+                    two_sum_acc(acc[2 * m], cmp[2 * m], val[m].x);
+                    two_sum_acc(acc[2 * m + 1], cmp[2 * m + 1], val[m].y);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const uint32_t v = rj[j] + zs[j];
+                rj[j] = v >= n ? v - n : v;
+            }
+        }
+        /* warp: double-float shuffle tree; warps and items in FP64 */
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) {
+            float s1 = acc[q], c1 = cmp[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float so = __shfl_down_sync(0xffffffffu, s1, off);
+                const float co = __shfl_down_sync(0xffffffffu, c1, off);
+                two_sum_acc(s1, c1, so);
+                c1 += co;
+            }
+            if (lane == 0) s_red[warp][q] = (double)s1 + (double)c1;
+        }
+        uint32_t f = fails;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+        if (lane == 0) s_fail[warp] = f;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            if (q < J.n_slots * 2) {
+                double s2 = 0.0, c2 = 0.0;
+                if (q < 2 * (MAXM + 1))
+                    for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
+                J.partials[local * J.n_slots * 2 + q] = s2 - c2;
+            }
+            if (q == 0) {
+                uint32_t tf = 0;
+                for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
+                J.part_fails[local] = tf;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int S, bool DEF, int MAXM>
+__global__ void __launch_bounds__(256) qmc_eval_kernel_f32(const __grid_constant__ JobTable jt) {
+    eval_f32_body<S, DEF, MAXM, TabPolF<S>>(jt);
+}
+
+/* ------------------------------------------------------------------ K3: FP32-versus-FP64 probe per sector */
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void probe_body(const ProbeArgs &a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[4][4 * (MAXM + 1)];
+    const int psec = a.sector_begin + blockIdx.x;
+    /* FP64 record + terms, then the FP32 terms */
+    stage_sector(a.packed, a.sectors_off, a.terms_off, psec, smem);
+    const PackedSector *gps = reinterpret_cast<const PackedSector *>(a.packed + a.sectors_off) + psec;
+    const int nt = gps->n_terms;
+    unsigned char *smf = smem + sizeof(PackedSector) + (size_t)nt * sizeof(PackedTerm);
+    {
+        const int4 *tsrc = reinterpret_cast<const int4 *>(a.packed + a.termsf_off) + gps->term0;
+        int4 *tdst = reinterpret_cast<int4 *>(smf);
+        for (int k = threadIdx.x; k < nt; k += blockDim.x) tdst[k] = tsrc[k];
+    }
+    __syncthreads();
+    const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
+    const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
+    const PackedTermF *TF = reinterpret_cast<const PackedTermF *>(smf);
+    const Pol pol = Pol::make(TF, sec, psec);
+    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
+    const double lam = a.lambda[sec.orig_index];
+    const float invnf = 1.f / (float)a.n;
+    const unsigned long long stride = a.n_sample >= (int64_t)a.n ? 1ull : (unsigned long long)(a.n / a.n_sample);
+    double acc[4 * (MAXM + 1)];
+#pragma unroll
+    for (int q = 0; q < 4 * (MAXM + 1); ++q) acc[q] = 0.0;
+    uint32_t Rj[S], aj[S];
+    float bj[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        Rj[j] = wrap_threshold(a.shift[j], a.n, a.invn);
+        split_shift(a.shift[j], a.n, aj[j], bj[j]);
+    }
+    uint32_t f64 = 0, f32 = 0;
+    for (long long k = threadIdx.x; k < a.n_sample && (unsigned long long)k * stride < a.n; k += blockDim.x) {
+        const unsigned long long i = (unsigned long long)k * stride;
+        double x[S];
+        float xf[S], yf[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const uint32_t r = (uint32_t)((i * a.z[j]) % a.n);
+            x[j] = fma((double)r, a.invn, a.shift[j]) - (r >= Rj[j] ? 1.0 : 0.0);
+            lattice_f32(r, aj[j], bj[j], a.n, invnf, xf[j], yf[j]);
+        }
+        cd v64[MAXM + 1];
+        cf v32[MAXM + 1];
+        point_integrand<S, DEF, MAXM>(sec, T, x, a.r, lam, ex, v64, f64);
+        point_integrand_f<S, DEF, MAXM>(sec, pol, xf, yf, a.r, (float)lam, ex, v32, f32);
+#pragma unroll
+        for (int n = 0; n <= MAXM; ++n) {
+            const double dr = (double)v32[n].x - v64[n].x, di = (double)v32[n].y - v64[n].y;
+            acc[4 * n] += hypot(v64[n].x, v64[n].y);
+            acc[4 * n + 1] += hypot(dr, di);
+            acc[4 * n + 2] += dr;
+            acc[4 * n + 3] += di;
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4 * (MAXM + 1); ++q) {
+        double v = acc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) s_red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 * a.n_slots) {
+        const int q = threadIdx.x;
+        double v = 0.0;
+        if (q < 4 * (MAXM + 1))
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w][q];
+        a.out[(size_t)sec.orig_index * a.n_slots * 4 + q] = v;
+    }
+}
+
+template <int S, bool DEF, int MAXM>
+__global__ void __launch_bounds__(128) qmc_probe_kernel(ProbeArgs a) {
+    probe_body<S, DEF, MAXM, TabPolF<S>>(a);
+}
+
+/* ------------------------------------------------------------------ per-point values on explicit indices */
+template <int S, bool DEF, int MAXM>
+__global__ void __launch_bounds__(256) qmc_points_kernel(PointArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_sector(a.packed, a.sectors_off, a.terms_off, a.sector, smem);
+    __syncthreads();
+    const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
+    const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
+    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.npts;
+         j += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = (unsigned long long)a.idx[j];
+        double x[S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+            const uint32_t rj = (uint32_t)((i * a.z[d]) % a.n);
+            const double v = fma((double)rj, a.invn, a.shift[d]);
+            x[d] = v >= 1.0 ? v - 1.0 : v;
+        }
+        cd val[MAXM + 1];
+        uint32_t f = 0;
+        point_integrand<S, DEF, MAXM>(sec, T, x, a.r, a.lambda, ex, val, f);
+        for (int n = 0; n < a.n_slots; ++n) {
+            const cd v = n <= MAXM ? val[n < MAXM + 1 ? n : 0] : mk(0.0, 0.0);
+            a.out[(j * a.n_slots + n) * 2] = v.x;
+            a.out[(j * a.n_slots + n) * 2 + 1] = v.y;
+        }
+        a.fails[j] = (int32_t)f;
+    }
+}

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -536,6 +537,7 @@ int pack_table(const Table &t, const double *inv, int n_inv, int order_min, int 
             std::memcpy(out.data() + h.termsf_off + (int64_t)sizeof(PackedTermF) * (w.ps.term0 + k), &pf, sizeof(pf));
         }
     }
+    reinterpret_cast<PackedHeader *>(out.data())->family = qmc_family_key(out.data());
     if (info) {
         std::memset(info, 0, sizeof(*info));
         info->n_sectors = t.n_sectors;
@@ -580,15 +582,47 @@ struct Plan {
     int64_t total_items;
 };
 
+/* Launch shapes chosen by qmc_autotune, per (family, precision, evaluator, lattice-size bucket 2^k >= n); passes
+   that leave both block and points_per_thread at 0 use them. */
+struct TuneKey {
+    uint64_t family;
+    int prec, evaluator, log2n;
+    bool operator<(const TuneKey &o) const {
+        if (family != o.family) return family < o.family;
+        if (prec != o.prec) return prec < o.prec;
+        if (evaluator != o.evaluator) return evaluator < o.evaluator;
+        return log2n < o.log2n;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tuned;
+
+TuneKey tune_key(const PackedHeader *h, const qmc_pass *p) {
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << b) < p->lattice.n) ++b;
+    const int ev = (p->precision == QMC_PREC_MIXED && p->evaluator != QMC_EVAL_TABLE) ? QMC_EVAL_GENERATED : QMC_EVAL_TABLE;
+    return TuneKey{h->family, p->precision, ev, b};
+}
+
 int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
     if (!h || !p) return QMC_ERR_ARG;
     if (p->lattice.n < 2 || p->lattice.n >= ((int64_t)1 << 31)) return QMC_ERR_ARG;
     if (p->n_shifts < 1 || p->n_shifts > 4096) return QMC_ERR_ARG;
     if (p->transform_r < 0 || p->transform_r > 3) return QMC_ERR_ARG;
     if (p->precision != QMC_PREC_FP64 && p->precision != QMC_PREC_MIXED) return QMC_ERR_ARG;
-    pl.block = p->block ? p->block : 128;
+    if (p->evaluator < QMC_EVAL_AUTO || p->evaluator > QMC_EVAL_GENERATED) return QMC_ERR_ARG;
+    int block = p->block, P = p->points_per_thread;
+    if (block == 0 && P == 0) {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tuned.find(tune_key(h, p));
+        if (it != g_tuned.end()) {
+            block = it->second.first;
+            P = it->second.second;
+        }
+    }
+    pl.block = block ? block : 128;
     if (pl.block < 32 || pl.block > 256 || pl.block % 32) return QMC_ERR_ARG;
-    pl.P = p->points_per_thread ? p->points_per_thread : (p->precision == QMC_PREC_MIXED ? 16 : 8);
+    pl.P = P ? P : (p->precision == QMC_PREC_MIXED ? 16 : 8);
     if (pl.P < 1 || pl.P > 64) return QMC_ERR_ARG;
     for (int j = 0; j < h->dim; ++j)
         if (p->lattice.z[j] == 0 || (int64_t)p->lattice.z[j] >= p->lattice.n) return QMC_ERR_ARG;
@@ -642,6 +676,7 @@ const char *qmc_strerror(int s) {
         case QMC_ERR_NOT_FOUND: return "unknown id";
         case QMC_ERR_NO_DEVICE: return "no CUDA device";
         case QMC_ERR_NOT_CONVERGED: return "lattice ladder exhausted before the requested accuracy";
+        case QMC_ERR_CODEGEN: return "run-time compilation of the generated evaluator failed";
         default: return "unknown status";
     }
 }
@@ -735,15 +770,19 @@ int check_items(const qmc_batch_item *items, int n, bool need_eval_inputs, bool 
     return QMC_OK;
 }
 
+/* gen: kernel handle of a generated evaluator (FP32 jobs of one family), null for the ahead-of-time kernels */
 struct LaunchKey {
     int dim, deform, maxm, prec, block, P, r;
+    const void *gen;
     bool operator<(const LaunchKey &o) const {
         const int a[7] = {dim, deform, maxm, prec, block, P, r}, b[7] = {o.dim, o.deform, o.maxm, o.prec, o.block, o.P, o.r};
         for (int k = 0; k < 7; ++k)
             if (a[k] != b[k]) return a[k] < b[k];
-        return false;
+        return std::less<const void *>()(gen, o.gen);
     }
 };
+
+bool use_generated(const qmc_pass &p) { return p.precision == QMC_PREC_MIXED && p.evaluator != QMC_EVAL_TABLE; }
 
 /* Evaluation launches of a batch: every (pass, class, precision) becomes a job; jobs sharing a kernel
    instantiation and launch shape go into one persistent launch (tables of up to QMC_MAX_JOBS jobs). */
@@ -793,8 +832,13 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
                 J.eU1 = h->eU1;
                 J.eF0 = h->eF0;
                 J.eF1 = h->eF1;
+                const void *gen = nullptr;
+                if (prec == 1 && use_generated(b.pass)) {
+                    rc = qmc_gen_kernel(b.packed_host, c, &gen);
+                    if (rc) return rc;
+                }
                 const LaunchKey key{h->dim, c, class_maxm(h, c), prec == 0 ? QMC_PREC_FP64 : QMC_PREC_MIXED, pl.block,
-                                    pl.P, b.pass.transform_r};
+                                    pl.P, b.pass.transform_r, gen};
                 groups[key].push_back(J);
                 const int need = (int)(sizeof(PackedSector) + (size_t)h->max_terms * sizeof(PackedTerm));
                 smem_need[key] = std::max(smem_need[key], need);
@@ -824,14 +868,16 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
             jt->counter = counters + counter++;
             jt->smem_bytes = smem_need[k];
             int per_sm = 0;
-            rc = qmc_eval_blocks_per_sm(k.dim, k.deform, k.maxm, k.prec, k.block, jt->smem_bytes, &per_sm);
+            rc = k.gen ? qmc_gen_blocks_per_sm(k.gen, k.block, jt->smem_bytes, &per_sm)
+                       : qmc_eval_blocks_per_sm(k.dim, k.deform, k.maxm, k.prec, k.block, jt->smem_bytes, &per_sm);
             if (rc) return rc;
             if (per_sm < 1) return QMC_ERR_UNSUPPORTED;
             int64_t grid = (int64_t)sms * per_sm;
             for (int i = 0; i < n; ++i)
                 if (items[i].pass.grid > 0) grid = std::min<int64_t>(grid, items[i].pass.grid);
             if (grid > total) grid = total;
-            rc = qmc_launch_eval(k.dim, k.deform, k.maxm, k.prec, *jt, (int)grid, k.block, stream);
+            rc = k.gen ? qmc_gen_launch_eval(k.gen, *jt, (int)grid, k.block, stream)
+                       : qmc_launch_eval(k.dim, k.deform, k.maxm, k.prec, *jt, (int)grid, k.block, stream);
             if (rc) return rc;
         }
     }
@@ -1010,6 +1056,84 @@ int qmc_eval_sums(const void *packed_host, const void *packed_dev, const qmc_pas
                   int64_t *fails_dev, void *stream) {
     const qmc_batch_item b = single_item(packed_host, packed_dev, pass, shifts_dev, lambda_dev, sums_dev, fails_dev);
     return qmc_eval_batch(&b, 1, scratch_dev, scratch_bytes, stream);
+}
+
+/* ------------------------------------------------------------------ launch-shape autotuner */
+static const int k_tune_block[] = {64, 128, 256};
+static const int k_tune_P[] = {4, 8, 16, 32};
+
+size_t qmc_autotune_scratch_bytes(const void *packed_host, const qmc_pass *pass) {
+    if (!header_of(packed_host) || !pass) return 0;
+    size_t need = 0;
+    for (int b : k_tune_block)
+        for (int P : k_tune_P) {
+            qmc_pass q = *pass;
+            q.block = b;
+            q.points_per_thread = P;
+            const size_t s = qmc_scratch_bytes(packed_host, &q);
+            if (!s) return 0;
+            need = std::max(need, s);
+        }
+    return need;
+}
+
+int qmc_autotune(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shifts_dev,
+                 const double *lambda_dev, void *scratch_dev, size_t scratch_bytes, qmc_tune_result *out,
+                 void *stream) {
+    const PackedHeader *h = header_of(packed_host);
+    if (!h || !pass || !out) return QMC_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    if (scratch_bytes < qmc_autotune_scratch_bytes(packed_host, pass)) return QMC_ERR_MEMORY;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return QMC_ERR_CUDA;
+    int rc = QMC_OK;
+    float best = -1.f;
+    bool warm = false;
+    for (int b : k_tune_block)
+        for (int P : k_tune_P) {
+            if (rc) break;
+            qmc_pass q = *pass;
+            q.block = b;
+            q.points_per_thread = P;
+            if (!warm) { /* first launch of the kernel (module load, attributes) stays out of the timings */
+                rc = qmc_eval_partials(packed_host, packed_dev, &q, shifts_dev, lambda_dev, scratch_dev, scratch_bytes,
+                                       stream);
+                warm = true;
+                if (rc) break;
+            }
+            rc = cuda_status(cudaEventRecord(e0, st));
+            if (!rc)
+                rc = qmc_eval_partials(packed_host, packed_dev, &q, shifts_dev, lambda_dev, scratch_dev, scratch_bytes,
+                                       stream);
+            if (!rc) rc = cuda_status(cudaEventRecord(e1, st));
+            if (!rc) rc = cuda_status(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            if (!rc) rc = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+            if (rc) break;
+            const int k = out->n_candidates++;
+            out->candidate_block[k] = b;
+            out->candidate_points_per_thread[k] = P;
+            out->candidate_ms[k] = ms;
+            if (best < 0.f || ms < best) {
+                best = ms;
+                out->block = b;
+                out->points_per_thread = P;
+                out->ms = ms;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tuned[tune_key(h, pass)] = {out->block, out->points_per_thread};
+    return QMC_OK;
+}
+
+int qmc_autotune_clear(void) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tuned.clear();
+    return QMC_OK;
 }
 
 int qmc_eval_points(const void *packed_host, const void *packed_dev, int32_t sector, const qmc_pass *pass,
@@ -1352,6 +1476,7 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
         pass.precision = opt->precision;
         pass.block = opt->block;
         pass.points_per_thread = opt->points_per_thread;
+        pass.evaluator = opt->evaluator;
         pass.sector_precision = mixed ? (const int32_t *)c->prec.p : nullptr;
         const size_t need = qmc_scratch_bytes(I.packed.data(), &pass);
         if (!need) return res->status = QMC_ERR_ARG;
@@ -1610,6 +1735,7 @@ qmc_pass pass_of(const Request &r) {
     p.precision = r.opt.precision;
     p.block = r.opt.block;
     p.points_per_thread = r.opt.points_per_thread;
+    p.evaluator = r.opt.evaluator;
     p.sector_precision = r.opt.precision == QMC_PREC_MIXED ? (const int32_t *)r.dprec.p : nullptr;
     return p;
 }

@@ -38,6 +38,8 @@ struct PackedHeader {
     double flops_per_eval, transc_per_eval;
     int32_t n_deformed, n_negative, max_sigma, reserved;
     int64_t termsf_off;
+    uint64_t family;                      /* hash of everything the generated evaluators depend on (exponents) */
+    int64_t reserved2;
 };
 
 struct PackedSector {
@@ -172,3 +174,11 @@ int qmc_launch_points(int dim, int deform, int maxm, int precision, const PointA
 int qmc_device_sm_count(int *sms);
 int qmc_eval_blocks_per_sm(int dim, int deform, int maxm, int precision, int block, int smem_bytes, int *out);
 int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *stream);
+
+/* Generated evaluators (qmc_jit.cpp): the FP32 evaluation kernel of a family's module for sector class cls
+   (compiled and loaded on first use), its occupancy and launch.  Kernel handles are cudaKernel_t values passed
+   as const void *. */
+int qmc_gen_kernel(const void *packed_host, int cls, const void **eval_kernel);
+uint64_t qmc_family_key(const void *packed_host); /* computed from the image, not read from its header */
+int qmc_gen_blocks_per_sm(const void *kernel, int block, int smem_bytes, int *out);
+int qmc_gen_launch_eval(const void *kernel, const JobTable &t, int grid, int block, void *stream);

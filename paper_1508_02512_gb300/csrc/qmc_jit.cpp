@@ -1,0 +1,514 @@
+/*
+ * Generated polynomial evaluators for the FP32 pass (run-time code generation with NVRTC).
+ *
+ * The sector integrand of Eqs. 7-9 and 14 is dominated by polynomial evaluation: U~, F~ and, for deformed
+ * sectors, the S gradient and S(S+1)/2 Hessian polynomials of F~ (Eq. 14 and its Jacobian), at real t or at
+ * the complex point z.  The table evaluator of the kernels walks the staged terms and decodes each term's
+ * exponent bytes on every point, which costs far more integer instructions than the FP32 arithmetic itself.
+ * The exponents of a sector table depend only on the topology and on the kinematic class (which invariants
+ * vanish); the coefficients depend on the kinematic point.  So, once per family of tables, this file writes
+ * every sector's monomials as straight-line CUDA: each distinct monomial is formed once, as its parent
+ * monomial times one variable (the parent drops one power of the highest-index variable, so the factors are
+ * multiplied in the same order as in the table evaluator), and every term adds coefficient x monomial to its
+ * polynomial with the same two FMAs (coefficient hi + lo) as the table evaluator.  Coefficients are still read
+ * from the sector's staged term table, so a new kinematic point of the same family reuses the compiled code.
+ *
+ * The generated source includes the kernel templates of qmc_dev.cuh (embedded into this library at build
+ * time) and instantiates, for each sector class of the family, the persistent FP32 evaluation kernel with the
+ * generated evaluator (the FP32/FP64 probe keeps the table evaluator: it only samples a few thousand points).  NVRTC compiles it for sm_103a; the cubin is loaded with the
+ * runtime's library API and launched through its kernel handles.  Modules are cached per family for the life
+ * of the process.
+ */
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qmc_internal.h"
+#include "qmc_jit_sources.h" /* generated at build time: the device headers as string literals */
+
+namespace {
+
+#define QMC_JIT_GENERATOR_VERSION 2u
+#define QMC_GEN_INLINE_TERMS 2048 /* families with more terms get out-of-line sector functions */
+
+const PackedHeader *hdr(const void *p) {
+    const PackedHeader *h = static_cast<const PackedHeader *>(p);
+    return (h && h->magic == QMC_PACK_MAGIC) ? h : nullptr;
+}
+
+int maxm_of(const PackedHeader *h, int c) { return h->class_maxm[c] == 0 ? 0 : (h->class_maxm[c] <= 2 ? 2 : 4); }
+
+const PackedSector *sectors(const PackedHeader *h) {
+    return reinterpret_cast<const PackedSector *>(reinterpret_cast<const unsigned char *>(h) + h->sectors_off);
+}
+const PackedTermF *terms_f(const PackedHeader *h) {
+    return reinterpret_cast<const PackedTermF *>(reinterpret_cast<const unsigned char *>(h) + h->termsf_off);
+}
+
+/* ---------------------------------------------------------------- family key (what the generated code depends on) */
+struct Fnv {
+    uint64_t v = 1469598103934665603ull;
+    void add(const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) {
+            v ^= b[i];
+            v *= 1099511628211ull;
+        }
+    }
+    void add_i(int64_t x) { add(&x, sizeof(x)); }
+};
+
+uint64_t family_key(const PackedHeader *h) {
+    Fnv f;
+    f.add_i(QMC_JIT_GENERATOR_VERSION);
+    f.add_i(h->dim);
+    f.add_i(h->n_sectors);
+    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+        f.add_i(h->class_begin[c]);
+        f.add_i(h->class_end[c]);
+        f.add_i(maxm_of(h, c));
+    }
+    const PackedSector *ps = sectors(h);
+    const PackedTermF *tf = terms_f(h);
+    for (int s = 0; s < h->n_sectors; ++s) {
+        const PackedSector &p = ps[s];
+        f.add_i(p.nU);
+        f.add_i(p.nF);
+        f.add_i(p.nG);
+        f.add_i(p.nH);
+        f.add(p.gstart, sizeof(p.gstart));
+        f.add(p.hstart, sizeof(p.hstart));
+        for (int k = 0; k < p.n_terms; ++k) f.add(tf[p.term0 + k].e, 8);
+    }
+    return f.v;
+}
+
+/* ---------------------------------------------------------------- code generation */
+struct Entry {
+    int acc;   /* accumulator (polynomial) */
+    int term;  /* term index within the sector */
+};
+
+using Key = uint64_t; /* exponents packed 4 bits per variable */
+
+Key key_of(const uint8_t *e, int S) {
+    Key k = 0;
+    for (int j = 0; j < S; ++j) k |= (Key)(e[j] & 15u) << (4 * j);
+    return k;
+}
+int exp_of(Key k, int j) { return (int)((k >> (4 * j)) & 15u); }
+int top_var(Key k, int S) {
+    for (int j = S - 1; j >= 0; --j)
+        if (exp_of(k, j)) return j;
+    return -1;
+}
+
+struct PolySet {
+    int S = 0;
+    bool complex_ = false;
+    int n_acc = 0;
+    std::vector<Entry> constants;
+    std::map<Key, std::vector<Entry>> mono; /* every needed monomial (terms' and their parents), key -> terms */
+};
+
+void add_term(PolySet &P, int acc, int term, const uint8_t *e) {
+    Key k = key_of(e, P.S);
+    if (k == 0) {
+        P.constants.push_back({acc, term});
+        return;
+    }
+    P.mono[k].push_back({acc, term});
+    /* parents: drop one power of the highest variable until degree 1 */
+    for (;;) {
+        const int j = top_var(k, P.S);
+        const Key par = k - ((Key)1 << (4 * j));
+        if (par == 0 || P.mono.count(par)) break;
+        P.mono[par];
+        k = par;
+    }
+}
+
+void emit_fma(std::string &o, const PolySet &P, const Entry &E, const std::string &m, const std::string &ind) {
+    char b[256];
+    if (!P.complex_) {
+        std::snprintf(b, sizeof(b), "%sa%d = fmaf(C[%d].hi, %s, fmaf(C[%d].lo, %s, a%d));\n", ind.c_str(), E.acc,
+                      E.term, m.c_str(), E.term, m.c_str(), E.acc);
+    } else {
+        std::snprintf(b, sizeof(b),
+                      "%sa%d.x = fmaf(C[%d].hi, %s.x, fmaf(C[%d].lo, %s.x, a%d.x)); "
+                      "a%d.y = fmaf(C[%d].hi, %s.y, fmaf(C[%d].lo, %s.y, a%d.y));\n",
+                      ind.c_str(), E.acc, E.term, m.c_str(), E.term, m.c_str(), E.acc, E.acc, E.term, m.c_str(),
+                      E.term, m.c_str(), E.acc);
+    }
+    o += b;
+}
+
+void emit_node(std::string &o, const PolySet &P, Key k, const std::string &parent, int depth, int &id) {
+    const int j = top_var(k, P.S);
+    const std::string ind(4 + 2 * depth, ' ');
+    const std::string name = "m" + std::to_string(id++);
+    const std::string var = (P.complex_ ? "z[" : "t[") + std::to_string(j) + "]";
+    o += ind + "{\n";
+    if (parent.empty())
+        o += ind + "  const " + (P.complex_ ? "cf " : "float ") + name + " = " + var + ";\n";
+    else if (P.complex_)
+        o += ind + "  const cf " + name + " = cmulf(" + parent + ", " + var + ");\n";
+    else
+        o += ind + "  const float " + name + " = " + parent + " * " + var + ";\n";
+    for (const Entry &E : P.mono.at(k)) emit_fma(o, P, E, name, ind + "  ");
+    for (int jj = j; jj < P.S; ++jj) {
+        const Key ch = k + ((Key)1 << (4 * jj));
+        if (exp_of(k, jj) >= 15) continue;
+        if (P.mono.count(ch)) emit_node(o, P, ch, name, depth + 1, id);
+    }
+    o += ind + "}\n";
+}
+
+void emit_body(std::string &o, const PolySet &P) {
+    for (int a = 0; a < P.n_acc; ++a)
+        o += P.complex_ ? "    cf a" + std::to_string(a) + " = mkf(0.f, 0.f);\n"
+                        : "    float a" + std::to_string(a) + " = 0.f;\n";
+    for (const Entry &E : P.constants) {
+        char b[160];
+        std::snprintf(b, sizeof(b), P.complex_ ? "    a%d.x += C[%d].hi + C[%d].lo;\n" : "    a%d += C[%d].hi + C[%d].lo;\n",
+                      E.acc, E.term, E.term);
+        o += b;
+    }
+    int id = 0;
+    for (int j = 0; j < P.S; ++j) {
+        const Key k = (Key)1 << (4 * j);
+        if (P.mono.count(k)) emit_node(o, P, k, "", 0, id);
+    }
+}
+
+/* source of one family: per-sector functions, the evaluator and the kernels of every class present */
+std::string generate(const PackedHeader *h) {
+    const int S = h->dim;
+    const int NP = S * (S + 1) / 2;
+    const PackedSector *ps = sectors(h);
+    const PackedTermF *tf = terms_f(h);
+    std::string o;
+    o.reserve(1 << 20);
+    char b[512];
+    std::snprintf(b, sizeof(b),
+                  "/* generated: polynomial evaluators of one family of %d-dimensional sector tables (%d sectors) */\n"
+                  "#include \"qmc_dev.cuh\"\n\n",
+                  S, h->n_sectors);
+    o += b;
+    std::vector<int> cls(h->n_sectors, -1);
+    for (int c = 0; c < QMC_N_CLASSES; ++c)
+        for (int s = h->class_begin[c]; s < h->class_end[c]; ++s) cls[s] = c;
+    /* Small families are inlined into the kernels.  Large ones get one non-inlined function per sector and
+       polynomial set (arguments and results by value, so they stay in registers): ptxas then compiles each
+       function on its own, which keeps compilation time linear in the family size. */
+    const bool out_of_line = h->n_terms_total > QMC_GEN_INLINE_TERMS;
+    std::string targs, tvals, zargs, zvals, tcall, zcall;
+    for (int j = 0; j < S; ++j) {
+        const std::string J = std::to_string(j);
+        targs += ", float t" + J;
+        tvals += (j ? ", t" : "t") + J;
+        zargs += ", float z" + J + "r, float z" + J + "i";
+        zvals += (j ? ", mkf(z" : "mkf(z") + J + "r, z" + J + "i)";
+        tcall += ", t[" + J + "]";
+        zcall += ", z[" + J + "].x, z[" + J + "].y";
+    }
+    if (out_of_line) {
+        std::snprintf(b, sizeof(b),
+                      "struct QgR { float U, F; };\nstruct QgC { cf U, F; };\nstruct QgGH { float g[%d], h[%d]; };\n\n",
+                      S, NP);
+        o += b;
+    }
+    auto head = [&](const char *kind, int s) {
+        const std::string n = std::to_string(s);
+        if (!out_of_line) {
+            if (!std::strcmp(kind, "ufr"))
+                return "DEV void qg_ufr_" + n + "(const PackedTermF *__restrict__ C, const float *t, float &U, float &F) {\n";
+            if (!std::strcmp(kind, "gh"))
+                return "DEV void qg_gh_" + n + "(const PackedTermF *__restrict__ C, const float *t, float *g, float *h) {\n";
+            return "DEV void qg_ufc_" + n + "(const PackedTermF *__restrict__ C, const cf *z, cf &U, cf &F) {\n";
+        }
+        if (!std::strcmp(kind, "ufr"))
+            return "__device__ __noinline__ QgR qg_ufr_" + n + "(const PackedTermF *__restrict__ C" + targs +
+                   ") {\n    const float t[] = {" + tvals + "};\n";
+        if (!std::strcmp(kind, "gh"))
+            return "__device__ __noinline__ QgGH qg_gh_" + n + "(const PackedTermF *__restrict__ C" + targs +
+                   ") {\n    const float t[] = {" + tvals + "};\n";
+        return "__device__ __noinline__ QgC qg_ufc_" + n + "(const PackedTermF *__restrict__ C" + zargs +
+               ") {\n    const cf z[] = {" + zvals + "};\n";
+    };
+    for (int s = 0; s < h->n_sectors; ++s) {
+        const PackedSector &p = ps[s];
+        const PackedTermF *T = tf + p.term0;
+        if (cls[s] == 0) {
+            PolySet P;
+            P.S = S;
+            P.n_acc = 2;
+            for (int k = 0; k < p.nU; ++k) add_term(P, 0, k, T[k].e);
+            for (int k = 0; k < p.nF; ++k) add_term(P, 1, p.nU + k, T[p.nU + k].e);
+            o += head("ufr", s);
+            emit_body(o, P);
+            o += out_of_line ? "    return QgR{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+        } else if (cls[s] == 1) {
+            PolySet P;
+            P.S = S;
+            P.n_acc = S + NP;
+            const int bG = p.nU + p.nF, bH = bG + p.nG;
+            for (int j = 0; j < S; ++j)
+                for (int k = bG + p.gstart[j]; k < bG + p.gstart[j + 1]; ++k) add_term(P, j, k, T[k].e);
+            for (int q = 0; q < NP; ++q)
+                for (int k = bH + p.hstart[q]; k < bH + p.hstart[q + 1]; ++k) add_term(P, S + q, k, T[k].e);
+            o += head("gh", s);
+            emit_body(o, P);
+            const char *gv = out_of_line ? "    r.g[" : "    g[";
+            const char *hv = out_of_line ? "    r.h[" : "    h[";
+            if (out_of_line) o += "    QgGH r;\n";
+            for (int j = 0; j < S; ++j) o += gv + std::to_string(j) + "] = a" + std::to_string(j) + ";\n";
+            for (int q = 0; q < NP; ++q) o += hv + std::to_string(q) + "] = a" + std::to_string(S + q) + ";\n";
+            o += out_of_line ? "    return r;\n}\n" : "}\n";
+            PolySet Q;
+            Q.S = S;
+            Q.complex_ = true;
+            Q.n_acc = 2;
+            for (int k = 0; k < p.nU; ++k) add_term(Q, 0, k, T[k].e);
+            for (int k = 0; k < p.nF; ++k) add_term(Q, 1, p.nU + k, T[p.nU + k].e);
+            o += head("ufc", s);
+            emit_body(o, Q);
+            o += out_of_line ? "    return QgC{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+        }
+    }
+    /* the evaluator: a warp-uniform switch over the packed sector index */
+    o += "\nstruct QgPol {\n    const PackedTermF *T;\n    int sec;\n"
+         "    DEV static QgPol make(const PackedTermF *T, const PackedSector &, int psec) { return QgPol{T, psec}; }\n";
+    o += "    DEV void UFr(const float *t, float &U, float &F) const {\n        switch (sec) {\n";
+    for (int s = 0; s < h->n_sectors; ++s)
+        if (cls[s] == 0) {
+            const std::string n = std::to_string(s);
+            o += out_of_line ? "        case " + n + ": { const QgR r = qg_ufr_" + n + "(T" + tcall + "); U = r.U; F = r.F; return; }\n"
+                             : "        case " + n + ": qg_ufr_" + n + "(T, t, U, F); return;\n";
+        }
+    o += "        default: U = 0.f; F = 0.f;\n        }\n    }\n";
+    o += "    DEV void GH(const float *t, float *g, float *h) const {\n        switch (sec) {\n";
+    for (int s = 0; s < h->n_sectors; ++s)
+        if (cls[s] == 1) {
+            const std::string n = std::to_string(s);
+            o += out_of_line ? "        case " + n + ": { const QgGH r = qg_gh_" + n + "(T" + tcall +
+                                   "); for (int j = 0; j < " + std::to_string(S) + "; ++j) g[j] = r.g[j]; for (int q = 0; q < " +
+                                   std::to_string(NP) + "; ++q) h[q] = r.h[q]; return; }\n"
+                             : "        case " + n + ": qg_gh_" + n + "(T, t, g, h); return;\n";
+        }
+    std::snprintf(b, sizeof(b),
+                  "        default:\n            for (int j = 0; j < %d; ++j) g[j] = 0.f;\n"
+                  "            for (int q = 0; q < %d; ++q) h[q] = 0.f;\n        }\n    }\n",
+                  S, NP);
+    o += b;
+    o += "    DEV void UFc(const cf *z, bool, cf &U, cf &F) const {\n        switch (sec) {\n";
+    for (int s = 0; s < h->n_sectors; ++s)
+        if (cls[s] == 1) {
+            const std::string n = std::to_string(s);
+            o += out_of_line ? "        case " + n + ": { const QgC r = qg_ufc_" + n + "(T" + zcall + "); U = r.U; F = r.F; return; }\n"
+                             : "        case " + n + ": qg_ufc_" + n + "(T, z, U, F); return;\n";
+        }
+    o += "        default: U = mkf(0.f, 0.f); F = mkf(0.f, 0.f);\n        }\n    }\n};\n\n";
+    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+        if (h->class_end[c] <= h->class_begin[c]) continue;
+        const char *def = c == 1 ? "true" : "false";
+        const int mm = maxm_of(h, c);
+        std::snprintf(b, sizeof(b),
+                      "extern \"C\" __global__ void __launch_bounds__(256) qg_eval_c%d(const __grid_constant__ JobTable jt) {\n"
+                      "    eval_f32_body<%d, %s, %d, QgPol>(jt);\n}\n",
+                      c, S, def, mm);
+        o += b;
+    }
+    return o;
+}
+
+/* ---------------------------------------------------------------- NVRTC */
+const char *k_stdint =
+    "#pragma once\n"
+    "typedef signed char int8_t; typedef short int16_t; typedef int int32_t; typedef long int64_t;\n"
+    "typedef unsigned char uint8_t; typedef unsigned short uint16_t; typedef unsigned int uint32_t;\n"
+    "typedef unsigned long uint64_t; typedef long intptr_t; typedef unsigned long uintptr_t;\n";
+const char *k_stddef = "#pragma once\n";
+
+struct Compiled {
+    std::vector<char> cubin;
+    std::string log;
+    double ms = 0.0;
+    size_t source_bytes = 0;
+};
+
+int compile(const std::string &src, Compiled &out) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const char *headers[] = {k_stdint, k_stddef, qmc_src_qmcfi_h, qmc_src_qmc_internal_h, qmc_src_qmc_dev_cuh};
+    const char *names[] = {"stdint.h", "stddef.h", "../../include/qmcfi.h", "qmc_internal.h", "qmc_dev.cuh"};
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "qmc_generated.cu", 5, headers, names) != NVRTC_SUCCESS)
+        return QMC_ERR_CODEGEN;
+    /* -default-device: the C-ABI declarations of the included headers become (unused) device declarations */
+    const char *opts[] = {"-arch=sm_103a", "-std=c++17", "-default-device", "-DQMC_GENERATED=1"};
+    const nvrtcResult r = nvrtcCompileProgram(prog, 4, opts);
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    if (ls > 1) {
+        out.log.resize(ls);
+        nvrtcGetProgramLog(prog, &out.log[0]);
+    }
+    int rc = QMC_OK;
+    if (r != NVRTC_SUCCESS) {
+        rc = QMC_ERR_CODEGEN;
+    } else {
+        size_t cs = 0;
+        if (nvrtcGetCUBINSize(prog, &cs) != NVRTC_SUCCESS || cs == 0) {
+            rc = QMC_ERR_CODEGEN;
+        } else {
+            out.cubin.resize(cs);
+            if (nvrtcGetCUBIN(prog, out.cubin.data()) != NVRTC_SUCCESS) rc = QMC_ERR_CODEGEN;
+        }
+    }
+    nvrtcDestroyProgram(&prog);
+    out.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    out.source_bytes = src.size();
+    if (rc) std::fprintf(stderr, "qmcfi: generated-code compilation failed:\n%.4000s\n", out.log.c_str());
+    return rc;
+}
+
+/* ---------------------------------------------------------------- module cache */
+struct Module {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t eval[QMC_N_CLASSES] = {nullptr, nullptr};
+    double compile_ms = 0.0;
+    int64_t source_bytes = 0, cubin_bytes = 0;
+};
+
+std::mutex g_mu;
+std::map<uint64_t, std::unique_ptr<Module>> g_modules;
+
+int get_module(const PackedHeader *h, const Module **out, bool *was_cached) {
+    const uint64_t key = family_key(h);
+    std::lock_guard<std::mutex> g(g_mu);
+    auto it = g_modules.find(key);
+    if (it != g_modules.end()) {
+        *out = it->second.get();
+        if (was_cached) *was_cached = true;
+        return QMC_OK;
+    }
+    if (was_cached) *was_cached = false;
+    Compiled cc;
+    int rc = compile(generate(h), cc);
+    if (rc) return rc;
+    std::unique_ptr<Module> m(new Module());
+    if (cudaLibraryLoadData(&m->lib, cc.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+        if (h->class_end[c] <= h->class_begin[c]) continue;
+        const std::string e = "qg_eval_c" + std::to_string(c);
+        if (cudaLibraryGetKernel(&m->eval[c], m->lib, e.c_str()) != cudaSuccess) {
+            cudaLibraryUnload(m->lib);
+            return QMC_ERR_CUDA;
+        }
+    }
+    m->compile_ms = cc.ms;
+    m->source_bytes = (int64_t)cc.source_bytes;
+    m->cubin_bytes = (int64_t)cc.cubin.size();
+    *out = m.get();
+    g_modules[key] = std::move(m);
+    return QMC_OK;
+}
+
+}  // namespace
+
+/* ---------------------------------------------------------------- internal interface (qmc_internal.h) */
+uint64_t qmc_family_key(const void *packed_host) {
+    const PackedHeader *h = hdr(packed_host);
+    return h ? family_key(h) : 0;
+}
+
+int qmc_gen_kernel(const void *packed_host, int cls, const void **eval_kernel) {
+    const PackedHeader *h = hdr(packed_host);
+    if (!h || !eval_kernel || cls < 0 || cls >= QMC_N_CLASSES) return QMC_ERR_ARG;
+    const Module *m = nullptr;
+    const int rc = get_module(h, &m, nullptr);
+    if (rc) return rc;
+    if (!m->eval[cls]) return QMC_ERR_ARG;
+    *eval_kernel = reinterpret_cast<const void *>(m->eval[cls]);
+    return QMC_OK;
+}
+
+int qmc_gen_blocks_per_sm(const void *kernel, int block, int smem_bytes, int *out) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kernel, block, smem_bytes) == cudaSuccess ? QMC_OK
+                                                                                                       : QMC_ERR_CUDA;
+}
+
+int qmc_gen_launch_eval(const void *kernel, const JobTable &t, int grid, int block, void *stream) {
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem_bytes) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    void *args[] = {const_cast<JobTable *>(&t)};
+    return cudaLaunchKernel(kernel, dim3(grid), dim3(block), args, (size_t)t.smem_bytes, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? QMC_OK
+               : QMC_ERR_CUDA;
+}
+
+/* ---------------------------------------------------------------- public entry points */
+extern "C" {
+
+int qmc_gen_source(const void *packed_host, char *buf, size_t cap, size_t *len) {
+    const PackedHeader *h = hdr(packed_host);
+    if (!h) return QMC_ERR_ARG;
+    try {
+        const std::string s = generate(h);
+        if (len) *len = s.size() + 1;
+        if (buf) {
+            if (cap < s.size() + 1) return QMC_ERR_MEMORY;
+            std::memcpy(buf, s.c_str(), s.size() + 1);
+        }
+        return QMC_OK;
+    } catch (const std::bad_alloc &) {
+        return QMC_ERR_MEMORY;
+    }
+}
+
+int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info) {
+    const PackedHeader *h = hdr(packed_host);
+    if (!h) return QMC_ERR_ARG;
+    try {
+        if (info) std::memset(info, 0, sizeof(*info));
+        if (info) info->family = family_key(h);
+        if (!load) {
+            const std::string src = generate(h);
+            Compiled cc;
+            const int rc = compile(src, cc);
+            if (info) {
+                info->compile_ms = cc.ms;
+                info->source_bytes = (int64_t)cc.source_bytes;
+                info->cubin_bytes = (int64_t)cc.cubin.size();
+            }
+            return rc;
+        }
+        const Module *m = nullptr;
+        bool cached = false;
+        const int rc = get_module(h, &m, &cached);
+        if (rc) return rc;
+        if (info) {
+            info->compile_ms = m->compile_ms;
+            info->source_bytes = m->source_bytes;
+            info->cubin_bytes = m->cubin_bytes;
+            info->cached = cached ? 1 : 0;
+        }
+        return QMC_OK;
+    } catch (const std::bad_alloc &) {
+        return QMC_ERR_MEMORY;
+    }
+}
+
+}  // extern "C"

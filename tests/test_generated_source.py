@@ -1,0 +1,233 @@
+"""Generated polynomial evaluators, checked on the host without a GPU.
+
+The library writes, per family of sector tables, straight-line code for every sector's U~, F~ (at real t or at
+the complex deformed point z of Eq. 14) and the gradient and Hessian polynomials of F~ (Eq. 14 and its
+Jacobian).  Here that code is compiled for the host with a small shim and evaluated at random points against
+the packed table's own terms (coefficient hi + lo, exponents) summed in FP64: every term must enter its own
+polynomial exactly once with its exponents.  NVRTC compiles the same source for sm_103a without a device.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_1508_02512_gb300 import _native as N
+from paper_1508_02512_gb300 import api
+from paper_1508_02512_gb300 import tables as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WORK = os.path.join(ROOT, "tests", "_gen_build")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1508_02512_gb300 import build
+    build.build()
+    N.lib()
+
+
+# host mirrors of the packed image records (csrc/qmc_internal.h)
+class PackedHeader(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("n_sectors", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("loops", ctypes.c_int32), ("n_nu", ctypes.c_int32), ("n_props", ctypes.c_int32),
+                ("eU0", ctypes.c_int32), ("eU1", ctypes.c_int32), ("eF0", ctypes.c_int32), ("eF1", ctypes.c_int32),
+                ("order_min", ctypes.c_int32), ("order_max", ctypes.c_int32), ("kmax", ctypes.c_int32),
+                ("n_slots", ctypes.c_int32), ("pre_low", ctypes.c_int32), ("n_pre", ctypes.c_int32),
+                ("pre", ctypes.c_double * (N.QMC_MAX_ORDERS + 4)), ("class_begin", ctypes.c_int32 * 2),
+                ("class_end", ctypes.c_int32 * 2), ("class_maxm", ctypes.c_int32 * 2), ("max_terms", ctypes.c_int32),
+                ("n_terms_total", ctypes.c_int32), ("sectors_off", ctypes.c_int64), ("terms_off", ctypes.c_int64),
+                ("total_bytes", ctypes.c_int64), ("flops_per_eval", ctypes.c_double),
+                ("transc_per_eval", ctypes.c_double), ("n_deformed", ctypes.c_int32), ("n_negative", ctypes.c_int32),
+                ("max_sigma", ctypes.c_int32), ("reserved", ctypes.c_int32), ("termsf_off", ctypes.c_int64),
+                ("family", ctypes.c_uint64), ("reserved2", ctypes.c_int64)]
+
+
+class PackedSector(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("sigma", ctypes.c_int32), ("sing_mask", ctypes.c_int32),
+                ("M", ctypes.c_int32), ("A", ctypes.c_int32 * 8), ("B", ctypes.c_int32 * 8), ("nU", ctypes.c_int32),
+                ("nF", ctypes.c_int32), ("nG", ctypes.c_int32), ("nH", ctypes.c_int32), ("term0", ctypes.c_int32),
+                ("n_terms", ctypes.c_int32), ("orig_index", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gstart", ctypes.c_int16 * 8), ("hstart", ctypes.c_int16 * 24), ("D", ctypes.c_double),
+                ("flops", ctypes.c_double), ("transc", ctypes.c_double), ("Df", ctypes.c_float),
+                ("pad", ctypes.c_float)]
+
+
+TERM_F = np.dtype([("hi", "<f4"), ("lo", "<f4"), ("e", "u1", (8,))])
+
+
+def prepared(cfg, **point):
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    kin = W.kinematics(cfg.topology, **{**cfg.point, **point}) if point else cfg.kin
+    return api.prepare(blob, kin, cfg.order_min, cfg.order_max)
+
+
+def image(prep):
+    buf = bytes(prep.packed)
+    h = PackedHeader.from_buffer_copy(buf, 0)
+    assert h.magic == 0x31504D51
+    secs = [PackedSector.from_buffer_copy(buf, h.sectors_off + k * ctypes.sizeof(PackedSector))
+            for k in range(h.n_sectors)]
+    terms = np.frombuffer(buf, dtype=TERM_F, count=h.n_terms_total, offset=h.termsf_off)
+    return h, secs, terms
+
+
+def blocks(h, s):
+    """term index ranges (within the sector) of U, F, every gradient and every Hessian polynomial"""
+    S = h.dim
+    bG = s.nU + s.nF
+    bH = bG + s.nG
+    g = [(bG + s.gstart[j], bG + s.gstart[j + 1]) for j in range(S)]
+    hh = [(bH + s.hstart[p], bH + s.hstart[p + 1]) for p in range(S * (S + 1) // 2)]
+    return (0, s.nU), (s.nU, s.nU + s.nF), g, hh
+
+
+def test_family_source_depends_on_structure_only():
+    pa, pb, pc = prepared(W.CONFIG1), prepared(W.CONFIG1, s=7.5, t=-2.5), prepared(W.CONFIG0)
+    a, b, c = api.gen_source(pa), api.gen_source(pb), api.gen_source(pc)
+    assert a == b and a != c
+    assert api.gen_source(prepared(W.CONFIG1)) == a  # deterministic
+    fa, fb, fc = (image(p)[0].family for p in (pa, pb, pc))
+    assert fa == fb and fa != fc and fa != 0
+
+
+@pytest.mark.parametrize("cfg", W.CONFIGS, ids=lambda c: c.name)
+def test_every_term_enters_its_polynomial_once(cfg):
+    prep = prepared(cfg)
+    h, secs, terms = image(prep)
+    src = api.gen_source(prep)
+    funcs = {}
+    for m in re.finditer(r"\b(qg_(?:ufr|gh|ufc)_(\d+))\(const PackedTermF[^{]*\{(.*?)\n\}", src, flags=re.S):
+        funcs[m.group(1)] = m.group(3)
+    for k, s in enumerate(secs):
+        U, F, G, H = blocks(h, s)
+        if h.class_begin[0] <= k < h.class_end[0]:
+            groups = {f"qg_ufr_{k}": [U, F]}
+        else:
+            groups = {f"qg_gh_{k}": G + H, f"qg_ufc_{k}": [U, F]}
+        for name, ranges in groups.items():
+            body = funcs[name]
+            # (accumulator, term) of every statement that adds a term; a complex FMA writes .x and .y
+            pairs = re.findall(r"a(\d+)(?:\.[xy])? (?:=|\+=) (?:fmaf\()?C\[(\d+)\]\.hi", body)
+            got = {}
+            for acc, term in pairs:
+                got.setdefault(int(term), set()).add(int(acc))
+            want = {i: {a} for a, (lo, hi) in enumerate(ranges) for i in range(lo, hi)}
+            assert got == want, (cfg.name, name)
+            n_stmt = len(pairs)
+            n_expected = sum(2 if (name.startswith("qg_ufc") and not constant) else 1
+                             for constant in [not any(terms[s.term0 + i]["e"]) for i in want])
+            assert n_stmt == n_expected, (cfg.name, name)
+
+
+SHIM = r"""
+#include <math.h>
+#define DEV static inline
+#define __device__
+#define __noinline__ static
+#define __restrict__
+struct cf { float x, y; };
+static inline cf mkf(float x, float y) { return cf{x, y}; }
+static inline cf cmulf(cf a, cf b) { return cf{fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
+struct PackedTermF { float hi, lo; unsigned char e[8]; };
+"""
+
+
+def host_harness(src, h, secs):
+    """C++ source: the generated per-sector functions plus extern "C" entry points taking arrays"""
+    i0 = src.index('#include "qmc_dev.cuh"') + len('#include "qmc_dev.cuh"')
+    body = src[i0:src.index("struct QgPol")]
+    S = h.dim
+    NP = S * (S + 1) // 2
+    ool = "struct QgGH" in body
+    out = [SHIM, body]
+    ufr, gh, ufc = [], [], []
+    ta = ", ".join(f"t[{j}]" for j in range(S))
+    za = ", ".join(f"z[{j}].x, z[{j}].y" for j in range(S))
+    for k in range(h.n_sectors):
+        if h.class_begin[0] <= k < h.class_end[0]:
+            ufr.append(f"case {k}: {{ QgR r = qg_ufr_{k}(C, {ta}); U[0] = r.U; U[1] = r.F; return; }}" if ool else
+                       f"case {k}: qg_ufr_{k}(C, t, U[0], U[1]); return;")
+        else:
+            gh.append(f"case {k}: {{ QgGH r = qg_gh_{k}(C, {ta}); for (int j = 0; j < {S}; ++j) g[j] = r.g[j]; "
+                      f"for (int q = 0; q < {NP}; ++q) hh[q] = r.h[q]; return; }}" if ool else
+                      f"case {k}: qg_gh_{k}(C, t, g, hh); return;")
+            ufc.append(f"case {k}: {{ QgC r = qg_ufc_{k}(C, {za}); UF[0] = r.U; UF[1] = r.F; return; }}" if ool else
+                       f"case {k}: qg_ufc_{k}(C, z, UF[0], UF[1]); return;")
+    out.append('extern "C" void h_ufr(int s, const PackedTermF *C, const float *t, float *U) { switch (s) { '
+               + " ".join(ufr) + " } }")
+    out.append('extern "C" void h_gh(int s, const PackedTermF *C, const float *t, float *g, float *hh) { switch (s) { '
+               + " ".join(gh) + " } }")
+    out.append('extern "C" void h_ufc(int s, const PackedTermF *C, const cf *z, cf *UF) { switch (s) { '
+               + " ".join(ufc) + " } }")
+    return "\n".join(out)
+
+
+def poly_value(terms, lo, hi, x):
+    """FP64 sum over terms[lo:hi] of (hi + lo) * prod_j x_j^e_j (x real or complex)"""
+    v = 0.0
+    mag = 0.0
+    for t in terms[lo:hi]:
+        c = float(t["hi"]) + float(t["lo"])
+        m = 1.0 + 0.0j if np.iscomplexobj(x) else 1.0
+        for j in range(len(x)):
+            m = m * x[j] ** int(t["e"][j])
+        v += c * m
+        mag += abs(c * m)
+    return v, mag
+
+
+@pytest.mark.parametrize("cfg", [W.CONFIG0, W.CONFIG1, W.CONFIG2], ids=lambda c: c.name)
+def test_generated_functions_evaluate_the_table_polynomials(cfg):
+    prep = prepared(cfg)
+    h, secs, terms = image(prep)
+    src = api.gen_source(prep)
+    os.makedirs(WORK, exist_ok=True)
+    cpp = os.path.join(WORK, f"gen_{cfg.name}.cpp")
+    so = os.path.join(WORK, f"gen_{cfg.name}.so")
+    open(cpp, "w").write(host_harness(src, h, secs))
+    subprocess.check_call(["g++", "-O1", "-ffp-contract=off", "-shared", "-fPIC", "-o", so, cpp])
+    L = ctypes.CDLL(so)
+    S = h.dim
+    NP = S * (S + 1) // 2
+    rng = np.random.Generator(np.random.PCG64(11))
+    fptr = ctypes.POINTER(ctypes.c_float)
+    worst = 0.0
+    for k, s in enumerate(secs):
+        T_s = np.ascontiguousarray(terms[s.term0: s.term0 + s.n_terms])
+        Cp = T_s.ctypes.data_as(ctypes.c_void_p)
+        U, F, G, H = blocks(h, s)
+        for _ in range(3):
+            t = rng.uniform(0.0, 1.0, S).astype(np.float32)
+            tp = t.ctypes.data_as(fptr)
+            if h.class_begin[0] <= k < h.class_end[0]:
+                outv = np.zeros(2, np.float32)
+                L.h_ufr(k, Cp, tp, outv.ctypes.data_as(fptr))
+                refs = [poly_value(T_s, *U, t.astype(np.float64)), poly_value(T_s, *F, t.astype(np.float64))]
+                got = list(outv)
+            else:
+                g = np.zeros(S, np.float32)
+                hh = np.zeros(NP, np.float32)
+                L.h_gh(k, Cp, tp, g.ctypes.data_as(fptr), hh.ctypes.data_as(fptr))
+                refs = [poly_value(T_s, lo, hi, t.astype(np.float64)) for lo, hi in G + H]
+                got = list(g) + list(hh)
+                zc = (t * (1 - 0.3j * rng.uniform(0, 1, S))).astype(np.complex64)
+                zf = np.ascontiguousarray(np.stack([zc.real, zc.imag], -1).astype(np.float32))
+                uf = np.zeros(4, np.float32)
+                L.h_ufc(k, Cp, zf.ctypes.data_as(fptr), uf.ctypes.data_as(fptr))
+                z64 = zc.astype(np.complex128)
+                refs += [poly_value(T_s, *U, z64), poly_value(T_s, *F, z64)]
+                got += [complex(uf[0], uf[1]), complex(uf[2], uf[3])]
+            for (rv, mag), gv in zip(refs, got):
+                err = abs(complex(gv) - rv) / max(mag, 1e-30)
+                worst = max(worst, err)
+    print(f"{cfg.name}: worst |generated FP32 - table FP64| / sum|terms| = {worst:.2e}")
+    assert worst < 2e-6
+
+
+def test_nvrtc_compiles_generated_source_without_a_device():
+    info = api.gen_compile(prepared(W.CONFIG1), load=False)
+    assert info.cubin_bytes > 0 and info.source_bytes > 0 and info.compile_ms > 0

@@ -192,5 +192,6 @@ def test_pass_validation_on_host():
     assert api.scratch_bytes(prep, good) > 0
     for bad in (api.make_pass(1, [1] * 6, 4), api.make_pass(1021, [0, 1, 1, 1, 1, 1], 4),
                 api.make_pass(1021, [1] * 6, 0), api.make_pass(1021, [1] * 6, 4, transform_r=7),
-                api.make_pass(1021, [1] * 6, 4, block=48), api.make_pass(1021, [1] * 6, 4, points_per_thread=65)):
+                api.make_pass(1021, [1] * 6, 4, block=48), api.make_pass(1021, [1] * 6, 4, points_per_thread=65),
+                api.make_pass(1021, [1] * 6, 4, evaluator=3)):
         assert api.scratch_bytes(prep, bad) == 0
