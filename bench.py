@@ -509,17 +509,18 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0):
             "precision": "f64" if precision == 0 else "f32+f64"}
 
 
-def profile_pass(precision="fp64"):
-    """Two passes of the benchmark integral at n = 1048573 (largest prime below 2^20), 16 shifts."""
+def profile_pass(precision="fp64", integral="massive_box"):
+    """Two passes of the benchmark integral at n = 1048573 (largest prime below 2^20; 65521 for a two-loop
+    integral), 16 shifts: the small case for ncu captures."""
     import torch
     from paper_1508_02512_gb300 import _native as N
     from paper_1508_02512_gb300 import api
     from paper_1508_02512_gb300 import tables as T
-    cfg = W.CONFIG1
+    cfg = INTEGRALS[integral]
     blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
-    prep = api.prepare(blob, cfg.kin, 0, 0)
+    prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
     dev = api.DeviceIntegral(prep)
-    n = 1048573
+    n = 1048573 if cfg.topology.loops == 1 else 65521
     p = api.make_pass(n, dict(api.builtin_lattices())[n], N_SHIFTS, 3,
                       precision=N.QMC_PREC_MIXED if precision == "mixed" else N.QMC_PREC_FP64)
     sh = torch.tensor(W.shifts(cfg.seed, N_SHIFTS), device="cuda")
@@ -536,7 +537,7 @@ if __name__ == "__main__":
     if a.serving:
         print(json.dumps({"metric": "serving time-to-1e-3", **serving_run(a.serving)}))
     elif a.profile_pass:
-        profile_pass(a.precision)
+        profile_pass(a.precision, a.integral)
     elif a.impl == "reference":
         main_reference(a)
     else:

@@ -202,10 +202,13 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
  *   into buf (cap bytes, NUL-terminated); *len receives the size needed (call with buf = NULL to query).
  *   Host only.  Errors: QMC_ERR_ARG, QMC_ERR_MEMORY (cap too small).
  * qmc_gen_compile: compiles that source with NVRTC for sm_103a.  load = 0: compile only (no CUDA device needed;
- *   nothing cached).  load != 0: compile unless the family is cached, load the module on the current device
- *   and keep it for the life of the process (the FP32 passes of QMC_EVAL_GENERATED do this on first use; call
- *   it beforehand to keep compilation out of a timed region).  info (may be NULL) receives the family key,
- *   compilation time (of the cached compilation when cached = 1), source and cubin sizes.
+ *   nothing cached).  load = 1: compile unless the family is cached (waiting for a compilation of the same
+ *   family already under way), load the module and keep it for the life of the process (the FP32 passes of
+ *   QMC_EVAL_GENERATED do this on first use; call it beforehand to keep compilation out of a timed region).
+ *   load = 2: the same in a background thread (current device): returns QMC_PENDING while it runs, QMC_OK once
+ *   the module is loaded (the serving loop uses this so that other requests keep running meanwhile).
+ *   info (may be NULL) receives the family key, compilation time (of the cached compilation when cached = 1),
+ *   source and cubin sizes.  A failed compilation is remembered: later calls return its status.
  *   Errors: QMC_ERR_ARG, QMC_ERR_CODEGEN (NVRTC failed; its log goes to stderr), QMC_ERR_CUDA (load failed).
  */
 typedef struct {

@@ -1668,6 +1668,7 @@ struct Serving {
     std::condition_variable cv;
     bool stop = false;
     std::deque<std::shared_ptr<Request>> queue;
+    std::vector<std::shared_ptr<Request>> compiling; /* admitted; waiting for their family's generated code */
     std::vector<std::shared_ptr<Request>> active;
     std::map<int64_t, std::shared_ptr<Request>> all;
     int64_t next_id = 1;
@@ -1847,7 +1848,9 @@ void serve_loop(qmc_ctx *c) {
         }
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || !S->active.empty(); });
+            auto ready = [&] { return S->stop || !S->queue.empty() || !S->active.empty(); };
+            if (S->compiling.empty()) S->cv.wait(lk, ready);
+            else S->cv.wait_for(lk, std::chrono::milliseconds(2), ready);
             if (S->stop) return;
             /* cancelled requests leave at the round boundary (finished below, outside this lock) */
             for (auto it = S->active.begin(); it != S->active.end();) {
@@ -1890,8 +1893,37 @@ void serve_loop(qmc_ctx *c) {
                 }
             }
         }
+        /* requests whose family's generated evaluator is still compiling (in the background) wait aside */
+        {
+            std::vector<std::shared_ptr<Request>> still;
+            for (auto &r : S->compiling) {
+                const int rc = r->cancelled ? QMC_ERR_CANCELLED : qmc_gen_compile(r->packed.data(), 2, nullptr);
+                if (rc == QMC_PENDING) {
+                    still.push_back(r);
+                } else if (rc) {
+                    std::lock_guard<std::mutex> g(c->mu);
+                    finish(S, c, *r, rc);
+                } else {
+                    fresh.push_back(r);
+                }
+            }
+            S->compiling.swap(still);
+        }
         for (auto &r : fresh) {
             if (!r) continue;
+            if (r->opt.precision == QMC_PREC_MIXED && r->opt.evaluator != QMC_EVAL_TABLE &&
+                std::find(S->compiling.begin(), S->compiling.end(), r) == S->compiling.end()) {
+                const int g = qmc_gen_compile(r->packed.data(), 2, nullptr);
+                if (g == QMC_PENDING) {
+                    S->compiling.push_back(r);
+                    continue;
+                }
+                if (g) {
+                    std::lock_guard<std::mutex> lk2(c->mu);
+                    finish(S, c, *r, g);
+                    continue;
+                }
+            }
             int rc = r->probe_due ? probe(S, c, *r) : QMC_OK;
             if (rc) {
                 std::lock_guard<std::mutex> g(c->mu);

@@ -25,10 +25,12 @@
 #include <chrono>
 #include <cstdio>
 #include <cstring>
+#include <condition_variable>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "qmc_internal.h"
@@ -388,19 +390,27 @@ struct Module {
     int64_t source_bytes = 0, cubin_bytes = 0;
 };
 
-std::mutex g_mu;
-std::map<uint64_t, std::unique_ptr<Module>> g_modules;
+/* Per-family state.  Compilation runs outside the lock (other families' lookups and launches go on); callers
+   of the same family wait on the condition variable, or, in the background form, return QMC_PENDING.  The
+   state is never destroyed (a background compilation may still run while the process exits). */
+enum { GEN_NONE = 0, GEN_COMPILING, GEN_READY, GEN_FAILED };
+struct Slot {
+    int state = GEN_NONE;
+    int rc = QMC_OK;
+    std::unique_ptr<Module> mod;
+};
+struct Cache {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<uint64_t, Slot> slots;
+};
+Cache &cache() {
+    static Cache *c = new Cache();
+    return *c;
+}
 
-int get_module(const PackedHeader *h, const Module **out, bool *was_cached) {
-    const uint64_t key = family_key(h);
-    std::lock_guard<std::mutex> g(g_mu);
-    auto it = g_modules.find(key);
-    if (it != g_modules.end()) {
-        *out = it->second.get();
-        if (was_cached) *was_cached = true;
-        return QMC_OK;
-    }
-    if (was_cached) *was_cached = false;
+/* compile and load (no lock held) */
+int build_module(const PackedHeader *h, std::unique_ptr<Module> &out) {
     Compiled cc;
     int rc = compile(generate(h), cc);
     if (rc) return rc;
@@ -418,8 +428,67 @@ int get_module(const PackedHeader *h, const Module **out, bool *was_cached) {
     m->compile_ms = cc.ms;
     m->source_bytes = (int64_t)cc.source_bytes;
     m->cubin_bytes = (int64_t)cc.cubin.size();
-    *out = m.get();
-    g_modules[key] = std::move(m);
+    out = std::move(m);
+    return QMC_OK;
+}
+
+void finish_slot(uint64_t key, int rc, std::unique_ptr<Module> m) {
+    Cache &C = cache();
+    {
+        std::lock_guard<std::mutex> g(C.mu);
+        Slot &s = C.slots[key];
+        s.rc = rc;
+        s.state = rc ? GEN_FAILED : GEN_READY;
+        if (!rc) s.mod = std::move(m);
+    }
+    C.cv.notify_all();
+}
+
+/* mode 0: compile here and wait; mode 1: start a background compilation and return QMC_PENDING until ready */
+int get_module(const PackedHeader *h, const Module **out, bool *was_cached, int mode = 0, int device = 0) {
+    const uint64_t key = family_key(h);
+    Cache &C = cache();
+    std::unique_lock<std::mutex> lk(C.mu);
+    Slot &s = C.slots[key];
+    if (was_cached) *was_cached = s.state == GEN_READY;
+    if (s.state == GEN_COMPILING) {
+        if (mode == 1) return QMC_PENDING;
+        C.cv.wait(lk, [&] { return s.state != GEN_COMPILING; });
+    }
+    if (s.state == GEN_READY) {
+        *out = s.mod.get();
+        return QMC_OK;
+    }
+    if (s.state == GEN_FAILED) return s.rc;
+    s.state = GEN_COMPILING;
+    lk.unlock();
+    if (mode == 1) {
+        std::vector<unsigned char> img(reinterpret_cast<const unsigned char *>(h),
+                                       reinterpret_cast<const unsigned char *>(h) + h->total_bytes);
+        std::thread([key, device](std::vector<unsigned char> im) {
+            cudaSetDevice(device);
+            std::unique_ptr<Module> m;
+            int rc;
+            try {
+                rc = build_module(reinterpret_cast<const PackedHeader *>(im.data()), m);
+            } catch (const std::bad_alloc &) {
+                rc = QMC_ERR_MEMORY;
+            }
+            finish_slot(key, rc, std::move(m));
+        }, std::move(img)).detach();
+        return QMC_PENDING;
+    }
+    std::unique_ptr<Module> m;
+    int rc;
+    try {
+        rc = build_module(h, m);
+    } catch (const std::bad_alloc &) {
+        rc = QMC_ERR_MEMORY;
+    }
+    const Module *mp = m.get();
+    finish_slot(key, rc, std::move(m));
+    if (rc) return rc;
+    *out = mp;
     return QMC_OK;
 }
 
@@ -497,7 +566,9 @@ int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info) {
         }
         const Module *m = nullptr;
         bool cached = false;
-        const int rc = get_module(h, &m, &cached);
+        int device = 0;
+        if (load == 2 && cudaGetDevice(&device) != cudaSuccess) return QMC_ERR_NO_DEVICE;
+        const int rc = get_module(h, &m, &cached, load == 2 ? 1 : 0, device);
         if (rc) return rc;
         if (info) {
             info->compile_ms = m->compile_ms;
