@@ -96,7 +96,8 @@ typedef struct {
     int32_t n_shifts;          /* m random shifts, 1..4096 */
     int32_t transform_r;       /* periodising transform order 0..3 (Eq. 21 is r = 1) */
     int32_t precision;         /* QMC_PREC_FP64 or QMC_PREC_MIXED */
-    int32_t block;             /* threads per block: 0 = default, else 64..512 and a multiple of 32 */
+    int32_t block;             /* threads per block: 0 = default (128), else 32..256 and a multiple of 32; at most
+                                  128 for generated FP32 evaluators of 5- and 6-dimensional sectors */
     int32_t points_per_thread; /* 0 = default, else 1..64 */
     int32_t grid;              /* blocks of the persistent kernel: 0 = one wave on the device */
     int32_t evaluator;         /* QMC_EVAL_* of the FP32 evaluation */
@@ -224,8 +225,9 @@ int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info);
 /*
  * Launch-shape autotuner (the paper fixes no launch shape; this is the library's).  qmc_autotune runs the
  * evaluation launch of `pass` (qmc_eval_partials semantics, synchronous on `stream`) once per candidate shape,
- * block in {64, 128, 256} threads x points_per_thread in {4, 8, 16, 32}, times each with CUDA events (one
- * untimed launch first), returns the timings and the fastest shape in *out, and records that shape for the
+ * block in {64, 128, 256} threads (those the pass allows) x points_per_thread in {4, 8, 16, 32}, times each
+ * with CUDA events (one untimed launch first), returns the timings and the fastest shape in *out, and records
+ * that shape for the
  * family of the image, the pass's precision and evaluator and the lattice-size bucket (smallest 2^k >= n).
  * From then on, in this process, passes of that key whose block and points_per_thread are both 0 use the
  * recorded shape: qmc_scratch_bytes, qmc_eval_sums, qmc_integrate and the serving loop included.  Results

@@ -604,6 +604,13 @@ TuneKey tune_key(const PackedHeader *h, const qmc_pass *p) {
     return TuneKey{h->family, p->precision, ev, b};
 }
 
+/* Mixed-precision policy of qmc_integrate and the serving loop: a lattice rung runs in FP32 only when its whole
+   pass would cost more than ~1e8 flop in FP64 (about 0.2 ms at the FP64 rate this path reaches on a GB300).
+   Below that, the FP32 probe and its extra device round trip cost more than the FP64 pass saves. */
+bool fp32_pays(const PackedHeader *h, int m, int64_t n) {
+    return (double)h->n_sectors * m * (double)n * h->flops_per_eval > 1e8;
+}
+
 int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
     if (!h || !p) return QMC_ERR_ARG;
     if (p->lattice.n < 2 || p->lattice.n >= ((int64_t)1 << 31)) return QMC_ERR_ARG;
@@ -622,6 +629,8 @@ int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
     }
     pl.block = block ? block : 128;
     if (pl.block < 32 || pl.block > 256 || pl.block % 32) return QMC_ERR_ARG;
+    if (p->precision == QMC_PREC_MIXED && p->evaluator != QMC_EVAL_TABLE && pl.block > qmc_gen_max_block(h->dim))
+        return QMC_ERR_ARG;
     pl.P = P ? P : (p->precision == QMC_PREC_MIXED ? 16 : 8);
     if (pl.P < 1 || pl.P > 64) return QMC_ERR_ARG;
     for (int j = 0; j < h->dim; ++j)
@@ -1071,7 +1080,7 @@ size_t qmc_autotune_scratch_bytes(const void *packed_host, const qmc_pass *pass)
             q.block = b;
             q.points_per_thread = P;
             const size_t s = qmc_scratch_bytes(packed_host, &q);
-            if (!s) return 0;
+            if (!s) continue; /* shape not allowed for this pass (generated kernels of large sectors) */
             need = std::max(need, s);
         }
     return need;
@@ -1096,6 +1105,7 @@ int qmc_autotune(const void *packed_host, const void *packed_dev, const qmc_pass
             qmc_pass q = *pass;
             q.block = b;
             q.points_per_thread = P;
+            if (!qmc_scratch_bytes(packed_host, &q)) continue;
             if (!warm) { /* first launch of the kernel (module load, attributes) stays out of the timings */
                 rc = qmc_eval_partials(packed_host, packed_dev, &q, shifts_dev, lambda_dev, scratch_dev, scratch_bytes,
                                        stream);
@@ -1473,11 +1483,12 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
         pass.lattice = L;
         pass.n_shifts = m;
         pass.transform_r = opt->transform_r > 0 ? opt->transform_r : 3;
-        pass.precision = opt->precision;
+        const bool use32 = mixed && fp32_pays(h, m, L.n);
+        pass.precision = use32 ? QMC_PREC_MIXED : QMC_PREC_FP64;
         pass.block = opt->block;
         pass.points_per_thread = opt->points_per_thread;
         pass.evaluator = opt->evaluator;
-        pass.sector_precision = mixed ? (const int32_t *)c->prec.p : nullptr;
+        pass.sector_precision = use32 ? (const int32_t *)c->prec.p : nullptr;
         const size_t need = qmc_scratch_bytes(I.packed.data(), &pass);
         if (!need) return res->status = QMC_ERR_ARG;
         rc = dev_reserve(c, c->scratch, need);
@@ -1485,7 +1496,7 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
         for (;;) {
             rc = cuda_status(cudaMemcpyAsync(c->lambda.p, lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
                                              c->stream));
-            if (!rc && probe_due) {
+            if (!rc && probe_due && use32) {
                 /* FP32 budget: sectors whose FP32 values on the probe sample deviate from FP64 by more than
                    fp32_budget * rel_tol (L1, any order) are evaluated in FP64 */
                 const int64_t nsamp = opt->probe_samples > 0 ? opt->probe_samples : 4096;
@@ -1727,17 +1738,23 @@ int admit(Serving *S, qmc_ctx *c, Request &r) {
     return rc;
 }
 
+/* this rung of the request evaluates in FP32 (mixed policy, as in qmc_integrate) */
+bool fp32_rung(const Request &r) {
+    return r.opt.precision == QMC_PREC_MIXED &&
+           fp32_pays(header_of(r.packed.data()), (int)(r.shifts.size() / 6), r.ladder[r.rung].n);
+}
+
 qmc_pass pass_of(const Request &r) {
     qmc_pass p;
     std::memset(&p, 0, sizeof(p));
     p.lattice = r.ladder[r.rung];
     p.n_shifts = (int32_t)(r.shifts.size() / 6);
     p.transform_r = r.opt.transform_r > 0 ? r.opt.transform_r : 3;
-    p.precision = r.opt.precision;
+    p.precision = fp32_rung(r) ? QMC_PREC_MIXED : QMC_PREC_FP64;
     p.block = r.opt.block;
     p.points_per_thread = r.opt.points_per_thread;
     p.evaluator = r.opt.evaluator;
-    p.sector_precision = r.opt.precision == QMC_PREC_MIXED ? (const int32_t *)r.dprec.p : nullptr;
+    p.sector_precision = p.precision == QMC_PREC_MIXED ? (const int32_t *)r.dprec.p : nullptr;
     return p;
 }
 
@@ -1924,7 +1941,7 @@ void serve_loop(qmc_ctx *c) {
                     continue;
                 }
             }
-            int rc = r->probe_due ? probe(S, c, *r) : QMC_OK;
+            int rc = (r->probe_due && fp32_rung(*r)) ? probe(S, c, *r) : QMC_OK;
             if (rc) {
                 std::lock_guard<std::mutex> g(c->mu);
                 finish(S, c, *r, rc);
@@ -1944,7 +1961,7 @@ void serve_loop(qmc_ctx *c) {
         /* this round: one pass per active request, in shared launches (no context lock held meanwhile) */
         int rc = QMC_OK;
         for (auto &r : batch) {
-            if (r->probe_due) rc = probe(S, c, *r);
+            if (r->probe_due && fp32_rung(*r)) rc = probe(S, c, *r);
             if (rc) break;
             rc = cuda_status(cudaMemcpyAsync(r->dlambda.p, r->lam.data(), r->lam.size() * sizeof(double),
                                              cudaMemcpyHostToDevice, S->stream));

@@ -180,5 +180,6 @@ int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *st
    as const void *. */
 int qmc_gen_kernel(const void *packed_host, int cls, const void **eval_kernel);
 uint64_t qmc_family_key(const void *packed_host); /* computed from the image, not read from its header */
+int qmc_gen_max_block(int dim);                  /* largest block of a generated kernel for sectors of this dimension */
 int qmc_gen_blocks_per_sm(const void *kernel, int block, int smem_bytes, int *out);
 int qmc_gen_launch_eval(const void *kernel, const JobTable &t, int grid, int block, void *stream);

@@ -323,10 +323,13 @@ std::string generate(const PackedHeader *h) {
         if (h->class_end[c] <= h->class_begin[c]) continue;
         const char *def = c == 1 ? "true" : "false";
         const int mm = maxm_of(h, c);
+        /* 5- and 6-dimensional deformed sectors: 3 blocks of 128 threads per SM (<= 170 registers, no spills)
+           measured 13 % faster than the register-unbounded build (2 blocks); smaller sectors keep 256 */
+        const std::string lb = qmc_gen_max_block(S) == 128 ? "__launch_bounds__(128, 3)" : "__launch_bounds__(256)";
         std::snprintf(b, sizeof(b),
-                      "extern \"C\" __global__ void __launch_bounds__(256) qg_eval_c%d(const __grid_constant__ JobTable jt) {\n"
+                      "extern \"C\" __global__ void %s qg_eval_c%d(const __grid_constant__ JobTable jt) {\n"
                       "    eval_f32_body<%d, %s, %d, QgPol>(jt);\n}\n",
-                      c, S, def, mm);
+                      lb.c_str(), c, S, def, mm);
         o += b;
     }
     return o;
@@ -495,6 +498,8 @@ int get_module(const PackedHeader *h, const Module **out, bool *was_cached, int 
 }  // namespace
 
 /* ---------------------------------------------------------------- internal interface (qmc_internal.h) */
+int qmc_gen_max_block(int dim) { return dim >= 5 ? 128 : 256; }
+
 uint64_t qmc_family_key(const void *packed_host) {
     const PackedHeader *h = hdr(packed_host);
     return h ? family_key(h) : 0;

@@ -195,3 +195,15 @@ def test_pass_validation_on_host():
                 api.make_pass(1021, [1] * 6, 4, block=48), api.make_pass(1021, [1] * 6, 4, points_per_thread=65),
                 api.make_pass(1021, [1] * 6, 4, evaluator=3)):
         assert api.scratch_bytes(prep, bad) == 0
+
+
+def test_generated_fp32_passes_of_six_dimensional_sectors_take_at_most_128_threads():
+    cfg = W.CONFIG2
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
+    z = [1, 2, 3, 4, 5, 6]
+    for block, ok in ((128, True), (256, False)):
+        gen = api.make_pass(1021, z, 4, precision=N.QMC_PREC_MIXED, block=block)
+        assert (api.scratch_bytes(prep, gen) > 0) == ok
+    for ev, prec in ((N.QMC_EVAL_TABLE, N.QMC_PREC_MIXED), (N.QMC_EVAL_AUTO, N.QMC_PREC_FP64)):
+        assert api.scratch_bytes(prep, api.make_pass(1021, z, 4, precision=prec, block=256, evaluator=ev)) > 0
