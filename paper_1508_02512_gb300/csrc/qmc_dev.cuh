@@ -785,6 +785,33 @@ DEV cf det_deform_f(const float (&A)[S][S], float lam) {
     }
 }
 
+/* det(I - i lam A) for S >= 4 in FP32, A = D + T H (D = diag((1-2t)g), T = diag(t(1-t)), H the Hessian of F):
+   with s = T^(1/2), A is similar to the symmetric B = D + s H s, so the determinant is that of the complex
+   symmetric N = I - i lam B, whose Hermitian part is the identity.  Gaussian elimination without pivoting is
+   stable for matrices with a positive definite Hermitian part (every Schur complement keeps one, so no pivot
+   vanishes); symmetric elimination works on the upper triangle only.  N holds the upper triangle row-major
+   (S(S+1)/2 entries) and is overwritten. */
+template <int S>
+DEV cf det_sym_f(cf (&N)[S * (S + 1) / 2]) {
+    auto at = [](int i, int j) { return i * S - i * (i - 1) / 2 + (j - i); }; /* i <= j */
+    cf det = mkf(1.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const cf dk = N[at(k, k)];
+        det = cmulf(det, dk);
+        if (k + 1 < S) {
+            const cf inv = cinvf(dk);
+#pragma unroll
+            for (int i = k + 1; i < S; ++i) {
+                const cf l = cmulf(N[at(k, i)], inv);
+#pragma unroll
+                for (int j = i; j < S; ++j) N[at(i, j)] = csubf(N[at(i, j)], cmulf(l, N[at(k, j)]));
+            }
+        }
+    }
+    return det;
+}
+
 /* FP32 sign check: rounding leaves |Im F| ~ 1e-7 |F| where the deformation vanishes; a point fails when
    Im F(z) exceeds that noise */
 #define QMC_F32_SIGN_NOISE 4e-6f
@@ -813,20 +840,39 @@ DEV void eval_G_f(const PackedSector &s, const Pol &P, const float *tt, const fl
     } else {
         float g[S], h[S * (S + 1) / 2];
         P.GH(tt, g, h);
-        float A[S][S];
-        int p = 0;
+        cf detJ;
+        if constexpr (S >= 4) {
+            float s[S];
 #pragma unroll
-        for (int j = 0; j < S; ++j) {
+            for (int j = 0; j < S; ++j) s[j] = sqrtf(tt[j] * ttm[j]);
+            cf N[S * (S + 1) / 2];
+            int p = 0;
 #pragma unroll
-            for (int k = j; k < S; ++k) {
-                A[j][k] = tt[j] * ttm[j] * h[p];
-                if (k != j) A[k][j] = tt[k] * ttm[k] * h[p];
-                ++p;
+            for (int j = 0; j < S; ++j) {
+#pragma unroll
+                for (int k = j; k < S; ++k) {
+                    const float b = (k == j) ? fmaf(ttm[j] - tt[j], g[j], tt[j] * ttm[j] * h[p]) : s[j] * s[k] * h[p];
+                    N[p] = mkf(k == j ? 1.f : 0.f, -lam * b);
+                    ++p;
+                }
             }
-        }
+            detJ = det_sym_f<S>(N);
+        } else {
+            float A[S][S];
+            int p = 0;
 #pragma unroll
-        for (int j = 0; j < S; ++j) A[j][j] = fmaf(ttm[j] - tt[j], g[j], A[j][j]);
-        const cf detJ = det_deform_f<S>(A, lam);
+            for (int j = 0; j < S; ++j) {
+#pragma unroll
+                for (int k = j; k < S; ++k) {
+                    A[j][k] = tt[j] * ttm[j] * h[p];
+                    if (k != j) A[k][j] = tt[k] * ttm[k] * h[p];
+                    ++p;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < S; ++j) A[j][j] = fmaf(ttm[j] - tt[j], g[j], A[j][j]);
+            detJ = det_deform_f<S>(A, lam);
+        }
         cf z[S], q[S];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
