@@ -104,6 +104,10 @@ typedef struct {
     int32_t reserved;
     const int32_t *sector_precision; /* QMC_PREC_MIXED only: device array, one entry per sector (table order),
                                         1 = evaluate in FP32, anything else = FP64; NULL = every sector FP32 */
+    const int32_t *sector_active;    /* HOST array, one entry per sector (table order): nonzero = evaluate this
+                                        sector; NULL = every sector.  The pass writes sums/fails of the evaluated
+                                        sectors only and leaves the others' entries as they were, so passes of
+                                        different lattice sizes can fill one output (per-sector lattices). */
 } qmc_pass;
 
 /* One pass of one prepared integral, as an element of a batch (qmc_eval_batch). */
@@ -286,6 +290,12 @@ int qmc_builtin_lattices(qmc_lattice *out, int32_t cap);
 int qmc_combine(const void *packed_host, const qmc_pass *pass, const double *sums, double *Q, double *mean,
                 double *err);
 
+/* qmc_combine for sums whose sectors come from lattices of different sizes (passes with sector_active):
+ * n_sector[s] = lattice size that produced sector s's sums (table order).  Each sector's estimate of Eq. 19 is
+ * still unbiased per shift, so the per-shift totals and Eq. 20 keep their meaning.  Host only. */
+int qmc_combine_sectors(const void *packed_host, int32_t n_shifts, const int64_t *n_sector, const double *sums,
+                        double *Q, double *mean, double *err);
+
 /* ------------------------------------------------------------------ integrate to a requested accuracy */
 
 typedef struct qmc_ctx qmc_ctx;
@@ -310,7 +320,10 @@ typedef struct {
     double fp32_budget;      /* QMC_PREC_MIXED: a sector runs in FP64 when its probe's sum|v32-v64| exceeds
                                 fp32_budget * rel_tol * sum|v64| in any order (0 = 0.1) */
     int32_t evaluator;       /* QMC_EVAL_* of the FP32 evaluation (passes and probe) */
-    int32_t reserved;
+    int32_t lock_step;       /* 0 (default): each sector has its own lattice size, and after each step only the
+                                sectors that carry most of the remaining error per unit of cost move up the ladder
+                                (the per-shift totals stay valid estimates, qmc_combine_sectors); nonzero: all
+                                sectors climb the ladder together */
 } qmc_options;
 
 typedef struct {

@@ -57,7 +57,7 @@ class qmc_sector_desc(ctypes.Structure):
 class qmc_pass(ctypes.Structure):
     _fields_ = [("lattice", qmc_lattice), ("n_shifts", c_int32), ("transform_r", c_int32), ("precision", c_int32),
                 ("block", c_int32), ("points_per_thread", c_int32), ("grid", c_int32), ("evaluator", c_int32),
-                ("reserved", c_int32), ("sector_precision", c_void_p)]
+                ("reserved", c_int32), ("sector_precision", c_void_p), ("sector_active", c_void_p)]
 
 
 class qmc_batch_item(ctypes.Structure):
@@ -71,7 +71,7 @@ class qmc_options(ctypes.Structure):
                 ("ladder_start", c_int32), ("n_lattices", c_int32), ("lattices", POINTER(qmc_lattice)),
                 ("shifts", POINTER(c_double)), ("max_n", c_int64), ("max_seconds", c_double), ("block", c_int32),
                 ("points_per_thread", c_int32), ("probe_samples", c_int64), ("fp32_budget", c_double),
-                ("evaluator", c_int32), ("reserved", c_int32)]
+                ("evaluator", c_int32), ("lock_step", c_int32)]
 
 
 class qmc_result(ctypes.Structure):
@@ -129,6 +129,7 @@ PROTOTYPES = {
                                 c_int64, c_void_p, c_void_p, c_void_p]),
     "qmc_builtin_lattices": (c_int, [POINTER(qmc_lattice), c_int32]),
     "qmc_combine": (c_int, [c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p]),
+    "qmc_combine_sectors": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "qmc_create": (c_int, [POINTER(c_void_p), c_int32, c_size_t, c_void_p]),
     "qmc_destroy": (c_int, [c_void_p]),
     "qmc_load_sectors": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_int32)]),

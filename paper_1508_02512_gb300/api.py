@@ -48,6 +48,19 @@ def make_pass(n: int, z, n_shifts: int, transform_r: int = 3, precision: int = N
     return p
 
 
+def combine_sectors(prep: Prepared, n_shifts: int, n_sector, sums: np.ndarray):
+    """qmc_combine_sectors: like combine(), with the lattice size of each sector's sums (table order)."""
+    sums = np.ascontiguousarray(sums, dtype=np.float64)
+    nv = np.ascontiguousarray(np.asarray(n_sector, dtype=np.int64))
+    nord = prep.info.order_max - prep.info.order_min + 1
+    Q = np.zeros((n_shifts, nord, 2))
+    mean = np.zeros((nord, 2))
+    err = np.zeros((nord, 2))
+    N.check(N.lib().qmc_combine_sectors(prep.packed, n_shifts, nv.ctypes.data, sums.ctypes.data, Q.ctypes.data,
+                                        mean.ctypes.data, err.ctypes.data), "qmc_combine_sectors")
+    return Q[..., 0] + 1j * Q[..., 1], mean[:, 0] + 1j * mean[:, 1], err
+
+
 def gen_source(prep) -> str:
     """qmc_gen_source: the CUDA source generated for the family of a prepared integral."""
     n = ctypes.c_size_t()
@@ -201,13 +214,14 @@ class Context:
     @staticmethod
     def options(rel_tol=1e-3, abs_tol=0.0, precision=N.QMC_PREC_FP64, n_shifts=16, seed=0, lam=0.5, transform_r=3,
                 ladder_start=0, lattices=None, shifts=None, max_n=0, max_seconds=0.0, max_halvings=6, block=0,
-                points_per_thread=0, evaluator=N.QMC_EVAL_AUTO, probe_samples=0, fp32_budget=0.0):
+                points_per_thread=0, evaluator=N.QMC_EVAL_AUTO, probe_samples=0, fp32_budget=0.0, lock_step=0):
         """qmc_options and the Python objects that must outlive the call that uses them."""
         o = N.qmc_options()
         o.rel_tol, o.abs_tol, o.precision, o.n_shifts, o.seed = rel_tol, abs_tol, precision, n_shifts, seed
         o.lambda_, o.max_halvings, o.transform_r, o.ladder_start = lam, max_halvings, transform_r, ladder_start
         o.max_n, o.max_seconds, o.block, o.points_per_thread = max_n, max_seconds, block, points_per_thread
         o.evaluator, o.probe_samples, o.fp32_budget = evaluator, probe_samples, fp32_budget
+        o.lock_step = lock_step
         keep = []
         if lattices is not None:
             arr = (N.qmc_lattice * len(lattices))(*[make_lattice(n, z) for n, z in lattices])

@@ -574,11 +574,16 @@ const PackedSector *sectors_of(const void *packed) {
 }
 
 /* ------------------------------------------------------------------ launch planning */
+/* A run: consecutive packed sectors of one class that the pass evaluates (all of the class unless the pass
+   names a subset); each run becomes one job per precision and one reduction job. */
+struct Run {
+    int cls, sector_begin, n_sect;
+    int64_t items, item_off;  /* items of the run; its first item within the pass */
+};
 struct Plan {
     int block, P;
     int64_t chunks;
-    int64_t items[QMC_N_CLASSES];     /* items of each sector class */
-    int64_t item_off[QMC_N_CLASSES];  /* first item of the class within the pass */
+    std::vector<Run> runs;
     int64_t total_items;
 };
 
@@ -637,12 +642,29 @@ int make_plan(const PackedHeader *h, const qmc_pass *p, Plan &pl) {
         if (p->lattice.z[j] == 0 || (int64_t)p->lattice.z[j] >= p->lattice.n) return QMC_ERR_ARG;
     const int64_t C = (int64_t)pl.block * pl.P;
     pl.chunks = (p->lattice.n + C - 1) / C;
+    const PackedSector *ps =
+        reinterpret_cast<const PackedSector *>(reinterpret_cast<const unsigned char *>(h) + h->sectors_off);
     int64_t off = 0;
+    pl.runs.clear();
     for (int c = 0; c < QMC_N_CLASSES; ++c) {
-        const int64_t ns = h->class_end[c] - h->class_begin[c];
-        pl.items[c] = ns * p->n_shifts * pl.chunks;
-        pl.item_off[c] = off;
-        off += pl.items[c];
+        int s = h->class_begin[c];
+        while (s < h->class_end[c]) {
+            if (p->sector_active && !p->sector_active[ps[s].orig_index]) {
+                ++s;
+                continue;
+            }
+            int e = s + 1;
+            while (e < h->class_end[c] && (!p->sector_active || p->sector_active[ps[e].orig_index])) ++e;
+            Run r;
+            r.cls = c;
+            r.sector_begin = s;
+            r.n_sect = e - s;
+            r.items = (int64_t)r.n_sect * p->n_shifts * pl.chunks;
+            r.item_off = off;
+            off += r.items;
+            pl.runs.push_back(r);
+            s = e;
+        }
     }
     pl.total_items = off;
     return QMC_OK;
@@ -762,7 +784,9 @@ int batch_layout(const qmc_batch_item *items, int n, BatchLayout &L) {
         L.fail_off[i] = off;
         off += up256((size_t)L.plans[i].total_items * sizeof(uint32_t));
     }
-    L.n_counters = 4 * n + 4; /* at most one launch per (pass, class, precision) */
+    size_t runs = 0;
+    for (int i = 0; i < n; ++i) runs += L.plans[i].runs.size();
+    L.n_counters = (int)(2 * runs + 4); /* at most one launch per (run, precision) */
     L.counters_off = off;
     off += up256((size_t)L.n_counters * sizeof(unsigned long long));
     L.total = off;
@@ -810,8 +834,8 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
         const PackedHeader *h = header_of(b.packed_host);
         const Plan &pl = L.plans[i];
         const bool mixed = b.pass.precision == QMC_PREC_MIXED;
-        for (int c = 0; c < QMC_N_CLASSES; ++c) {
-            if (pl.items[c] == 0) continue;
+        for (const Run &run : pl.runs) {
+            const int c = run.cls;
             for (int prec = 0; prec < 2; ++prec) {
                 if (!mixed && prec == 1) continue;
                 if (mixed && prec == 0 && !b.pass.sector_precision) continue;
@@ -825,16 +849,16 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
                 J.shifts = b.shifts_dev;
                 J.lambda = b.lambda_dev;
                 J.sector_prec = mixed ? b.pass.sector_precision : nullptr;
-                J.partials = reinterpret_cast<double *>(scr + L.partial_off[i]) + pl.item_off[c] * h->n_slots * 2;
-                J.part_fails = reinterpret_cast<uint32_t *>(scr + L.fail_off[i]) + pl.item_off[c];
+                J.partials = reinterpret_cast<double *>(scr + L.partial_off[i]) + run.item_off * h->n_slots * 2;
+                J.part_fails = reinterpret_cast<uint32_t *>(scr + L.fail_off[i]) + run.item_off;
                 J.n = (uint32_t)b.pass.lattice.n;
                 J.invn = 1.0 / (double)b.pass.lattice.n;
                 for (int j = 0; j < QMC_MAX_DIM; ++j) {
                     J.z[j] = j < h->dim ? b.pass.lattice.z[j] : 0;
                     J.zstep[j] = (uint32_t)(((uint64_t)pl.block * J.z[j]) % (uint64_t)b.pass.lattice.n);
                 }
-                J.sector_begin = h->class_begin[c];
-                J.n_sect = h->class_end[c] - h->class_begin[c];
+                J.sector_begin = run.sector_begin;
+                J.n_sect = run.n_sect;
                 J.m = b.pass.n_shifts;
                 J.n_slots = h->n_slots;
                 J.eU0 = h->eU0;
@@ -910,8 +934,7 @@ int run_reduce(const qmc_batch_item *items, int n, const BatchLayout &L, const u
         const qmc_batch_item &b = items[i];
         const PackedHeader *h = header_of(b.packed_host);
         const Plan &pl = L.plans[i];
-        for (int c = 0; c < QMC_N_CLASSES; ++c) {
-            if (pl.items[c] == 0) continue;
+        for (const Run &run : pl.runs) {
             if (ft->n_jobs == QMC_MAX_JOBS) {
                 const int rc = flush();
                 if (rc) return rc;
@@ -921,12 +944,12 @@ int run_reduce(const qmc_batch_item *items, int n, const BatchLayout &L, const u
             J.sectors_off = h->sectors_off;
             J.chunks = pl.chunks;
             J.pair_begin = pairs;
-            J.partials = reinterpret_cast<const double *>(scr + L.partial_off[i]) + pl.item_off[c] * h->n_slots * 2;
-            J.part_fails = reinterpret_cast<const uint32_t *>(scr + L.fail_off[i]) + pl.item_off[c];
+            J.partials = reinterpret_cast<const double *>(scr + L.partial_off[i]) + run.item_off * h->n_slots * 2;
+            J.part_fails = reinterpret_cast<const uint32_t *>(scr + L.fail_off[i]) + run.item_off;
             J.sums = b.sums_dev;
             J.fails = b.fails_dev;
-            J.sector_begin = h->class_begin[c];
-            J.n_sect = h->class_end[c] - h->class_begin[c];
+            J.sector_begin = run.sector_begin;
+            J.n_sect = run.n_sect;
             J.m = b.pass.n_shifts;
             J.n_slots = h->n_slots;
             pairs += (int64_t)J.n_sect * J.m;
@@ -1196,23 +1219,29 @@ int qmc_builtin_lattices(qmc_lattice *out, int32_t cap) {
     return QMC_BUILTIN_LATTICES;
 }
 
-int qmc_combine(const void *packed_host, const qmc_pass *pass, const double *sums, double *Q, double *mean,
-                double *err) {
+}  // extern "C"
+
+namespace {
+
+/* Eqs. 19-20 with the Gamma prefactor: per-shift totals Q, their mean and standard errors.  invn[s] = 1/n of
+   the lattice that produced sector s's sums (table order); only >= 0 restricts the totals to that sector. */
+int combine_core(const void *packed_host, int m, const double *invn_of, int only, const double *sums, double *Q,
+                 double *mean, double *err) {
     const PackedHeader *h = header_of(packed_host);
-    if (!h || !pass || !sums || !Q || !mean || !err || pass->n_shifts < 1 || pass->lattice.n < 1) return QMC_ERR_ARG;
-    const int m = pass->n_shifts, ns = h->n_slots;
+    const int ns = h->n_slots;
     const int nord = h->order_max - h->order_min + 1;
     const PackedSector *ps = sectors_of(packed_host);
     /* sector-sum orders run from -max_sigma to kmax */
     const int lo = -h->max_sigma;
     const int width = h->kmax - lo + 1;
-    const double invn = 1.0 / (double)pass->lattice.n;
     std::vector<double> tr(width), ti(width);
     for (int k = 0; k < m; ++k) {
         std::fill(tr.begin(), tr.end(), 0.0);
         std::fill(ti.begin(), ti.end(), 0.0);
         for (int pi = 0; pi < h->n_sectors; ++pi) {
             const PackedSector &s = ps[pi];
+            if (only >= 0 && s.orig_index != only) continue;
+            const double invn = invn_of[s.orig_index];
             const double *v = sums + ((size_t)s.orig_index * m + k) * ns * 2;
             /* kind 1: multiply by exp(i pi eF(eps)) = (-1)^{eF0} sum_n (i pi eF1 eps)^n / n! */
             std::vector<double> phr(ns, 0.0), phi(ns, 0.0);
@@ -1276,6 +1305,30 @@ int qmc_combine(const void *packed_host, const qmc_pass *pass, const double *sum
     return QMC_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int qmc_combine(const void *packed_host, const qmc_pass *pass, const double *sums, double *Q, double *mean,
+                double *err) {
+    const PackedHeader *h = header_of(packed_host);
+    if (!h || !pass || !sums || !Q || !mean || !err || pass->n_shifts < 1 || pass->lattice.n < 1) return QMC_ERR_ARG;
+    std::vector<double> invn(h->n_sectors, 1.0 / (double)pass->lattice.n);
+    return combine_core(packed_host, pass->n_shifts, invn.data(), -1, sums, Q, mean, err);
+}
+
+int qmc_combine_sectors(const void *packed_host, int32_t n_shifts, const int64_t *n_sector, const double *sums,
+                        double *Q, double *mean, double *err) {
+    const PackedHeader *h = header_of(packed_host);
+    if (!h || !n_sector || !sums || !Q || !mean || !err || n_shifts < 1) return QMC_ERR_ARG;
+    std::vector<double> invn(h->n_sectors);
+    for (int s = 0; s < h->n_sectors; ++s) {
+        if (n_sector[s] < 1) return QMC_ERR_ARG;
+        invn[s] = 1.0 / (double)n_sector[s];
+    }
+    return combine_core(packed_host, n_shifts, invn.data(), -1, sums, Q, mean, err);
+}
+
 }  // extern "C"
 
 /* ====================================================================== context */
@@ -1331,6 +1384,256 @@ void dev_release(qmc_ctx *c, DevBuf &b) {
     b.p = nullptr;
     b.bytes = 0;
 }
+
+}  // namespace
+
+namespace {
+
+/* ------------------------------------------------------------------ integration to a requested accuracy
+ * State of one integration (qmc_integrate, or one serving request).  Every sector s has its own rung r_s on the
+ * lattice ladder, deformation parameter lambda_s (halved on sign failures, Eq. 14) and precision flag; sums
+ * holds the latest per-(sector, shift) sums, each from its own lattice.  A step evaluates the active sectors
+ * (one pass per distinct rung, sector_active masks), then:
+ *   sign failures -> halve lambda of the failing sectors, which alone are evaluated again;
+ *   otherwise the per-shift totals over all sectors (Eqs. 19-20, qmc_combine_sectors) give value and error;
+ *   converged (every order meets the target) -> done;
+ *   else lock-step (lock_step != 0): every sector moves one rung up, as in a plain ladder;
+ *        per-sector (lock_step = 0, the default): for each order still above target, sectors are taken in order of
+ *        variance contribution per cost of their next rung until they hold enough of the variance for one
+ *        doubling of n (which removes at least 3/4 of a QMC sector variance) to bring the order to its target,
+ *        and at most 90 % of it; only those move up. */
+struct IntegState {
+    const unsigned char *packed = nullptr;
+    const PackedHeader *h = nullptr;
+    qmc_options opt;
+    int m = 0, ns = 0, nord = 0, max_h = 6;
+    bool mixed = false, adaptive = false, probe_due = false;
+    std::vector<qmc_lattice> ladder;
+    std::vector<double> shifts, lam, sums;
+    std::vector<int64_t> fails;
+    std::vector<int> rung, halv;
+    std::vector<char> active;
+    std::vector<int32_t> prec;
+    std::vector<double> flops;                  /* per sector (table order) */
+    std::vector<std::vector<int32_t>> masks;    /* host masks of the current passes */
+    int probe_item = -1;
+    std::chrono::steady_clock::time_point t0;
+
+    int init(const unsigned char *packed_host, const qmc_options &o, std::chrono::steady_clock::time_point start,
+             qmc_result &res) {
+        packed = packed_host;
+        h = header_of(packed);
+        opt = o;
+        t0 = start;
+        m = o.n_shifts > 0 ? o.n_shifts : 16;
+        if (m < 2 || m > 4096) return QMC_ERR_ARG;
+        if (o.rel_tol < 0 || o.abs_tol < 0) return QMC_ERR_ARG;
+        ns = h->n_sectors;
+        nord = h->order_max - h->order_min + 1;
+        res.order_min = h->order_min;
+        res.n_orders = nord;
+        max_h = o.max_halvings > 0 ? o.max_halvings : 6;
+        if (o.n_lattices > 0) {
+            if (!o.lattices) return QMC_ERR_ARG;
+            ladder.assign(o.lattices, o.lattices + o.n_lattices);
+        } else {
+            for (int i = std::max(0, o.ladder_start); i < QMC_BUILTIN_LATTICES; ++i) {
+                qmc_lattice L;
+                L.n = qmc_builtin_lattice[i].n;
+                for (int j = 0; j < QMC_MAX_DIM; ++j) L.z[j] = qmc_builtin_lattice[i].z[j];
+                ladder.push_back(L);
+            }
+        }
+        while (!ladder.empty() && o.max_n > 0 && ladder.back().n > o.max_n) ladder.pop_back();
+        if (ladder.empty()) return QMC_ERR_NOT_CONVERGED;
+        /* shifts (Eq. 18): explicit, or splitmix64 from the seed */
+        if (o.shifts) shifts.assign(o.shifts, o.shifts + (size_t)m * 6);
+        else splitmix_shifts(o.seed, m, shifts);
+        mixed = o.precision == QMC_PREC_MIXED;
+        adaptive = o.lock_step == 0;
+        probe_due = mixed;
+        rung.assign(ns, 0);
+        halv.assign(ns, 0);
+        active.assign(ns, 1);
+        lam.assign(ns, o.lambda > 0 ? o.lambda : 0.5);
+        prec.assign(ns, 1);
+        sums.assign((size_t)ns * m * h->n_slots * 2, 0.0);
+        fails.assign((size_t)ns * m, 0);
+        flops.assign(ns, 0.0);
+        const PackedSector *ps = sectors_of(packed);
+        for (int pi = 0; pi < ns; ++pi) flops[ps[pi].orig_index] = std::max(ps[pi].flops, 1.0);
+        return QMC_OK;
+    }
+
+    int64_t probe_samples() const { return opt.probe_samples > 0 ? opt.probe_samples : 4096; }
+
+    /* passes of the next evaluation: one per distinct rung among the active sectors */
+    void passes(std::vector<qmc_pass> &out, const int32_t *prec_dev) {
+        out.clear();
+        masks.clear();
+        probe_item = -1;
+        std::vector<int> rs;
+        for (int s = 0; s < ns; ++s)
+            if (active[s] && std::find(rs.begin(), rs.end(), rung[s]) == rs.end()) rs.push_back(rung[s]);
+        std::sort(rs.begin(), rs.end());
+        for (int r : rs) {
+            std::vector<int32_t> mk(ns, 0);
+            double fl = 0.0;
+            int cnt = 0;
+            for (int s = 0; s < ns; ++s)
+                if (active[s] && rung[s] == r) {
+                    mk[s] = 1;
+                    fl += flops[s];
+                    ++cnt;
+                }
+            qmc_pass p;
+            std::memset(&p, 0, sizeof(p));
+            p.lattice = ladder[r];
+            p.n_shifts = m;
+            p.transform_r = opt.transform_r > 0 ? opt.transform_r : 3;
+            p.block = opt.block;
+            p.points_per_thread = opt.points_per_thread;
+            p.evaluator = opt.evaluator;
+            /* mixed policy: FP32 only where this pass would cost more than ~1e8 flop in FP64 */
+            const bool use32 = mixed && fl * m * (double)ladder[r].n > 1e8;
+            p.precision = use32 ? QMC_PREC_MIXED : QMC_PREC_FP64;
+            p.sector_precision = use32 ? prec_dev : nullptr;
+            if (use32 && probe_due && probe_item < 0) probe_item = (int)out.size();
+            masks.push_back(cnt == ns ? std::vector<int32_t>() : mk);
+            out.push_back(p);
+        }
+        for (size_t k = 0; k < out.size(); ++k) out[k].sector_active = masks[k].empty() ? nullptr : masks[k].data();
+    }
+
+    void set_precision(const std::vector<double> &pr, qmc_result &res) {
+        const double budget = (opt.fp32_budget > 0 ? opt.fp32_budget : 0.1) * opt.rel_tol;
+        res.fp64_reruns = 0;
+        for (int s = 0; s < ns; ++s) {
+            bool bad = false;
+            for (int o = 0; o < h->n_slots; ++o) {
+                const double *v = &pr[((size_t)s * h->n_slots + o) * 4];
+                if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
+            }
+            prec[s] = bad ? 0 : 1;
+            res.fp64_reruns += bad;
+        }
+        probe_due = false;
+    }
+
+    void count(const std::vector<qmc_pass> &ps, qmc_result &res) const {
+        res.passes += 1;
+        for (const qmc_pass &p : ps) {
+            int cnt = 0;
+            for (int s = 0; s < ns; ++s) cnt += p.sector_active ? (p.sector_active[s] != 0) : 1;
+            res.evals += (int64_t)cnt * m * p.lattice.n;
+        }
+    }
+
+    /* after an evaluation: returns QMC_PENDING to continue, or the final status */
+    int step(qmc_result &res) {
+        /* sign check of Eq. (14) on the sectors just evaluated */
+        bool again = false;
+        for (int s = 0; s < ns; ++s) {
+            if (!active[s]) continue;
+            int64_t f = 0;
+            for (int k = 0; k < m; ++k) f += fails[(size_t)s * m + k];
+            if (f > 0) {
+                res.sign_failures += (int32_t)std::min<int64_t>(f, INT32_MAX);
+                if (halv[s] >= max_h) return QMC_ERR_DEFORMATION;
+                lam[s] *= 0.5;
+                halv[s] += 1;
+                res.lambda_halvings += 1;
+                again = true;
+            } else {
+                active[s] = 0;
+            }
+        }
+        if (again) {
+            probe_due = mixed;
+            return QMC_PENDING;
+        }
+        std::vector<int64_t> nvec(ns);
+        int64_t nmax = 0;
+        for (int s = 0; s < ns; ++s) {
+            nvec[s] = ladder[rung[s]].n;
+            nmax = std::max(nmax, nvec[s]);
+        }
+        std::vector<double> Q((size_t)m * nord * 2), mean(nord * 2), err(nord * 2);
+        qmc_combine_sectors(packed, m, nvec.data(), sums.data(), Q.data(), mean.data(), err.data());
+        res.n_final = nmax;
+        for (int o = 0; o < nord && o < QMC_MAX_ORDERS; ++o) {
+            res.value[o][0] = mean[2 * o];
+            res.value[o][1] = mean[2 * o + 1];
+            res.error[o][0] = err[2 * o];
+            res.error[o][1] = err[2 * o + 1];
+        }
+        double vmax = 0.0;
+        for (int o = 0; o < nord; ++o) vmax = std::max(vmax, std::hypot(mean[2 * o], mean[2 * o + 1]));
+        std::vector<double> tau(nord), e(nord);
+        bool ok = true;
+        for (int o = 0; o < nord; ++o) {
+            e[o] = std::hypot(err[2 * o], err[2 * o + 1]);
+            tau[o] = std::max(opt.rel_tol * std::max(std::hypot(mean[2 * o], mean[2 * o + 1]), 1e-6 * vmax), opt.abs_tol);
+            ok &= e[o] <= tau[o];
+        }
+        if (ok) return QMC_OK;
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (opt.max_seconds > 0 && el > opt.max_seconds) return QMC_ERR_TIMEOUT;
+        if (!adaptive) {
+            for (int s = 0; s < ns; ++s)
+                if (rung[s] + 1 >= (int)ladder.size()) return QMC_ERR_NOT_CONVERGED;
+            for (int s = 0; s < ns; ++s) {
+                rung[s] += 1;
+                active[s] = 1;
+            }
+            return QMC_PENDING;
+        }
+        /* per-sector allocation: error contribution of each sector per order */
+        std::vector<double> Qs((size_t)m * nord * 2), ms(nord * 2), es(nord * 2);
+        std::vector<double> invn(ns);
+        for (int s = 0; s < ns; ++s) invn[s] = 1.0 / (double)nvec[s];
+        std::vector<double> e2((size_t)ns * nord, 0.0);
+        for (int s = 0; s < ns; ++s) {
+            combine_core(packed, m, invn.data(), s, sums.data(), Qs.data(), ms.data(), es.data());
+            for (int o = 0; o < nord; ++o) e2[(size_t)s * nord + o] = es[2 * o] * es[2 * o] + es[2 * o + 1] * es[2 * o + 1];
+        }
+        std::vector<char> pick(ns, 0);
+        for (int o = 0; o < nord; ++o) {
+            if (e[o] <= tau[o]) continue;
+            double tot = 0.0;
+            for (int s = 0; s < ns; ++s) tot += e2[(size_t)s * nord + o];
+            if (tot <= 0.0) continue;
+            /* share of this order's variance the step must remove; one doubling removes >= 3/4 of a sector's, so
+               the picked sectors must hold >= 4/3 of that share (with a margin), but never the last 10 %: sectors
+               that barely contribute stay on their lattice until their share grows */
+            const double need_frac = 1.0 - (tau[o] * tau[o]) / (e[o] * e[o]);
+            const double need = std::min(0.9, 1.2 * need_frac / 0.75) * tot;
+            std::vector<std::pair<double, int>> order;
+            for (int s = 0; s < ns; ++s) {
+                if (rung[s] + 1 >= (int)ladder.size()) continue;
+                const double cost = flops[s] * (double)ladder[rung[s] + 1].n;
+                order.push_back({e2[(size_t)s * nord + o] / cost, s});
+            }
+            std::sort(order.begin(), order.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+                return a.first > b.first || (a.first == b.first && a.second < b.second);
+            });
+            double got = 0.0;
+            for (const auto &pr : order) {
+                if (got >= need) break;
+                pick[pr.second] = 1;
+                got += e2[(size_t)pr.second * nord + o];
+            }
+        }
+        bool any = false;
+        for (int s = 0; s < ns; ++s)
+            if (pick[s]) {
+                rung[s] += 1;
+                active[s] = 1;
+                any = true;
+            }
+        return any ? QMC_PENDING : QMC_ERR_NOT_CONVERGED;
+    }
+};
 
 }  // namespace
 
@@ -1429,165 +1732,75 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
     if (it == c->integrals.end()) return res->status = QMC_ERR_NOT_FOUND;
     Integral &I = it->second;
     if (I.packed.empty()) return res->status = QMC_ERR_ARG;
-    const PackedHeader *h = header_of(I.packed.data());
-    const int m = opt->n_shifts > 0 ? opt->n_shifts : 16;
-    if (m < 2 || m > 4096) return res->status = QMC_ERR_ARG;
-    const int nord = h->order_max - h->order_min + 1;
-    res->order_min = h->order_min;
-    res->n_orders = nord;
     cudaSetDevice(c->device);
-    /* lattice ladder */
-    std::vector<qmc_lattice> ladder;
-    if (opt->n_lattices > 0) {
-        if (!opt->lattices) return res->status = QMC_ERR_ARG;
-        ladder.assign(opt->lattices, opt->lattices + opt->n_lattices);
-    } else {
-        for (int i = std::max(0, opt->ladder_start); i < QMC_BUILTIN_LATTICES; ++i) {
-            qmc_lattice L;
-            L.n = qmc_builtin_lattice[i].n;
-            for (int j = 0; j < QMC_MAX_DIM; ++j) L.z[j] = qmc_builtin_lattice[i].z[j];
-            ladder.push_back(L);
-        }
-    }
-    /* shifts (Eq. 18): explicit, or splitmix64 from the seed */
-    std::vector<double> shifts;
-    if (opt->shifts) shifts.assign(opt->shifts, opt->shifts + (size_t)m * 6);
-    else splitmix_shifts(opt->seed, m, shifts);
-    int rc = dev_reserve(c, c->shifts, shifts.size() * sizeof(double));
-    if (!rc) rc = cuda_status(cudaMemcpyAsync(c->shifts.p, shifts.data(), shifts.size() * sizeof(double),
-                                              cudaMemcpyHostToDevice, c->stream));
-    const int ns = h->n_sectors;
-    std::vector<double> lam(ns, opt->lambda > 0 ? opt->lambda : 0.5);
-    std::vector<int> halv(ns, 0);
-    const int max_h = opt->max_halvings > 0 ? opt->max_halvings : 6;
-    if (!rc) rc = dev_reserve(c, c->lambda, ns * sizeof(double));
-    if (!rc) rc = dev_reserve(c, c->sums, (size_t)ns * m * h->n_slots * 2 * sizeof(double));
-    if (!rc) rc = dev_reserve(c, c->fails, (size_t)ns * m * sizeof(int64_t));
+    IntegState st;
+    int rc = st.init(I.packed.data(), *opt, t0, *res);
     if (rc) return res->status = rc;
-    std::vector<double> sums((size_t)ns * m * h->n_slots * 2), Q((size_t)m * nord * 2), mean(nord * 2), err(nord * 2);
-    std::vector<int64_t> fails((size_t)ns * m);
-    const bool mixed = opt->precision == QMC_PREC_MIXED;
-    std::vector<int32_t> prec(ns, 1);
-    bool probe_due = mixed;
-    if (mixed) {
-        rc = dev_reserve(c, c->prec, ns * sizeof(int32_t));
-        if (!rc) rc = dev_reserve(c, c->probe, (size_t)ns * h->n_slots * 4 * sizeof(double));
-        if (rc) return res->status = rc;
-    }
-    int status = QMC_ERR_NOT_CONVERGED;
+    const int ns = st.ns, m = st.m;
+    const PackedHeader *h = st.h;
+    rc = dev_reserve(c, c->shifts, st.shifts.size() * sizeof(double));
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(c->shifts.p, st.shifts.data(), st.shifts.size() * sizeof(double),
+                                              cudaMemcpyHostToDevice, c->stream));
+    if (!rc) rc = dev_reserve(c, c->lambda, ns * sizeof(double));
+    if (!rc) rc = dev_reserve(c, c->sums, st.sums.size() * sizeof(double));
+    if (!rc) rc = dev_reserve(c, c->fails, st.fails.size() * sizeof(int64_t));
+    if (!rc && st.mixed) rc = dev_reserve(c, c->prec, ns * sizeof(int32_t));
+    if (!rc && st.mixed) rc = dev_reserve(c, c->probe, (size_t)ns * h->n_slots * 4 * sizeof(double));
+    if (rc) return res->status = rc;
     float kernel_ms_total = 0.f;
-    for (const qmc_lattice &L : ladder) {
-        if (opt->max_n > 0 && L.n > opt->max_n) break;
-        qmc_pass pass;
-        std::memset(&pass, 0, sizeof(pass));
-        pass.lattice = L;
-        pass.n_shifts = m;
-        pass.transform_r = opt->transform_r > 0 ? opt->transform_r : 3;
-        const bool use32 = mixed && fp32_pays(h, m, L.n);
-        pass.precision = use32 ? QMC_PREC_MIXED : QMC_PREC_FP64;
-        pass.block = opt->block;
-        pass.points_per_thread = opt->points_per_thread;
-        pass.evaluator = opt->evaluator;
-        pass.sector_precision = use32 ? (const int32_t *)c->prec.p : nullptr;
-        const size_t need = qmc_scratch_bytes(I.packed.data(), &pass);
-        if (!need) return res->status = QMC_ERR_ARG;
-        rc = dev_reserve(c, c->scratch, need);
-        if (rc) return res->status = rc;
-        for (;;) {
-            rc = cuda_status(cudaMemcpyAsync(c->lambda.p, lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
-                                             c->stream));
-            if (!rc && probe_due && use32) {
-                /* FP32 budget: sectors whose FP32 values on the probe sample deviate from FP64 by more than
-                   fp32_budget * rel_tol (L1, any order) are evaluated in FP64 */
-                const int64_t nsamp = opt->probe_samples > 0 ? opt->probe_samples : 4096;
-                const double budget = (opt->fp32_budget > 0 ? opt->fp32_budget : 0.1) * opt->rel_tol;
-                std::vector<double> pr((size_t)ns * h->n_slots * 4);
-                rc = qmc_probe_precision(I.packed.data(), I.dpacked.p, &pass, (const double *)c->shifts.p,
-                                         (const double *)c->lambda.p, nsamp, (double *)c->probe.p, c->stream);
-                if (!rc)
-                    rc = cuda_status(cudaMemcpyAsync(pr.data(), c->probe.p, pr.size() * sizeof(double),
-                                                     cudaMemcpyDeviceToHost, c->stream));
-                if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
-                if (rc) return res->status = rc;
-                res->fp64_reruns = 0;
-                for (int s2 = 0; s2 < ns; ++s2) {
-                    bool bad = false;
-                    for (int o = 0; o < h->n_slots; ++o) {
-                        const double *v = &pr[((size_t)s2 * h->n_slots + o) * 4];
-                        if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
-                    }
-                    prec[s2] = bad ? 0 : 1;
-                    res->fp64_reruns += bad;
-                }
-                rc = cuda_status(cudaMemcpyAsync(c->prec.p, prec.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice,
-                                                 c->stream));
-                probe_due = false;
-            }
-            if (!rc) rc = cuda_status(cudaEventRecord(c->ev0, c->stream));
+    std::vector<qmc_pass> passes;
+    std::vector<qmc_batch_item> items;
+    int status = QMC_PENDING;
+    while (status == QMC_PENDING) {
+        st.passes(passes, (const int32_t *)c->prec.p);
+        rc = cuda_status(cudaMemcpyAsync(c->lambda.p, st.lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
+                                         c->stream));
+        if (!rc && st.probe_item >= 0) {
+            /* FP32 budget of Sec. II's cancellation-prone sectors: the probe decides which sectors stay in FP32 */
+            std::vector<double> pr((size_t)ns * h->n_slots * 4);
+            rc = qmc_probe_precision(st.packed, I.dpacked.p, &passes[st.probe_item], (const double *)c->shifts.p,
+                                     (const double *)c->lambda.p, st.probe_samples(), (double *)c->probe.p, c->stream);
             if (!rc)
-                rc = qmc_eval_sums(I.packed.data(), I.dpacked.p, &pass, (const double *)c->shifts.p,
-                                   (const double *)c->lambda.p, c->scratch.p, c->scratch.bytes, (double *)c->sums.p,
-                                   (int64_t *)c->fails.p, c->stream);
-            if (!rc) rc = cuda_status(cudaEventRecord(c->ev1, c->stream));
-            if (!rc)
-                rc = cuda_status(cudaMemcpyAsync(sums.data(), c->sums.p, sums.size() * sizeof(double),
-                                                 cudaMemcpyDeviceToHost, c->stream));
-            if (!rc)
-                rc = cuda_status(cudaMemcpyAsync(fails.data(), c->fails.p, fails.size() * sizeof(int64_t),
+                rc = cuda_status(cudaMemcpyAsync(pr.data(), c->probe.p, pr.size() * sizeof(double),
                                                  cudaMemcpyDeviceToHost, c->stream));
             if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
-            if (rc) return res->status = rc;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, c->ev0, c->ev1);
-            kernel_ms_total += ms;
-            res->passes += 1;
-            res->evals += (int64_t)ns * m * L.n;
-            /* sign check of Eq. (14): halve lambda of failing sectors and repeat this lattice size */
-            bool again = false;
-            for (int s = 0; s < ns; ++s) {
-                int64_t f = 0;
-                for (int k = 0; k < m; ++k) f += fails[(size_t)s * m + k];
-                if (f > 0) {
-                    res->sign_failures += (int32_t)std::min<int64_t>(f, INT32_MAX);
-                    if (halv[s] >= max_h) {
-                        res->kernel_ms = kernel_ms_total;
-                        return res->status = QMC_ERR_DEFORMATION;
-                    }
-                    lam[s] *= 0.5;
-                    halv[s] += 1;
-                    res->lambda_halvings += 1;
-                    again = true;
-                }
+            if (!rc) {
+                st.set_precision(pr, *res);
+                rc = cuda_status(cudaMemcpyAsync(c->prec.p, st.prec.data(), ns * sizeof(int32_t),
+                                                 cudaMemcpyHostToDevice, c->stream));
             }
-            if (!again) break;
-            probe_due = mixed;
         }
-        qmc_combine(I.packed.data(), &pass, sums.data(), Q.data(), mean.data(), err.data());
-        res->n_final = L.n;
-        double vmax = 0.0;
-        for (int o = 0; o < nord; ++o) vmax = std::max(vmax, std::hypot(mean[2 * o], mean[2 * o + 1]));
-        bool ok = true;
-        for (int o = 0; o < nord; ++o) {
-            const double e = std::hypot(err[2 * o], err[2 * o + 1]);
-            const double v = std::hypot(mean[2 * o], mean[2 * o + 1]);
-            const double target = std::max(opt->rel_tol * std::max(v, 1e-6 * vmax), opt->abs_tol);
-            ok &= e <= target;
+        if (rc) return res->status = rc;
+        items.assign(passes.size(), qmc_batch_item());
+        for (size_t k = 0; k < passes.size(); ++k) {
+            std::memset(&items[k], 0, sizeof(qmc_batch_item));
+            items[k].packed_host = st.packed;
+            items[k].packed_dev = I.dpacked.p;
+            items[k].pass = passes[k];
+            items[k].shifts_dev = (const double *)c->shifts.p;
+            items[k].lambda_dev = (const double *)c->lambda.p;
+            items[k].sums_dev = (double *)c->sums.p;
+            items[k].fails_dev = (int64_t *)c->fails.p;
         }
-        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        if (ok) {
-            status = QMC_OK;
-            break;
-        }
-        if (opt->max_seconds > 0 && el > opt->max_seconds) {
-            status = QMC_ERR_TIMEOUT;
-            break;
-        }
-    }
-    for (int o = 0; o < nord && o < QMC_MAX_ORDERS; ++o) {
-        res->value[o][0] = mean[2 * o];
-        res->value[o][1] = mean[2 * o + 1];
-        res->error[o][0] = err[2 * o];
-        res->error[o][1] = err[2 * o + 1];
+        const size_t need = qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
+        if (!need) return res->status = QMC_ERR_ARG;
+        rc = dev_reserve(c, c->scratch, need);
+        if (!rc) rc = cuda_status(cudaEventRecord(c->ev0, c->stream));
+        if (!rc) rc = qmc_eval_batch(items.data(), (int32_t)items.size(), c->scratch.p, c->scratch.bytes, c->stream);
+        if (!rc) rc = cuda_status(cudaEventRecord(c->ev1, c->stream));
+        if (!rc)
+            rc = cuda_status(cudaMemcpyAsync(st.sums.data(), c->sums.p, st.sums.size() * sizeof(double),
+                                             cudaMemcpyDeviceToHost, c->stream));
+        if (!rc)
+            rc = cuda_status(cudaMemcpyAsync(st.fails.data(), c->fails.p, st.fails.size() * sizeof(int64_t),
+                                             cudaMemcpyDeviceToHost, c->stream));
+        if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
+        if (rc) return res->status = rc;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        kernel_ms_total += ms;
+        st.count(passes, *res);
+        status = st.step(*res);
     }
     res->kernel_ms = kernel_ms_total;
     res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1651,18 +1864,13 @@ struct Request {
     std::vector<double> inv;
     int32_t omin = 0, omax = 0;
     qmc_options opt;
-    std::vector<double> shifts;
-    std::vector<qmc_lattice> ladder;
     std::vector<unsigned char> packed;
     qmc_info info;
     DevBuf dpacked, dshifts, dlambda, dsums, dfails, dprec, dprobe;
-    size_t rung = 0;
-    std::vector<double> lam;
-    std::vector<int> halv;
-    std::vector<int32_t> prec;
-    bool probe_due = false;
-    std::vector<double> sums;
-    std::vector<int64_t> fails;
+    std::vector<double> shifts_copy;          /* the caller's explicit shifts / lattices, copied at submission */
+    std::vector<qmc_lattice> lattices_copy;
+    IntegState st;                 /* the same integration state machine as qmc_integrate */
+    std::vector<qmc_pass> passes;  /* passes of the current round */
     qmc_result res;
     std::chrono::steady_clock::time_point t_submit, t_admit;
     bool cancelled = false;
@@ -1694,7 +1902,7 @@ void release_request(qmc_ctx *c, Request &r) {
 
 void finish(Serving *S, qmc_ctx *c, Request &r, int status) {
     release_request(c, r);
-    if (status != QMC_OK && r.rung < r.ladder.size() && r.res.n_final == 0) r.res.n_final = r.ladder[r.rung].n;
+    if (status != QMC_OK && r.res.n_final == 0 && !r.st.ladder.empty()) r.res.n_final = r.st.ladder[0].n;
     r.res.status = status;
     r.res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
     r.res.queued_seconds = std::chrono::duration<double>(r.t_admit - r.t_submit).count();
@@ -1712,144 +1920,42 @@ int admit(Serving *S, qmc_ctx *c, Request &r) {
     rc = qmc_prepare(r.table.data(), r.table.size(), r.inv.data(), (int32_t)r.inv.size(), r.omin, r.omax,
                      r.packed.data(), r.packed.size(), &r.info);
     if (rc) return rc;
-    const PackedHeader *h = header_of(r.packed.data());
-    const int ns = h->n_sectors, m = (int)(r.shifts.size() / 6);
-    const size_t sums_bytes = (size_t)ns * m * h->n_slots * 2 * sizeof(double);
+    if (!r.shifts_copy.empty()) r.opt.shifts = r.shifts_copy.data();
+    if (!r.lattices_copy.empty()) r.opt.lattices = r.lattices_copy.data();
+    rc = r.st.init(r.packed.data(), r.opt, r.t_submit, r.res);
+    if (rc) return rc;
+    const PackedHeader *h = r.st.h;
+    const int ns = h->n_sectors;
     rc = dev_reserve(c, r.dpacked, r.packed.size());
-    if (!rc) rc = dev_reserve(c, r.dshifts, r.shifts.size() * sizeof(double));
+    if (!rc) rc = dev_reserve(c, r.dshifts, r.st.shifts.size() * sizeof(double));
     if (!rc) rc = dev_reserve(c, r.dlambda, ns * sizeof(double));
-    if (!rc) rc = dev_reserve(c, r.dsums, sums_bytes);
-    if (!rc) rc = dev_reserve(c, r.dfails, (size_t)ns * m * sizeof(int64_t));
+    if (!rc) rc = dev_reserve(c, r.dsums, r.st.sums.size() * sizeof(double));
+    if (!rc) rc = dev_reserve(c, r.dfails, r.st.fails.size() * sizeof(int64_t));
     if (!rc) rc = dev_reserve(c, r.dprec, ns * sizeof(int32_t));
     if (!rc) rc = dev_reserve(c, r.dprobe, (size_t)ns * h->n_slots * 4 * sizeof(double));
     if (rc) return rc;
     rc = cuda_status(cudaMemcpyAsync(r.dpacked.p, r.packed.data(), r.packed.size(), cudaMemcpyHostToDevice, S->stream));
     if (!rc)
-        rc = cuda_status(cudaMemcpyAsync(r.dshifts.p, r.shifts.data(), r.shifts.size() * sizeof(double),
+        rc = cuda_status(cudaMemcpyAsync(r.dshifts.p, r.st.shifts.data(), r.st.shifts.size() * sizeof(double),
                                          cudaMemcpyHostToDevice, S->stream));
-    r.lam.assign(ns, r.opt.lambda > 0 ? r.opt.lambda : 0.5);
-    r.halv.assign(ns, 0);
-    r.prec.assign(ns, 1);
-    r.probe_due = r.opt.precision == QMC_PREC_MIXED;
-    r.sums.assign(sums_bytes / sizeof(double), 0.0);
-    r.fails.assign((size_t)ns * m, 0);
-    r.res.order_min = h->order_min;
-    r.res.n_orders = h->order_max - h->order_min + 1;
     return rc;
 }
 
-/* this rung of the request evaluates in FP32 (mixed policy, as in qmc_integrate) */
-bool fp32_rung(const Request &r) {
-    return r.opt.precision == QMC_PREC_MIXED &&
-           fp32_pays(header_of(r.packed.data()), (int)(r.shifts.size() / 6), r.ladder[r.rung].n);
-}
-
-qmc_pass pass_of(const Request &r) {
-    qmc_pass p;
-    std::memset(&p, 0, sizeof(p));
-    p.lattice = r.ladder[r.rung];
-    p.n_shifts = (int32_t)(r.shifts.size() / 6);
-    p.transform_r = r.opt.transform_r > 0 ? r.opt.transform_r : 3;
-    p.precision = fp32_rung(r) ? QMC_PREC_MIXED : QMC_PREC_FP64;
-    p.block = r.opt.block;
-    p.points_per_thread = r.opt.points_per_thread;
-    p.evaluator = r.opt.evaluator;
-    p.sector_precision = p.precision == QMC_PREC_MIXED ? (const int32_t *)r.dprec.p : nullptr;
-    return p;
-}
-
-/* FP32 budget check of a mixed-precision request (as in qmc_integrate) */
-int probe(Serving *S, qmc_ctx *c, Request &r) {
-    const PackedHeader *h = header_of(r.packed.data());
-    const int ns = h->n_sectors;
-    qmc_pass p = pass_of(r);
-    const int64_t nsamp = r.opt.probe_samples > 0 ? r.opt.probe_samples : 4096;
-    const double budget = (r.opt.fp32_budget > 0 ? r.opt.fp32_budget : 0.1) * r.opt.rel_tol;
-    std::vector<double> pr((size_t)ns * h->n_slots * 4);
-    int rc = cuda_status(cudaMemcpyAsync(r.dlambda.p, r.lam.data(), ns * sizeof(double), cudaMemcpyHostToDevice,
-                                         S->stream));
-    if (!rc)
-        rc = qmc_probe_precision(r.packed.data(), r.dpacked.p, &p, (const double *)r.dshifts.p,
-                                 (const double *)r.dlambda.p, nsamp, (double *)r.dprobe.p, S->stream);
+/* FP32 budget check of a mixed-precision request before the first FP32 pass (as in qmc_integrate); lambda
+   must already be on the device */
+int probe(Serving *S, Request &r) {
+    const PackedHeader *h = r.st.h;
+    std::vector<double> pr((size_t)h->n_sectors * h->n_slots * 4);
+    int rc = qmc_probe_precision(r.packed.data(), r.dpacked.p, &r.passes[r.st.probe_item], (const double *)r.dshifts.p,
+                                 (const double *)r.dlambda.p, r.st.probe_samples(), (double *)r.dprobe.p, S->stream);
     if (!rc)
         rc = cuda_status(cudaMemcpyAsync(pr.data(), r.dprobe.p, pr.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                          S->stream));
     if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
     if (rc) return rc;
-    r.res.fp64_reruns = 0;
-    for (int s2 = 0; s2 < ns; ++s2) {
-        bool bad = false;
-        for (int o = 0; o < h->n_slots; ++o) {
-            const double *v = &pr[((size_t)s2 * h->n_slots + o) * 4];
-            if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
-        }
-        r.prec[s2] = bad ? 0 : 1;
-        r.res.fp64_reruns += bad;
-    }
-    r.probe_due = false;
-    return cuda_status(cudaMemcpyAsync(r.dprec.p, r.prec.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice,
+    r.st.set_precision(pr, r.res);
+    return cuda_status(cudaMemcpyAsync(r.dprec.p, r.st.prec.data(), r.st.ns * sizeof(int32_t), cudaMemcpyHostToDevice,
                                        S->stream));
-}
-
-/* after a pass: lambda halving, combination, convergence; returns true when the request is finished */
-bool advance(Serving *S, qmc_ctx *c, Request &r) {
-    const PackedHeader *h = header_of(r.packed.data());
-    const int ns = h->n_sectors, m = (int)(r.shifts.size() / 6);
-    const int max_h = r.opt.max_halvings > 0 ? r.opt.max_halvings : 6;
-    bool again = false;
-    for (int s2 = 0; s2 < ns; ++s2) {
-        int64_t f = 0;
-        for (int k = 0; k < m; ++k) f += r.fails[(size_t)s2 * m + k];
-        if (f > 0) {
-            r.res.sign_failures += (int32_t)std::min<int64_t>(f, INT32_MAX);
-            if (r.halv[s2] >= max_h) {
-                finish(S, c, r, QMC_ERR_DEFORMATION);
-                return true;
-            }
-            r.lam[s2] *= 0.5;
-            r.halv[s2] += 1;
-            r.res.lambda_halvings += 1;
-            again = true;
-        }
-    }
-    if (again) {
-        r.probe_due = r.opt.precision == QMC_PREC_MIXED;
-        return false;
-    }
-    const qmc_pass p = pass_of(r);
-    const int nord = h->order_max - h->order_min + 1;
-    std::vector<double> Q((size_t)m * nord * 2), mean(nord * 2), err(nord * 2);
-    qmc_combine(r.packed.data(), &p, r.sums.data(), Q.data(), mean.data(), err.data());
-    r.res.n_final = p.lattice.n;
-    for (int o = 0; o < nord && o < QMC_MAX_ORDERS; ++o) {
-        r.res.value[o][0] = mean[2 * o];
-        r.res.value[o][1] = mean[2 * o + 1];
-        r.res.error[o][0] = err[2 * o];
-        r.res.error[o][1] = err[2 * o + 1];
-    }
-    double vmax = 0.0;
-    for (int o = 0; o < nord; ++o) vmax = std::max(vmax, std::hypot(mean[2 * o], mean[2 * o + 1]));
-    bool ok = true;
-    for (int o = 0; o < nord; ++o) {
-        const double e = std::hypot(err[2 * o], err[2 * o + 1]);
-        const double v = std::hypot(mean[2 * o], mean[2 * o + 1]);
-        ok &= e <= std::max(r.opt.rel_tol * std::max(v, 1e-6 * vmax), r.opt.abs_tol);
-    }
-    if (ok) {
-        finish(S, c, r, QMC_OK);
-        return true;
-    }
-    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
-    if (r.opt.max_seconds > 0 && el > r.opt.max_seconds) {
-        finish(S, c, r, QMC_ERR_TIMEOUT);
-        return true;
-    }
-    ++r.rung;
-    if (r.rung >= r.ladder.size() || (r.opt.max_n > 0 && r.ladder[r.rung].n > r.opt.max_n)) {
-        finish(S, c, r, QMC_ERR_NOT_CONVERGED);
-        return true;
-    }
-    return false;
 }
 
 void serve_loop(qmc_ctx *c) {
@@ -1941,12 +2047,6 @@ void serve_loop(qmc_ctx *c) {
                     continue;
                 }
             }
-            int rc = (r->probe_due && fp32_rung(*r)) ? probe(S, c, *r) : QMC_OK;
-            if (rc) {
-                std::lock_guard<std::mutex> g(c->mu);
-                finish(S, c, *r, rc);
-                continue;
-            }
             std::lock_guard<std::mutex> g2(S->mu);
             r->state = REQ_ACTIVE;
             S->active.push_back(r);
@@ -1958,54 +2058,60 @@ void serve_loop(qmc_ctx *c) {
             batch = S->active;
         }
         if (batch.empty()) continue;
-        /* this round: one pass per active request, in shared launches (no context lock held meanwhile) */
+        /* this round: one step of every active request (its passes: one per lattice rung among the sectors it
+           evaluates), all in shared launches; no context lock is held meanwhile */
         int rc = QMC_OK;
         for (auto &r : batch) {
-            if (r->probe_due && fp32_rung(*r)) rc = probe(S, c, *r);
-            if (rc) break;
-            rc = cuda_status(cudaMemcpyAsync(r->dlambda.p, r->lam.data(), r->lam.size() * sizeof(double),
+            r->st.passes(r->passes, (const int32_t *)r->dprec.p);
+            rc = cuda_status(cudaMemcpyAsync(r->dlambda.p, r->st.lam.data(), r->st.lam.size() * sizeof(double),
                                              cudaMemcpyHostToDevice, S->stream));
+            if (!rc && r->st.probe_item >= 0) rc = probe(S, *r);
             if (rc) break;
         }
-        std::vector<qmc_batch_item> items(batch.size());
+        std::vector<qmc_batch_item> items;
+        std::vector<size_t> first(batch.size() + 1, 0); /* items of batch[i]: [first[i], first[i + 1]) */
         for (size_t i = 0; i < batch.size() && !rc; ++i) {
             Request &r = *batch[i];
-            qmc_batch_item &b = items[i];
-            std::memset(&b, 0, sizeof(b));
-            b.packed_host = r.packed.data();
-            b.packed_dev = r.dpacked.p;
-            b.pass = pass_of(r);
-            b.shifts_dev = (const double *)r.dshifts.p;
-            b.lambda_dev = (const double *)r.dlambda.p;
-            b.sums_dev = (double *)r.dsums.p;
-            b.fails_dev = (int64_t *)r.dfails.p;
+            for (const qmc_pass &ps : r.passes) {
+                qmc_batch_item b;
+                std::memset(&b, 0, sizeof(b));
+                b.packed_host = r.packed.data();
+                b.packed_dev = r.dpacked.p;
+                b.pass = ps;
+                b.shifts_dev = (const double *)r.dshifts.p;
+                b.lambda_dev = (const double *)r.dlambda.p;
+                b.sums_dev = (double *)r.dsums.p;
+                b.fails_dev = (int64_t *)r.dfails.p;
+                items.push_back(b);
+            }
+            first[i + 1] = items.size();
         }
         size_t need = rc ? 0 : qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
         if (!rc && !need) rc = QMC_ERR_ARG;
         if (!rc) {
             std::lock_guard<std::mutex> g(c->mu);
             /* the round shrinks (later requests wait) when its scratch would not fit the budget */
-            while (items.size() > 1 && c->used - S->scratch.bytes + ((need + 4095) & ~size_t(4095)) > c->budget) {
-                items.pop_back();
+            while (batch.size() > 1 && c->used - S->scratch.bytes + ((need + 4095) & ~size_t(4095)) > c->budget) {
                 batch.pop_back();
+                items.resize(first[batch.size()]);
                 need = qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
             }
             rc = dev_reserve(c, S->scratch, need);
         }
         if (!rc) rc = qmc_eval_batch(items.data(), (int32_t)items.size(), S->scratch.p, S->scratch.bytes, S->stream);
         for (size_t i = 0; i < batch.size() && !rc; ++i) {
-            Request &r = *batch[i];
-            rc = cuda_status(cudaMemcpyAsync(r.sums.data(), r.dsums.p, r.sums.size() * sizeof(double),
+            IntegState &st = batch[i]->st;
+            rc = cuda_status(cudaMemcpyAsync(st.sums.data(), batch[i]->dsums.p, st.sums.size() * sizeof(double),
                                              cudaMemcpyDeviceToHost, S->stream));
             if (!rc)
-                rc = cuda_status(cudaMemcpyAsync(r.fails.data(), r.dfails.p, r.fails.size() * sizeof(int64_t),
+                rc = cuda_status(cudaMemcpyAsync(st.fails.data(), batch[i]->dfails.p, st.fails.size() * sizeof(int64_t),
                                                  cudaMemcpyDeviceToHost, S->stream));
         }
         if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
         {
             std::lock_guard<std::mutex> g2(S->mu);
             S->stats.rounds += 1;
-            S->stats.batched_passes += (int64_t)batch.size();
+            S->stats.batched_passes += (int64_t)items.size();
         }
         std::vector<std::shared_ptr<Request>> done;
         {
@@ -2017,9 +2123,12 @@ void serve_loop(qmc_ctx *c) {
                     done.push_back(rp);
                     continue;
                 }
-                r.res.passes += 1;
-                r.res.evals += (int64_t)r.info.n_sectors * (int64_t)(r.shifts.size() / 6) * r.ladder[r.rung].n;
-                if (advance(S, c, r)) done.push_back(rp);
+                r.st.count(r.passes, r.res);
+                const int st = r.st.step(r.res);
+                if (st != QMC_PENDING) {
+                    finish(S, c, r, st);
+                    done.push_back(rp);
+                }
             }
         }
         std::lock_guard<std::mutex> g2(S->mu);
@@ -2066,20 +2175,14 @@ int qmc_submit(qmc_ctx *c, int32_t integral_id, const double *invariants, int32_
     std::memset(&r->res, 0, sizeof(r->res));
     const int m = opt->n_shifts > 0 ? opt->n_shifts : 16;
     if (m < 2 || m > 4096 || opt->rel_tol < 0) return QMC_ERR_ARG;
-    if (opt->shifts) r->shifts.assign(opt->shifts, opt->shifts + (size_t)m * 6);
-    else splitmix_shifts(opt->seed, m, r->shifts);
+    if (opt->n_lattices > 0 && !opt->lattices) return QMC_ERR_ARG;
+    if (opt->n_lattices <= 0 && std::max(0, opt->ladder_start) >= QMC_BUILTIN_LATTICES) return QMC_ERR_ARG;
+    if (opt->shifts) r->opt.shifts = nullptr; /* copied below: the caller's array need not outlive the call */
+    if (opt->shifts) r->shifts_copy.assign(opt->shifts, opt->shifts + (size_t)m * 6);
     if (opt->n_lattices > 0) {
-        if (!opt->lattices) return QMC_ERR_ARG;
-        r->ladder.assign(opt->lattices, opt->lattices + opt->n_lattices);
-    } else {
-        for (int i = std::max(0, opt->ladder_start); i < QMC_BUILTIN_LATTICES; ++i) {
-            qmc_lattice L;
-            L.n = qmc_builtin_lattice[i].n;
-            for (int j = 0; j < QMC_MAX_DIM; ++j) L.z[j] = qmc_builtin_lattice[i].z[j];
-            r->ladder.push_back(L);
-        }
+        r->lattices_copy.assign(opt->lattices, opt->lattices + opt->n_lattices);
+        r->opt.lattices = nullptr;
     }
-    if (r->ladder.empty()) return QMC_ERR_ARG;
     r->t_submit = std::chrono::steady_clock::now();
     r->t_admit = r->t_submit;
     {

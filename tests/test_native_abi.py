@@ -151,6 +151,38 @@ def test_combine_matches_oracle(cfg):
     assert np.allclose(np.hypot(err[:, 0], err[:, 1]), eo, rtol=1e-12)
 
 
+@pytest.mark.parametrize("cfg", [W.CONFIG0, W.CONFIG1], ids=lambda c: c.name)
+def test_combine_sectors_matches_oracle_with_per_sector_lattices(cfg):
+    """Sectors from lattices of different sizes: each sector's sum enters Eq. 19 with its own 1/n_s, so the oracle's
+    single-n combination of the rescaled sums n/n_s * v_s gives the same totals."""
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
+    prob = OI.make_problem(cfg.topology, cfg.point, cfg.order_min, cfg.order_max)
+    m, n = 5, 1021
+    rng = np.random.default_rng(2)
+    slots = prep.info.n_slots
+    ladder = [1021, 2039, 4093, 8191]
+    n_s = [ladder[s % len(ladder)] for s in range(prep.info.n_sectors)]
+    sums = np.zeros((prep.info.n_sectors, m, slots, 2))
+    per = []
+    for s, sec in enumerate(prob.sectors):
+        nout = prob.kmax + sec.sigma + 1
+        v = rng.normal(size=(m, nout)) + 1j * rng.normal(size=(m, nout))
+        per.append(v * (n / n_s[s]))
+        sums[s, :, :nout, 0] = v.real
+        sums[s, :, :nout, 1] = v.imag
+    Q, mean, err = api.combine_sectors(prep, m, n_s, sums)
+    Qo = OI.combine(prob, per, n)
+    mo, eo = OI.mean_and_error(Qo)
+    assert np.allclose(Q, Qo, rtol=1e-13, atol=1e-15)
+    assert np.allclose(mean, mo, rtol=1e-13, atol=1e-15)
+    assert np.allclose(np.hypot(err[:, 0], err[:, 1]), eo, rtol=1e-12)
+    # equal sizes reduce to qmc_combine
+    Q2, mean2, _ = api.combine_sectors(prep, m, [n] * prep.info.n_sectors, sums)
+    Q3, mean3, _ = api.combine(prep, api.make_pass(n, [1] * 6, m), sums)
+    assert np.array_equal(Q2, Q3) and np.array_equal(mean2, mean3)
+
+
 def _prep_status(blob, kin, omin=0, omax=0):
     inv = np.ascontiguousarray(np.asarray(kin, dtype=np.float64))
     info = N.qmc_info()
