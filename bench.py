@@ -41,6 +41,7 @@ import numpy as np  # noqa: E402
 import workloads as W  # noqa: E402
 
 LOG2_N = 24
+N_PREC_FP64 = 0
 N_SHIFTS = 16
 LAMBDA = 0.5
 METRIC = "integrand evals/s"
@@ -81,6 +82,8 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
     ap.add_argument("--serving", type=int, default=0,
                     help="run only the serving workload with this many requests and print its JSON line")
+    ap.add_argument("--serving-baseline", action="store_true",
+                    help="with --serving: also run the requests one at a time through the plain FP64 path")
     return ap.parse_args()
 
 
@@ -168,12 +171,14 @@ def korobov_vector(n, a=76):
     return [pow(a, j, n) for j in range(6)]
 
 
-def cpu_baseline(n_log2=18):
-    """The oracle as it stands (plain C, OpenMP over all host cores) on a bounded sample of the workload."""
+def cpu_baseline(cfg=None, n_log2=0):
+    """The oracle as it stands (plain C, OpenMP over all host cores) on a bounded sample of the workload:
+    n = largest prime below 2^18 for the one-loop box, 2^12 for a double box (about 10-20 s of CPU work)."""
     from oracle import integrate as OI
     from oracle import lattice as OL
-    cfg = W.CONFIG1
-    prob = OI.make_problem(cfg.topology, {**cfg.point}, 0, 0)
+    cfg = cfg or W.CONFIG1
+    n_log2 = n_log2 or (18 if cfg.topology.loops == 1 else 12)
+    prob = OI.make_problem(cfg.topology, {**cfg.point}, cfg.order_min, cfg.order_max)
     n = OL.prime_below(1 << n_log2)
     z = korobov_vector(n)
     shifts = W.shifts(12345, N_SHIFTS)
@@ -183,8 +188,8 @@ def cpu_baseline(n_log2=18):
     dt = time.perf_counter() - t0
     evals = len(prob.sectors) * N_SHIFTS * n
     return {"value": evals / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
-            "sample": f"massive box, n={n} (largest prime < 2^{n_log2}), {N_SHIFTS} shifts, 4 sectors = {evals} "
-                      f"evals in {dt:.2f} s"}
+            "sample": f"{cfg.name}, n={n} (largest prime < 2^{n_log2}), {N_SHIFTS} shifts, {len(prob.sectors)} "
+                      f"sectors = {evals} evals in {dt:.2f} s"}
 
 
 def main_reference(args):
@@ -401,8 +406,11 @@ def main_ours(args):
 
     extras = {"mixed": mixed}
     if not args.no_extras and rank == 0:
-        extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream)
-        extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, precision=N.QMC_PREC_MIXED)
+        seeds = 32 if cfg.topology.loops == 1 else 6
+        extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream, seeds, lock_step=1)
+        extras["time_to_1e-3_fp64_per_sector"] = time_to_accuracy(api, blob, cfg, local, stream, seeds)
+        extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, seeds,
+                                                         precision=N.QMC_PREC_MIXED)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -422,7 +430,7 @@ def main_ours(args):
             "clocks": clocks,
         }
         if not args.no_extras:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"] = cpu_baseline(cfg)
         out.update(extras)
         print(json.dumps(out))
     if dist:
@@ -434,10 +442,18 @@ def maxm_of(prep):
     return 0 if k == 0 else (2 if k <= 2 else 4)
 
 
-def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0):
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+
+def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0, baseline=False, max_seconds=300.0):
     """Config 4: Poisson arrivals of requests for random integrals (massless box, massive box, planar and
     non-planar double box) at random s ~ U[4.5,12], t ~ U[-4,-0.5], each integrated to 1e-3 relative error with 16
-    shifts by the serving loop (continuous batching).  Latency = submission to completion."""
+    shifts by the serving loop (continuous batching, per-sector lattices).  Latency = submission to completion.
+    baseline: the same requests afterwards one at a time through the plain FP64 per-integral path (qmc_integrate,
+    FP64, all sectors on one lattice ladder); its latency is the request's own integration time, i.e. as if each
+    arrived at an idle GPU, which favours the baseline."""
     from paper_1508_02512_gb300 import api
     from paper_1508_02512_gb300 import tables as T
     arrivals = W.serving_arrivals(n_requests, rate, seed)
@@ -479,34 +495,54 @@ def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0):
     for (k_, ci, _), r in done.values():
         per_cfg.setdefault(W.CONFIGS[ci].name, []).append(r.seconds)
     ctx.close()
-    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
-    return {"requests": n_requests, "converged": ok, "offered_rate_per_s": rate, "wall_s": wall,
-            "throughput_req_per_s": n_requests / wall, "p50_s": statistics.median(lat), "p99_s": p99,
-            "per_integral_p50_s": {k2: statistics.median(v) for k2, v in per_cfg.items()},
-            "rounds": stats.rounds - base.rounds, "batched_passes": stats.batched_passes - base.batched_passes,
-            "peak_active": stats.peak_active, "precision": "f32+f64" if precision == 1 else "f64",
-            "codegen_compile_ms": compile_ms,
-            "rel_tol": 1e-3, "shifts": N_SHIFTS}
+    out = {"requests": n_requests, "converged": ok, "offered_rate_per_s": rate, "wall_s": wall,
+           "throughput_req_per_s": n_requests / wall, "p50_s": statistics.median(lat), "p99_s": pct(lat, 0.99),
+           "per_integral_p50_s": {k2: statistics.median(v) for k2, v in per_cfg.items()},
+           "rounds": stats.rounds - base.rounds, "batched_passes": stats.batched_passes - base.batched_passes,
+           "peak_active": stats.peak_active, "precision": "f32+f64" if precision == 1 else "f64",
+           "codegen_compile_ms": compile_ms, "rel_tol": 1e-3, "shifts": N_SHIFTS}
+    if baseline:
+        ctx = api.Context(device, 8 << 30)
+        ids = [ctx.load_sectors(b) for b in blobs]
+        secs, ok_b, evals = [], 0, 0
+        for k, (at, ci, sv, tv) in enumerate(arrivals):
+            cfg = W.CONFIGS[ci]
+            ctx.set_kinematics(ids[ci], W.kinematics(cfg.topology, **{**cfg.point, "s": sv, "t": tv}),
+                               cfg.order_min, cfg.order_max)
+            r = ctx.integrate(ids[ci], rel_tol=1e-3, n_shifts=N_SHIFTS, seed=100 + k, lam=LAMBDA,
+                              precision=N_PREC_FP64, lock_step=1, max_seconds=max_seconds)
+            secs.append(r.seconds)
+            ok_b += r.status == 0
+            evals += r.evals
+        ctx.close()
+        out["fp64_per_integral_baseline"] = {
+            "path": "qmc_integrate, FP64, one integral at a time, all sectors on one lattice ladder",
+            "converged": ok_b, "max_seconds": max_seconds, "total_s": sum(secs),
+            "p50_s": statistics.median(secs), "p99_s": pct(secs, 0.99), "evals": evals}
+    return out
 
 
-def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0):
-    """qmc_integrate of the massive box to 1e-3 relative error (lattice ladder from 2^10), over 32 seeds."""
-    ctx = api.Context(device, 1 << 30, stream)
+def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0, lock_step=0):
+    """qmc_integrate of the integral to 1e-3 relative error (lattice ladder from 2^10), over `seeds` seeds.
+    precision FP64 with lock_step = 1 is the plain FP64 per-integral path (all sectors on one ladder)."""
+    ctx = api.Context(device, 4 << 30, stream)
     iid = ctx.load_sectors(blob)
-    ctx.set_kinematics(iid, cfg.kin, 0, 0)
-    ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=999, lam=LAMBDA, precision=precision)  # warm-up
-    ts, ns, ok = [], [], 0
+    ctx.set_kinematics(iid, cfg.kin, cfg.order_min, cfg.order_max)
+    kw = dict(rel_tol=1e-3, n_shifts=N_SHIFTS, lam=LAMBDA, precision=precision, lock_step=lock_step, max_seconds=120)
+    ctx.integrate(iid, seed=999, **kw)  # warm-up (kernels, generated evaluator)
+    ts, ns, ev, ok = [], [], [], 0
     for s in range(seeds):
         t0 = time.perf_counter()
-        r = ctx.integrate(iid, rel_tol=1e-3, n_shifts=N_SHIFTS, seed=1000 + s, lam=LAMBDA, precision=precision)
+        r = ctx.integrate(iid, seed=1000 + s, **kw)
         ts.append(1e3 * (time.perf_counter() - t0))
         ns.append(r.n_final)
+        ev.append(r.evals)
         ok += r.status == 0
     ctx.close()
-    ts.sort()
-    return {"p50_ms": statistics.median(ts), "p99_ms": ts[min(len(ts) - 1, int(math.ceil(0.99 * len(ts))) - 1)],
-            "seeds": seeds, "converged": ok, "median_final_n": int(statistics.median(ns)),
-            "precision": "f64" if precision == 0 else "f32+f64"}
+    return {"p50_ms": statistics.median(ts), "p99_ms": pct(ts, 0.99), "seeds": seeds, "converged": ok,
+            "median_final_n": int(statistics.median(ns)), "median_evals": int(statistics.median(ev)),
+            "precision": "f64" if precision == 0 else "f32+f64",
+            "lattices": "one ladder for all sectors" if lock_step else "per sector"}
 
 
 def profile_pass(precision="fp64", integral="massive_box"):
@@ -535,7 +571,7 @@ def profile_pass(precision="fp64", integral="massive_box"):
 if __name__ == "__main__":
     a = parse()
     if a.serving:
-        print(json.dumps({"metric": "serving time-to-1e-3", **serving_run(a.serving)}))
+        print(json.dumps({"metric": "serving time-to-1e-3", **serving_run(a.serving, baseline=a.serving_baseline)}))
     elif a.profile_pass:
         profile_pass(a.precision, a.integral)
     elif a.impl == "reference":
