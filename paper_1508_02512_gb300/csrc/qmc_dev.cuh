@@ -565,10 +565,22 @@ struct cf {
     float x, y;
 };
 DEV cf mkf(float x, float y) { return cf{x, y}; }
-DEV cf caddf(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
-DEV cf csubf(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
-DEV cf cscalef(cf a, float s) { return cf{a.x * s, a.y * s}; }
-DEV cf cmulf(cf a, cf b) { return cf{fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
+/* Complex FP32 arithmetic on GB300's packed two-lane FP32 instructions (one instruction for the real and the
+   imaginary part); each lane rounds exactly like the scalar form (x*y + z with one rounding, products rounded
+   before they are added). */
+DEV float2 f2_(cf a) { return make_float2(a.x, a.y); }
+DEV cf cf_(float2 a) { return cf{a.x, a.y}; }
+DEV cf caddf(cf a, cf b) { return cf_(__fadd2_rn(f2_(a), f2_(b))); }
+DEV cf csubf(cf a, cf b) { return cf_(__fadd2_rn(f2_(a), make_float2(-b.x, -b.y))); }
+DEV cf cscalef(cf a, float s) { return cf_(__fmul2_rn(f2_(a), make_float2(s, s))); }
+/* (a.x b.x - a.y b.y, a.x b.y + a.y b.x) = (a.x, a.x) * (b.x, b.y) + rn((-a.y, a.y) * (b.y, b.x)) */
+DEV cf cmulf(cf a, cf b) {
+    return cf_(__ffma2_rn(make_float2(a.x, a.x), f2_(b), __fmul2_rn(make_float2(-a.y, a.y), make_float2(b.y, b.x))));
+}
+/* a + (c_hi + c_lo) m for a real coefficient split in two floats and a complex monomial m */
+DEV cf cfma2f(float hi, float lo, cf m, cf a) {
+    return cf_(__ffma2_rn(make_float2(hi, hi), f2_(m), __ffma2_rn(make_float2(lo, lo), f2_(m), f2_(a))));
+}
 DEV cf cinvf(cf a) {
     const float d = __frcp_rn(fmaf(a.x, a.x, a.y * a.y));
     return cf{a.x * d, -a.y * d};
@@ -682,8 +694,7 @@ DEV cf poly_cf(const Tab &T, int base, int n, const cf *z) {
                 for (int k = 0; k < e; ++k) m = cmulf(m, z[j]);
             }
         }
-        acc.x = fmaf(hi, m.x, fmaf(lo, m.x, acc.x));
-        acc.y = fmaf(hi, m.y, fmaf(lo, m.y, acc.y));
+        acc = cfma2f(hi, lo, m, acc);
     }
     return acc;
 }

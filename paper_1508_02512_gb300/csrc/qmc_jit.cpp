@@ -38,7 +38,7 @@
 
 namespace {
 
-#define QMC_JIT_GENERATOR_VERSION 2u
+#define QMC_JIT_GENERATOR_VERSION 3u
 #define QMC_GEN_INLINE_TERMS 2048 /* families with more terms get out-of-line sector functions */
 
 const PackedHeader *hdr(const void *p) {
@@ -144,10 +144,7 @@ void emit_fma(std::string &o, const PolySet &P, const Entry &E, const std::strin
         std::snprintf(b, sizeof(b), "%sa%d = fmaf(C[%d].hi, %s, fmaf(C[%d].lo, %s, a%d));\n", ind.c_str(), E.acc,
                       E.term, m.c_str(), E.term, m.c_str(), E.acc);
     } else {
-        std::snprintf(b, sizeof(b),
-                      "%sa%d.x = fmaf(C[%d].hi, %s.x, fmaf(C[%d].lo, %s.x, a%d.x)); "
-                      "a%d.y = fmaf(C[%d].hi, %s.y, fmaf(C[%d].lo, %s.y, a%d.y));\n",
-                      ind.c_str(), E.acc, E.term, m.c_str(), E.term, m.c_str(), E.acc, E.acc, E.term, m.c_str(),
+        std::snprintf(b, sizeof(b), "%sa%d = cfma2f(C[%d].hi, C[%d].lo, %s, a%d);\n", ind.c_str(), E.acc, E.term,
                       E.term, m.c_str(), E.acc);
     }
     o += b;

@@ -111,15 +111,14 @@ def test_every_term_enters_its_polynomial_once(cfg):
         for name, ranges in groups.items():
             body = funcs[name]
             # (accumulator, term) of every statement that adds a term; a complex FMA writes .x and .y
-            pairs = re.findall(r"a(\d+)(?:\.[xy])? (?:=|\+=) (?:fmaf\()?C\[(\d+)\]\.hi", body)
+            pairs = re.findall(r"a(\d+)(?:\.[xy])? (?:=|\+=) (?:fmaf\(|cfma2f\()?C\[(\d+)\]\.hi", body)
             got = {}
             for acc, term in pairs:
                 got.setdefault(int(term), set()).add(int(acc))
             want = {i: {a} for a, (lo, hi) in enumerate(ranges) for i in range(lo, hi)}
             assert got == want, (cfg.name, name)
             n_stmt = len(pairs)
-            n_expected = sum(2 if (name.startswith("qg_ufc") and not constant) else 1
-                             for constant in [not any(terms[s.term0 + i]["e"]) for i in want])
+            n_expected = len(want)
             assert n_stmt == n_expected, (cfg.name, name)
 
 
@@ -132,6 +131,9 @@ SHIM = r"""
 struct cf { float x, y; };
 static inline cf mkf(float x, float y) { return cf{x, y}; }
 static inline cf cmulf(cf a, cf b) { return cf{fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
+static inline cf cfma2f(float hi, float lo, cf m, cf a) {
+    return cf{fmaf(hi, m.x, fmaf(lo, m.x, a.x)), fmaf(hi, m.y, fmaf(lo, m.y, a.y))};
+}
 struct PackedTermF { float hi, lo; unsigned char e[8]; };
 """
 
