@@ -51,12 +51,14 @@ extern "C" {
 
 enum { QMC_PREC_FP64 = 0, QMC_PREC_MIXED = 1 };
 
-/* Polynomial evaluator of the FP32 evaluation (QMC_PREC_MIXED passes; FP64 evaluation always reads the table):
- *   QMC_EVAL_AUTO (0)      = QMC_EVAL_GENERATED
+/* Polynomial evaluator of a pass:
+ *   QMC_EVAL_AUTO (0)      generated for FP32 evaluation; for FP64 evaluation generated when the sectors have
+ *                          at most 3 variables, the table otherwise (measured faster there on GB300)
  *   QMC_EVAL_TABLE         the kernels walk each sector's staged term table and decode its exponents per point
  *   QMC_EVAL_GENERATED     straight-line code generated for the family of sector tables (same exponents) and
- *                          compiled at run time with NVRTC on first use (qmc_gen_compile); the coefficients
- *                          are still read from the staged table, so kinematic points of one family share it. */
+ *                          compiled at run time with NVRTC on first use (qmc_gen_compile), in each precision
+ *                          the pass evaluates in; the coefficients are still read from the staged table, so
+ *                          kinematic points of one family share it. */
 enum { QMC_EVAL_AUTO = 0, QMC_EVAL_TABLE = 1, QMC_EVAL_GENERATED = 2 };
 
 /* A rank-1 lattice (Eq. 17): prime size n and generating vector z (a dim-d sector uses z[0..d-1]). */
@@ -203,6 +205,8 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
  * Generated evaluators (the paper evaluates a fixed, hand-written integrand per sector; this is the
  * library's way of getting the same straight-line arithmetic for any table).  A family = the sector tables
  * with identical exponent structure (same topology and kinematic class, any kinematic point).
+ * precision: QMC_PREC_MIXED for the FP32 evaluator (coefficients as hi + lo float pairs), QMC_PREC_FP64 for
+ *   the FP64 one (one FMA per term on the FP64 coefficients).
  * qmc_gen_source: writes the CUDA source generated for the family of `packed_host` (an image from qmc_prepare)
  *   into buf (cap bytes, NUL-terminated); *len receives the size needed (call with buf = NULL to query).
  *   Host only.  Errors: QMC_ERR_ARG, QMC_ERR_MEMORY (cap too small).
@@ -223,8 +227,8 @@ typedef struct {
     int32_t cached, reserved;
 } qmc_gen_info;
 
-int qmc_gen_source(const void *packed_host, char *buf, size_t cap, size_t *len);
-int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info);
+int qmc_gen_source(const void *packed_host, int32_t precision, char *buf, size_t cap, size_t *len);
+int qmc_gen_compile(const void *packed_host, int32_t precision, int32_t load, qmc_gen_info *info);
 
 /*
  * Launch-shape autotuner (the paper fixes no launch shape; this is the library's).  qmc_autotune runs the

@@ -123,8 +123,8 @@ PROTOTYPES = {
     "qmc_autotune": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_size_t,
                              POINTER(qmc_tune_result), c_void_p]),
     "qmc_autotune_clear": (c_int, []),
-    "qmc_gen_source": (c_int, [c_void_p, c_void_p, c_size_t, POINTER(c_size_t)]),
-    "qmc_gen_compile": (c_int, [c_void_p, c_int32, POINTER(qmc_gen_info)]),
+    "qmc_gen_source": (c_int, [c_void_p, c_int32, c_void_p, c_size_t, POINTER(c_size_t)]),
+    "qmc_gen_compile": (c_int, [c_void_p, c_int32, c_int32, POINTER(qmc_gen_info)]),
     "qmc_eval_points": (c_int, [c_void_p, c_void_p, c_int32, POINTER(qmc_pass), c_void_p, c_double, c_void_p,
                                 c_int64, c_void_p, c_void_p, c_void_p]),
     "qmc_builtin_lattices": (c_int, [POINTER(qmc_lattice), c_int32]),

@@ -61,19 +61,19 @@ def combine_sectors(prep: Prepared, n_shifts: int, n_sector, sums: np.ndarray):
     return Q[..., 0] + 1j * Q[..., 1], mean[:, 0] + 1j * mean[:, 1], err
 
 
-def gen_source(prep) -> str:
-    """qmc_gen_source: the CUDA source generated for the family of a prepared integral."""
+def gen_source(prep, precision: int = N.QMC_PREC_MIXED) -> str:
+    """qmc_gen_source: the CUDA source generated for the family of a prepared integral (FP32 or FP64)."""
     n = ctypes.c_size_t()
-    N.check(N.lib().qmc_gen_source(prep.packed, None, 0, ctypes.byref(n)), "qmc_gen_source")
+    N.check(N.lib().qmc_gen_source(prep.packed, precision, None, 0, ctypes.byref(n)), "qmc_gen_source")
     buf = ctypes.create_string_buffer(n.value)
-    N.check(N.lib().qmc_gen_source(prep.packed, buf, n.value, ctypes.byref(n)), "qmc_gen_source")
+    N.check(N.lib().qmc_gen_source(prep.packed, precision, buf, n.value, ctypes.byref(n)), "qmc_gen_source")
     return buf.value.decode()
 
 
-def gen_compile(prep, load: bool = True) -> N.qmc_gen_info:
+def gen_compile(prep, load: bool = True, precision: int = N.QMC_PREC_MIXED) -> N.qmc_gen_info:
     """qmc_gen_compile: compile (load=False: compile only, no device) or compile-and-cache the family's module."""
     info = N.qmc_gen_info()
-    N.check(N.lib().qmc_gen_compile(prep.packed, 1 if load else 0, ctypes.byref(info)), "qmc_gen_compile")
+    N.check(N.lib().qmc_gen_compile(prep.packed, precision, 1 if load else 0, ctypes.byref(info)), "qmc_gen_compile")
     return info
 
 

@@ -226,6 +226,37 @@ DEV cd det_deform(const double (&A)[S][S], double lam) {
     }
 }
 
+/* ------------------------------------------------------------------ polynomial evaluators (FP64)
+   The integrand asks an evaluator for
+     UFr(t, U, F)          U~ and F~ at real t (undeformed sectors, Eqs. 7-8),
+     GH(t, g, h)           g_j = dF~/dt_j and h_p = d2F~/dt_j dt_k (p over j <= k, row-major upper triangle) at
+                           real t, the inputs of the deformation of Eq. 14,
+     UFc(z, needU, U, F)   U~ (1 when needU is false) and F~ at the deformed point z.
+   TabPol walks the staged term table; the generated FP64 evaluator (run-time compiled per family) holds each
+   sector's monomials as straight-line code and reads only the coefficients from the same table. */
+template <int S>
+struct TabPol {
+    const PackedTerm *T;
+    const PackedSector *s;
+    DEV static TabPol make(const PackedTerm *T, const PackedSector &s, int) { return TabPol{T, &s}; }
+    DEV void UFr(const double *t, double &U, double &F) const {
+        U = poly_r<S>(T, s->nU, t);
+        F = poly_r<S>(T + s->nU, s->nF, t);
+    }
+    DEV void GH(const double *t, double *g, double *h) const {
+        const PackedTerm *TG = T + s->nU + s->nF;
+        const PackedTerm *TH = TG + s->nG;
+#pragma unroll
+        for (int j = 0; j < S; ++j) g[j] = poly_r<S>(TG + s->gstart[j], s->gstart[j + 1] - s->gstart[j], t);
+#pragma unroll
+        for (int p = 0; p < S * (S + 1) / 2; ++p) h[p] = poly_r<S>(TH + s->hstart[p], s->hstart[p + 1] - s->hstart[p], t);
+    }
+    DEV void UFc(const cd *z, bool needU, cd &U, cd &F) const {
+        U = needU ? poly_c<S>(T, s->nU, z) : mk(1.0, 0.0);
+        F = poly_c<S>(T + s->nU, s->nF, z);
+    }
+};
+
 /* ------------------------------------------------------------------ sector integrand */
 struct Exps {
     int eU0, eU1, eF0, eF1;
@@ -233,14 +264,12 @@ struct Exps {
 
 /* G at the point tt (t with the subset Y zeroed): returns its eps^0 value G0 and the eps-coefficient X of
    its logarithm, so that G(eps) = G0 exp(X eps) (Sec. II, Eq. 9 with the deformation of Eq. 14). */
-template <int S, bool DEF, int MAXM>
-DEV void eval_G(const PackedSector &s, const PackedTerm *__restrict__ T, const double *tt, const double *ttm,
-                const double *Lt, double lam, int M, const Exps &ex, cd &G0, cd &X, uint32_t &fails) {
-    const PackedTerm *TU = T;
-    const PackedTerm *TF = T + s.nU;
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void eval_G(const PackedSector &s, const Pol &P, const double *tt, const double *ttm, const double *Lt, double lam,
+                int M, const Exps &ex, cd &G0, cd &X, uint32_t &fails) {
     if constexpr (!DEF) {
-        const double U = poly_r<S>(TU, s.nU, tt);
-        double F = poly_r<S>(TF, s.nF, tt);
+        double U, F;
+        P.UFr(tt, U, F);
         if (s.kind == 1) F = -F;
         double g = s.D * ipow(U, ex.eU0) * ipow(F, -ex.eF0);
 #pragma unroll
@@ -257,21 +286,17 @@ DEV void eval_G(const PackedSector &s, const PackedTerm *__restrict__ T, const d
             X = mk(x, 0.0);
         }
     } else {
-        const PackedTerm *TG = TF + s.nF;
-        const PackedTerm *TH = TG + s.nG;
-        double g[S];
-#pragma unroll
-        for (int j = 0; j < S; ++j) g[j] = poly_r<S>(TG + s.gstart[j], s.gstart[j + 1] - s.gstart[j], tt);
+        double g[S], h[S * (S + 1) / 2];
+        P.GH(tt, g, h);
         double A[S][S];
         int p = 0;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
 #pragma unroll
             for (int k = j; k < S; ++k) {
-                const double h = poly_r<S>(TH + s.hstart[p], s.hstart[p + 1] - s.hstart[p], tt);
+                A[j][k] = tt[j] * ttm[j] * h[p];
+                if (k != j) A[k][j] = tt[k] * ttm[k] * h[p];
                 ++p;
-                A[j][k] = tt[j] * ttm[j] * h;
-                if (k != j) A[k][j] = tt[k] * ttm[k] * h;
             }
         }
 #pragma unroll
@@ -285,8 +310,8 @@ DEV void eval_G(const PackedSector &s, const PackedTerm *__restrict__ T, const d
             q[j] = mk(1.0, -d);
         }
         const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
-        const cd U = needU ? poly_c<S>(TU, s.nU, z) : mk(1.0, 0.0);
-        const cd F = poly_c<S>(TF, s.nF, z);
+        cd U, F;
+        P.UFc(z, needU, U, F);
         fails += (F.y > 0.0) ? 1u : 0u;
         cd G = cscale(detJ, s.D);
         if (ex.eU0 != 0) G = cmul(G, cipow(U, ex.eU0));
@@ -322,8 +347,8 @@ DEV void eval_G(const PackedSector &s, const PackedTerm *__restrict__ T, const d
 /* w(x) * (sector integrand) at x, as series slots 0..M (slot n = coefficient of eps^(n - sigma)).
    Subtraction of Eq. (11) with alpha = -1, regrouped over the zeroed subsets Y of the singular set S:
    eps^sigma I = sum_Y G_Y(eps) V_Y(eps),  V_Y = prod_{j in S\Y} eps t_j^{-1+B eps} prod_{j in Y} (1/B_j - eps t_j^{-1+B eps}). */
-template <int S, bool DEF, int MAXM>
-DEV void point_integrand(const PackedSector &s, const PackedTerm *__restrict__ T, const double *x, int r, double lam,
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void point_integrand(const PackedSector &s, const Pol &P, const double *x, int r, double lam,
                          const Exps &ex, cd (&out)[MAXM + 1], uint32_t &fails) {
     double t[S], tm[S], w = 1.0;
     bool bad = false;
@@ -357,7 +382,7 @@ DEV void point_integrand(const PackedSector &s, const PackedTerm *__restrict__ T
             ttm[j] = zj ? 1.0 : tm[j];
         }
         cd G0, X;
-        eval_G<S, DEF, MAXM>(s, T, tt, ttm, Lt, lam, M, ex, G0, X, fails);
+        eval_G<S, DEF, MAXM>(s, P, tt, ttm, Lt, lam, M, ex, G0, X, fails);
         double V[MAXM + 1];
         V[0] = 1.0;
 #pragma unroll
@@ -444,8 +469,8 @@ DEV int find_job(const JobTable &jt, long long item) {
 }
 
 /* ------------------------------------------------------------------ K1: persistent FP64 evaluation */
-template <int S, bool DEF, int MAXM>
-__global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ JobTable jt) {
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void eval_f64_body(const JobTable &jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
     __shared__ int s_job;
@@ -488,6 +513,7 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ J
             cur_job = jb;
         }
         const Exps ex{J.eU0, J.eU1, J.eF0, J.eF1};
+        const Pol pol = Pol::make(T, sec, psec);
         const uint32_t n = J.n;
         const double invn = J.invn;
         const double lam = J.lambda[sec.orig_index];
@@ -514,7 +540,7 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ J
 #pragma unroll
                 for (int j = 0; j < S; ++j) x[j] = fma((double)rj[j], invn, delta[j]) - (rj[j] >= Rj[j] ? 1.0 : 0.0);
                 cd val[MAXM + 1];
-                point_integrand<S, DEF, MAXM>(sec, T, x, jt.r, lam, ex, val, fails);
+                point_integrand<S, DEF, MAXM>(sec, pol, x, jt.r, lam, ex, val, fails);
 #pragma unroll
                 for (int m = 0; m <= MAXM; ++m) {
                     acc[2 * m] += val[m].x;
@@ -555,6 +581,11 @@ __global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ J
         }
         __syncthreads();
     }
+}
+
+template <int S, bool DEF, int MAXM>
+__global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ JobTable jt) {
+    eval_f64_body<S, DEF, MAXM, TabPol<S>>(jt);
 }
 
 /* ================================================================== FP32 path of the mixed-precision pass
@@ -1212,7 +1243,7 @@ DEV void probe_body(const ProbeArgs &a) {
         }
         cd v64[MAXM + 1];
         cf v32[MAXM + 1];
-        point_integrand<S, DEF, MAXM>(sec, T, x, a.r, lam, ex, v64, f64);
+        point_integrand<S, DEF, MAXM>(sec, TabPol<S>{T, &sec}, x, a.r, lam, ex, v64, f64);
         point_integrand_f<S, DEF, MAXM>(sec, pol, xf, yf, a.r, (float)lam, ex, v32, f32);
 #pragma unroll
         for (int n = 0; n <= MAXM; ++n) {
@@ -1267,7 +1298,7 @@ __global__ void __launch_bounds__(256) qmc_points_kernel(PointArgs a) {
         }
         cd val[MAXM + 1];
         uint32_t f = 0;
-        point_integrand<S, DEF, MAXM>(sec, T, x, a.r, a.lambda, ex, val, f);
+        point_integrand<S, DEF, MAXM>(sec, TabPol<S>{T, &sec}, x, a.r, a.lambda, ex, val, f);
         for (int n = 0; n < a.n_slots; ++n) {
             const cd v = n <= MAXM ? val[n < MAXM + 1 ? n : 0] : mk(0.0, 0.0);
             a.out[(j * a.n_slots + n) * 2] = v.x;

@@ -816,6 +816,10 @@ struct LaunchKey {
 };
 
 bool use_generated(const qmc_pass &p) { return p.precision == QMC_PREC_MIXED && p.evaluator != QMC_EVAL_TABLE; }
+/* FP64 jobs: generated when asked for, or by default for sectors of at most 3 variables */
+bool use_generated64(const qmc_pass &p, const PackedHeader *h) {
+    return p.evaluator == QMC_EVAL_GENERATED || (p.evaluator == QMC_EVAL_AUTO && h->dim <= 3);
+}
 
 /* Evaluation launches of a batch: every (pass, class, precision) becomes a job; jobs sharing a kernel
    instantiation and launch shape go into one persistent launch (tables of up to QMC_MAX_JOBS jobs). */
@@ -867,7 +871,10 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
                 J.eF1 = h->eF1;
                 const void *gen = nullptr;
                 if (prec == 1 && use_generated(b.pass)) {
-                    rc = qmc_gen_kernel(b.packed_host, c, &gen);
+                    rc = qmc_gen_kernel(b.packed_host, QMC_PREC_MIXED, c, &gen);
+                    if (rc) return rc;
+                } else if (prec == 0 && use_generated64(b.pass, h)) {
+                    rc = qmc_gen_kernel(b.packed_host, QMC_PREC_FP64, c, &gen);
                     if (rc) return rc;
                 }
                 const LaunchKey key{h->dim, c, class_maxm(h, c), prec == 0 ? QMC_PREC_FP64 : QMC_PREC_MIXED, pl.block,
@@ -1941,6 +1948,16 @@ int admit(Serving *S, qmc_ctx *c, Request &r) {
     return rc;
 }
 
+/* generated evaluators the request's passes may use: compiled in the background; QMC_OK once all are loaded */
+int gen_ready(const Request &r) {
+    const PackedHeader *h = header_of(r.packed.data());
+    int rc = QMC_OK;
+    if (r.opt.precision == QMC_PREC_MIXED) rc = qmc_gen_compile(r.packed.data(), QMC_PREC_MIXED, 2, nullptr);
+    if (rc == QMC_OK && (r.opt.evaluator == QMC_EVAL_GENERATED || h->dim <= 3))
+        rc = qmc_gen_compile(r.packed.data(), QMC_PREC_FP64, 2, nullptr);
+    return rc;
+}
+
 /* FP32 budget check of a mixed-precision request before the first FP32 pass (as in qmc_integrate); lambda
    must already be on the device */
 int probe(Serving *S, Request &r) {
@@ -2020,7 +2037,7 @@ void serve_loop(qmc_ctx *c) {
         {
             std::vector<std::shared_ptr<Request>> still;
             for (auto &r : S->compiling) {
-                const int rc = r->cancelled ? QMC_ERR_CANCELLED : qmc_gen_compile(r->packed.data(), 2, nullptr);
+                const int rc = r->cancelled ? QMC_ERR_CANCELLED : gen_ready(*r);
                 if (rc == QMC_PENDING) {
                     still.push_back(r);
                 } else if (rc) {
@@ -2034,9 +2051,9 @@ void serve_loop(qmc_ctx *c) {
         }
         for (auto &r : fresh) {
             if (!r) continue;
-            if (r->opt.precision == QMC_PREC_MIXED && r->opt.evaluator != QMC_EVAL_TABLE &&
+            if (r->opt.evaluator != QMC_EVAL_TABLE &&
                 std::find(S->compiling.begin(), S->compiling.end(), r) == S->compiling.end()) {
-                const int g = qmc_gen_compile(r->packed.data(), 2, nullptr);
+                const int g = gen_ready(*r);
                 if (g == QMC_PENDING) {
                     S->compiling.push_back(r);
                     continue;

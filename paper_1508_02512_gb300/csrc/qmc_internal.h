@@ -175,10 +175,11 @@ int qmc_device_sm_count(int *sms);
 int qmc_eval_blocks_per_sm(int dim, int deform, int maxm, int precision, int block, int smem_bytes, int *out);
 int qmc_launch_probe(int dim, int deform, int maxm, const ProbeArgs &a, void *stream);
 
-/* Generated evaluators (qmc_jit.cpp): the FP32 evaluation kernel of a family's module for sector class cls
+/* Generated evaluators (qmc_jit.cpp): the evaluation kernel (QMC_PREC_FP64 or _MIXED = FP32) of a family's
+   module for sector class cls
    (compiled and loaded on first use), its occupancy and launch.  Kernel handles are cudaKernel_t values passed
    as const void *. */
-int qmc_gen_kernel(const void *packed_host, int cls, const void **eval_kernel);
+int qmc_gen_kernel(const void *packed_host, int precision, int cls, const void **eval_kernel);
 uint64_t qmc_family_key(const void *packed_host); /* computed from the image, not read from its header */
 int qmc_gen_max_block(int dim);                  /* largest block of a generated kernel for sectors of this dimension */
 int qmc_gen_blocks_per_sm(const void *kernel, int block, int smem_bytes, int *out);

@@ -14,8 +14,10 @@
  * from the sector's staged term table, so a new kinematic point of the same family reuses the compiled code.
  *
  * The generated source includes the kernel templates of qmc_dev.cuh (embedded into this library at build
- * time) and instantiates, for each sector class of the family, the persistent FP32 evaluation kernel with the
- * generated evaluator (the FP32/FP64 probe keeps the table evaluator: it only samples a few thousand points).  NVRTC compiles it for sm_103a; the cubin is loaded with the
+ * time) and instantiates, for each sector class of the family, the persistent evaluation kernel with the
+ * generated evaluator: FP32 (coefficients hi + lo, two FMAs per term) or FP64 (one FMA per term; the table
+ * evaluator's repeated monomial products are what the FP64 pipe spends much of its time on).  The FP32/FP64
+ * probe keeps the table evaluators: it only samples a few thousand points.  NVRTC compiles it for sm_103a; the cubin is loaded with the
  * runtime's library API and launched through its kernel handles.  Modules are cached per family for the life
  * of the process.
  */
@@ -113,6 +115,14 @@ int top_var(Key k, int S) {
     return -1;
 }
 
+/* Spelling of the generated code in one precision */
+struct Lang {
+    bool f64;
+    const char *real, *cplx, *mk, *cmul, *term, *pre, *pol, *body;
+};
+const Lang kF32{false, "float", "cf", "mkf", "cmulf", "PackedTermF", "qg", "QgPol", "eval_f32_body"};
+const Lang kF64{true, "double", "cd", "mk", "cmul", "PackedTerm", "qd", "QdPol", "eval_f64_body"};
+
 struct PolySet {
     int S = 0;
     bool complex_ = false;
@@ -138,9 +148,17 @@ void add_term(PolySet &P, int acc, int term, const uint8_t *e) {
     }
 }
 
-void emit_fma(std::string &o, const PolySet &P, const Entry &E, const std::string &m, const std::string &ind) {
+/* one term: FP32 adds (hi + lo) x m with two FMAs (complex: packed two-lane FMAs); FP64 one FMA */
+void emit_fma(std::string &o, const Lang &L, const PolySet &P, const Entry &E, const std::string &m,
+              const std::string &ind) {
     char b[256];
-    if (!P.complex_) {
+    if (L.f64) {
+        if (!P.complex_)
+            std::snprintf(b, sizeof(b), "%sa%d = fma(C[%d].c, %s, a%d);\n", ind.c_str(), E.acc, E.term, m.c_str(), E.acc);
+        else
+            std::snprintf(b, sizeof(b), "%sa%d.x = fma(C[%d].c, %s.x, a%d.x); a%d.y = fma(C[%d].c, %s.y, a%d.y);\n",
+                          ind.c_str(), E.acc, E.term, m.c_str(), E.acc, E.acc, E.term, m.c_str(), E.acc);
+    } else if (!P.complex_) {
         std::snprintf(b, sizeof(b), "%sa%d = fmaf(C[%d].hi, %s, fmaf(C[%d].lo, %s, a%d));\n", ind.c_str(), E.acc,
                       E.term, m.c_str(), E.term, m.c_str(), E.acc);
     } else {
@@ -150,57 +168,62 @@ void emit_fma(std::string &o, const PolySet &P, const Entry &E, const std::strin
     o += b;
 }
 
-void emit_node(std::string &o, const PolySet &P, Key k, const std::string &parent, int depth, int &id) {
+void emit_node(std::string &o, const Lang &L, const PolySet &P, Key k, const std::string &parent, int depth, int &id) {
     const int j = top_var(k, P.S);
     const std::string ind(4 + 2 * depth, ' ');
     const std::string name = "m" + std::to_string(id++);
     const std::string var = (P.complex_ ? "z[" : "t[") + std::to_string(j) + "]";
+    const std::string type = P.complex_ ? L.cplx : L.real;
     o += ind + "{\n";
     if (parent.empty())
-        o += ind + "  const " + (P.complex_ ? "cf " : "float ") + name + " = " + var + ";\n";
+        o += ind + "  const " + type + " " + name + " = " + var + ";\n";
     else if (P.complex_)
-        o += ind + "  const cf " + name + " = cmulf(" + parent + ", " + var + ");\n";
+        o += ind + "  const " + type + " " + name + " = " + L.cmul + "(" + parent + ", " + var + ");\n";
     else
-        o += ind + "  const float " + name + " = " + parent + " * " + var + ";\n";
-    for (const Entry &E : P.mono.at(k)) emit_fma(o, P, E, name, ind + "  ");
+        o += ind + "  const " + type + " " + name + " = " + parent + " * " + var + ";\n";
+    for (const Entry &E : P.mono.at(k)) emit_fma(o, L, P, E, name, ind + "  ");
     for (int jj = j; jj < P.S; ++jj) {
         const Key ch = k + ((Key)1 << (4 * jj));
         if (exp_of(k, jj) >= 15) continue;
-        if (P.mono.count(ch)) emit_node(o, P, ch, name, depth + 1, id);
+        if (P.mono.count(ch)) emit_node(o, L, P, ch, name, depth + 1, id);
     }
     o += ind + "}\n";
 }
 
-void emit_body(std::string &o, const PolySet &P) {
+void emit_body(std::string &o, const Lang &L, const PolySet &P) {
     for (int a = 0; a < P.n_acc; ++a)
-        o += P.complex_ ? "    cf a" + std::to_string(a) + " = mkf(0.f, 0.f);\n"
-                        : "    float a" + std::to_string(a) + " = 0.f;\n";
+        o += P.complex_ ? std::string("    ") + L.cplx + " a" + std::to_string(a) + " = " + L.mk + "(0, 0);\n"
+                        : std::string("    ") + L.real + " a" + std::to_string(a) + " = 0;\n";
     for (const Entry &E : P.constants) {
         char b[160];
-        std::snprintf(b, sizeof(b), P.complex_ ? "    a%d.x += C[%d].hi + C[%d].lo;\n" : "    a%d += C[%d].hi + C[%d].lo;\n",
-                      E.acc, E.term, E.term);
+        if (L.f64)
+            std::snprintf(b, sizeof(b), P.complex_ ? "    a%d.x += C[%d].c;\n" : "    a%d += C[%d].c;\n", E.acc, E.term);
+        else
+            std::snprintf(b, sizeof(b), P.complex_ ? "    a%d.x += C[%d].hi + C[%d].lo;\n" : "    a%d += C[%d].hi + C[%d].lo;\n",
+                          E.acc, E.term, E.term);
         o += b;
     }
     int id = 0;
     for (int j = 0; j < P.S; ++j) {
         const Key k = (Key)1 << (4 * j);
-        if (P.mono.count(k)) emit_node(o, P, k, "", 0, id);
+        if (P.mono.count(k)) emit_node(o, L, P, k, "", 0, id);
     }
 }
 
-/* source of one family: per-sector functions, the evaluator and the kernels of every class present */
-std::string generate(const PackedHeader *h) {
+/* source of one family in one precision: per-sector functions, the evaluator and the kernels of every class */
+std::string generate(const PackedHeader *h, const Lang &L) {
     const int S = h->dim;
     const int NP = S * (S + 1) / 2;
     const PackedSector *ps = sectors(h);
-    const PackedTermF *tf = terms_f(h);
+    const PackedTermF *tf = terms_f(h); /* exponents (the FP64 terms carry the same ones, in the same order) */
+    const std::string R = L.real, Cx = L.cplx, TT = L.term, pre = L.pre;
     std::string o;
     o.reserve(1 << 20);
     char b[512];
     std::snprintf(b, sizeof(b),
-                  "/* generated: polynomial evaluators of one family of %d-dimensional sector tables (%d sectors) */\n"
+                  "/* generated: %s polynomial evaluators of one family of %d-dimensional sector tables (%d sectors) */\n"
                   "#include \"qmc_dev.cuh\"\n\n",
-                  S, h->n_sectors);
+                  L.f64 ? "FP64" : "FP32", S, h->n_sectors);
     o += b;
     std::vector<int> cls(h->n_sectors, -1);
     for (int c = 0; c < QMC_N_CLASSES; ++c)
@@ -212,36 +235,31 @@ std::string generate(const PackedHeader *h) {
     std::string targs, tvals, zargs, zvals, tcall, zcall;
     for (int j = 0; j < S; ++j) {
         const std::string J = std::to_string(j);
-        targs += ", float t" + J;
+        targs += ", " + R + " t" + J;
         tvals += (j ? ", t" : "t") + J;
-        zargs += ", float z" + J + "r, float z" + J + "i";
-        zvals += (j ? ", mkf(z" : "mkf(z") + J + "r, z" + J + "i)";
+        zargs += ", " + R + " z" + J + "r, " + R + " z" + J + "i";
+        zvals += std::string(j ? ", " : "") + L.mk + "(z" + J + "r, z" + J + "i)";
         tcall += ", t[" + J + "]";
         zcall += ", z[" + J + "].x, z[" + J + "].y";
     }
+    const std::string SR = pre == "qg" ? "QgR" : "QdR", SC = pre == "qg" ? "QgC" : "QdC", SGH = pre == "qg" ? "QgGH" : "QdGH";
     if (out_of_line) {
-        std::snprintf(b, sizeof(b),
-                      "struct QgR { float U, F; };\nstruct QgC { cf U, F; };\nstruct QgGH { float g[%d], h[%d]; };\n\n",
-                      S, NP);
-        o += b;
+        o += "struct " + SR + " { " + R + " U, F; };\nstruct " + SC + " { " + Cx + " U, F; };\nstruct " + SGH + " { " + R +
+             " g[" + std::to_string(S) + "], h[" + std::to_string(NP) + "]; };\n\n";
     }
     auto head = [&](const char *kind, int s) {
         const std::string n = std::to_string(s);
+        const std::string C = "(const " + TT + " *__restrict__ C";
         if (!out_of_line) {
-            if (!std::strcmp(kind, "ufr"))
-                return "DEV void qg_ufr_" + n + "(const PackedTermF *__restrict__ C, const float *t, float &U, float &F) {\n";
-            if (!std::strcmp(kind, "gh"))
-                return "DEV void qg_gh_" + n + "(const PackedTermF *__restrict__ C, const float *t, float *g, float *h) {\n";
-            return "DEV void qg_ufc_" + n + "(const PackedTermF *__restrict__ C, const cf *z, cf &U, cf &F) {\n";
+            if (!std::strcmp(kind, "ufr")) return "DEV void " + pre + "_ufr_" + n + C + ", const " + R + " *t, " + R + " &U, " + R + " &F) {\n";
+            if (!std::strcmp(kind, "gh")) return "DEV void " + pre + "_gh_" + n + C + ", const " + R + " *t, " + R + " *g, " + R + " *h) {\n";
+            return "DEV void " + pre + "_ufc_" + n + C + ", const " + Cx + " *z, " + Cx + " &U, " + Cx + " &F) {\n";
         }
         if (!std::strcmp(kind, "ufr"))
-            return "__device__ __noinline__ QgR qg_ufr_" + n + "(const PackedTermF *__restrict__ C" + targs +
-                   ") {\n    const float t[] = {" + tvals + "};\n";
+            return "__device__ __noinline__ " + SR + " " + pre + "_ufr_" + n + C + targs + ") {\n    const " + R + " t[] = {" + tvals + "};\n";
         if (!std::strcmp(kind, "gh"))
-            return "__device__ __noinline__ QgGH qg_gh_" + n + "(const PackedTermF *__restrict__ C" + targs +
-                   ") {\n    const float t[] = {" + tvals + "};\n";
-        return "__device__ __noinline__ QgC qg_ufc_" + n + "(const PackedTermF *__restrict__ C" + zargs +
-               ") {\n    const cf z[] = {" + zvals + "};\n";
+            return "__device__ __noinline__ " + SGH + " " + pre + "_gh_" + n + C + targs + ") {\n    const " + R + " t[] = {" + tvals + "};\n";
+        return "__device__ __noinline__ " + SC + " " + pre + "_ufc_" + n + C + zargs + ") {\n    const " + Cx + " z[] = {" + zvals + "};\n";
     };
     for (int s = 0; s < h->n_sectors; ++s) {
         const PackedSector &p = ps[s];
@@ -253,8 +271,8 @@ std::string generate(const PackedHeader *h) {
             for (int k = 0; k < p.nU; ++k) add_term(P, 0, k, T[k].e);
             for (int k = 0; k < p.nF; ++k) add_term(P, 1, p.nU + k, T[p.nU + k].e);
             o += head("ufr", s);
-            emit_body(o, P);
-            o += out_of_line ? "    return QgR{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+            emit_body(o, L, P);
+            o += out_of_line ? "    return " + SR + "{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
         } else if (cls[s] == 1) {
             PolySet P;
             P.S = S;
@@ -265,10 +283,10 @@ std::string generate(const PackedHeader *h) {
             for (int q = 0; q < NP; ++q)
                 for (int k = bH + p.hstart[q]; k < bH + p.hstart[q + 1]; ++k) add_term(P, S + q, k, T[k].e);
             o += head("gh", s);
-            emit_body(o, P);
+            emit_body(o, L, P);
             const char *gv = out_of_line ? "    r.g[" : "    g[";
             const char *hv = out_of_line ? "    r.h[" : "    h[";
-            if (out_of_line) o += "    QgGH r;\n";
+            if (out_of_line) o += "    " + SGH + " r;\n";
             for (int j = 0; j < S; ++j) o += gv + std::to_string(j) + "] = a" + std::to_string(j) + ";\n";
             for (int q = 0; q < NP; ++q) o += hv + std::to_string(q) + "] = a" + std::to_string(S + q) + ";\n";
             o += out_of_line ? "    return r;\n}\n" : "}\n";
@@ -279,54 +297,55 @@ std::string generate(const PackedHeader *h) {
             for (int k = 0; k < p.nU; ++k) add_term(Q, 0, k, T[k].e);
             for (int k = 0; k < p.nF; ++k) add_term(Q, 1, p.nU + k, T[p.nU + k].e);
             o += head("ufc", s);
-            emit_body(o, Q);
-            o += out_of_line ? "    return QgC{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+            emit_body(o, L, Q);
+            o += out_of_line ? "    return " + SC + "{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
         }
     }
     /* the evaluator: a warp-uniform switch over the packed sector index */
-    o += "\nstruct QgPol {\n    const PackedTermF *T;\n    int sec;\n"
-         "    DEV static QgPol make(const PackedTermF *T, const PackedSector &, int psec) { return QgPol{T, psec}; }\n";
-    o += "    DEV void UFr(const float *t, float &U, float &F) const {\n        switch (sec) {\n";
+    const std::string Pol = L.pol;
+    o += "\nstruct " + Pol + " {\n    const " + TT + " *T;\n    int sec;\n    DEV static " + Pol + " make(const " + TT +
+         " *T, const PackedSector &, int psec) { return " + Pol + "{T, psec}; }\n";
+    o += "    DEV void UFr(const " + R + " *t, " + R + " &U, " + R + " &F) const {\n        switch (sec) {\n";
     for (int s = 0; s < h->n_sectors; ++s)
         if (cls[s] == 0) {
             const std::string n = std::to_string(s);
-            o += out_of_line ? "        case " + n + ": { const QgR r = qg_ufr_" + n + "(T" + tcall + "); U = r.U; F = r.F; return; }\n"
-                             : "        case " + n + ": qg_ufr_" + n + "(T, t, U, F); return;\n";
+            o += out_of_line ? "        case " + n + ": { const " + SR + " r = " + pre + "_ufr_" + n + "(T" + tcall + "); U = r.U; F = r.F; return; }\n"
+                             : "        case " + n + ": " + pre + "_ufr_" + n + "(T, t, U, F); return;\n";
         }
-    o += "        default: U = 0.f; F = 0.f;\n        }\n    }\n";
-    o += "    DEV void GH(const float *t, float *g, float *h) const {\n        switch (sec) {\n";
+    o += "        default: U = 0; F = 0;\n        }\n    }\n";
+    o += "    DEV void GH(const " + R + " *t, " + R + " *g, " + R + " *h) const {\n        switch (sec) {\n";
     for (int s = 0; s < h->n_sectors; ++s)
         if (cls[s] == 1) {
             const std::string n = std::to_string(s);
-            o += out_of_line ? "        case " + n + ": { const QgGH r = qg_gh_" + n + "(T" + tcall +
+            o += out_of_line ? "        case " + n + ": { const " + SGH + " r = " + pre + "_gh_" + n + "(T" + tcall +
                                    "); for (int j = 0; j < " + std::to_string(S) + "; ++j) g[j] = r.g[j]; for (int q = 0; q < " +
                                    std::to_string(NP) + "; ++q) h[q] = r.h[q]; return; }\n"
-                             : "        case " + n + ": qg_gh_" + n + "(T, t, g, h); return;\n";
+                             : "        case " + n + ": " + pre + "_gh_" + n + "(T, t, g, h); return;\n";
         }
     std::snprintf(b, sizeof(b),
-                  "        default:\n            for (int j = 0; j < %d; ++j) g[j] = 0.f;\n"
-                  "            for (int q = 0; q < %d; ++q) h[q] = 0.f;\n        }\n    }\n",
+                  "        default:\n            for (int j = 0; j < %d; ++j) g[j] = 0;\n"
+                  "            for (int q = 0; q < %d; ++q) h[q] = 0;\n        }\n    }\n",
                   S, NP);
     o += b;
-    o += "    DEV void UFc(const cf *z, bool, cf &U, cf &F) const {\n        switch (sec) {\n";
+    o += "    DEV void UFc(const " + Cx + " *z, bool, " + Cx + " &U, " + Cx + " &F) const {\n        switch (sec) {\n";
     for (int s = 0; s < h->n_sectors; ++s)
         if (cls[s] == 1) {
             const std::string n = std::to_string(s);
-            o += out_of_line ? "        case " + n + ": { const QgC r = qg_ufc_" + n + "(T" + zcall + "); U = r.U; F = r.F; return; }\n"
-                             : "        case " + n + ": qg_ufc_" + n + "(T, z, U, F); return;\n";
+            o += out_of_line ? "        case " + n + ": { const " + SC + " r = " + pre + "_ufc_" + n + "(T" + zcall + "); U = r.U; F = r.F; return; }\n"
+                             : "        case " + n + ": " + pre + "_ufc_" + n + "(T, z, U, F); return;\n";
         }
-    o += "        default: U = mkf(0.f, 0.f); F = mkf(0.f, 0.f);\n        }\n    }\n};\n\n";
+    o += std::string("        default: U = ") + L.mk + "(0, 0); F = " + L.mk + "(0, 0);\n        }\n    }\n};\n\n";
     for (int c = 0; c < QMC_N_CLASSES; ++c) {
         if (h->class_end[c] <= h->class_begin[c]) continue;
         const char *def = c == 1 ? "true" : "false";
         const int mm = maxm_of(h, c);
-        /* 5- and 6-dimensional deformed sectors: 3 blocks of 128 threads per SM (<= 170 registers, no spills)
-           measured 13 % faster than the register-unbounded build (2 blocks); smaller sectors keep 256 */
-        const std::string lb = qmc_gen_max_block(S) == 128 ? "__launch_bounds__(128, 3)" : "__launch_bounds__(256)";
+        /* FP32, 5- and 6-dimensional deformed sectors: 3 blocks of 128 threads per SM (<= 170 registers, no
+           spills) measured 13 % faster than the register-unbounded build (2 blocks); the rest keep 256 */
+        const std::string lb = (!L.f64 && qmc_gen_max_block(S) == 128) ? "__launch_bounds__(128, 3)" : "__launch_bounds__(256)";
         std::snprintf(b, sizeof(b),
-                      "extern \"C\" __global__ void %s qg_eval_c%d(const __grid_constant__ JobTable jt) {\n"
-                      "    eval_f32_body<%d, %s, %d, QgPol>(jt);\n}\n",
-                      lb.c_str(), c, S, def, mm);
+                      "extern \"C\" __global__ void %s %s_eval_c%d(const __grid_constant__ JobTable jt) {\n"
+                      "    %s<%d, %s, %d, %s>(jt);\n}\n",
+                      lb.c_str(), pre.c_str(), c, L.body, S, def, mm, L.pol);
         o += b;
     }
     return o;
@@ -409,17 +428,24 @@ Cache &cache() {
     return *c;
 }
 
+const Lang &lang_of(int precision) { return precision == QMC_PREC_FP64 ? kF64 : kF32; }
+
+/* cache key: the family and the precision of the generated evaluator */
+uint64_t module_key(const PackedHeader *h, int precision) {
+    return family_key(h) ^ (precision == QMC_PREC_FP64 ? 0x9E3779B97F4A7C15ull : 0ull);
+}
+
 /* compile and load (no lock held) */
-int build_module(const PackedHeader *h, std::unique_ptr<Module> &out) {
+int build_module(const PackedHeader *h, int precision, std::unique_ptr<Module> &out) {
     Compiled cc;
-    int rc = compile(generate(h), cc);
+    int rc = compile(generate(h, lang_of(precision)), cc);
     if (rc) return rc;
     std::unique_ptr<Module> m(new Module());
     if (cudaLibraryLoadData(&m->lib, cc.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
         return QMC_ERR_CUDA;
     for (int c = 0; c < QMC_N_CLASSES; ++c) {
         if (h->class_end[c] <= h->class_begin[c]) continue;
-        const std::string e = "qg_eval_c" + std::to_string(c);
+        const std::string e = std::string(lang_of(precision).pre) + "_eval_c" + std::to_string(c);
         if (cudaLibraryGetKernel(&m->eval[c], m->lib, e.c_str()) != cudaSuccess) {
             cudaLibraryUnload(m->lib);
             return QMC_ERR_CUDA;
@@ -445,8 +471,9 @@ void finish_slot(uint64_t key, int rc, std::unique_ptr<Module> m) {
 }
 
 /* mode 0: compile here and wait; mode 1: start a background compilation and return QMC_PENDING until ready */
-int get_module(const PackedHeader *h, const Module **out, bool *was_cached, int mode = 0, int device = 0) {
-    const uint64_t key = family_key(h);
+int get_module(const PackedHeader *h, int precision, const Module **out, bool *was_cached, int mode = 0,
+               int device = 0) {
+    const uint64_t key = module_key(h, precision);
     Cache &C = cache();
     std::unique_lock<std::mutex> lk(C.mu);
     Slot &s = C.slots[key];
@@ -465,12 +492,12 @@ int get_module(const PackedHeader *h, const Module **out, bool *was_cached, int 
     if (mode == 1) {
         std::vector<unsigned char> img(reinterpret_cast<const unsigned char *>(h),
                                        reinterpret_cast<const unsigned char *>(h) + h->total_bytes);
-        std::thread([key, device](std::vector<unsigned char> im) {
+        std::thread([key, device, precision](std::vector<unsigned char> im) {
             cudaSetDevice(device);
             std::unique_ptr<Module> m;
             int rc;
             try {
-                rc = build_module(reinterpret_cast<const PackedHeader *>(im.data()), m);
+                rc = build_module(reinterpret_cast<const PackedHeader *>(im.data()), precision, m);
             } catch (const std::bad_alloc &) {
                 rc = QMC_ERR_MEMORY;
             }
@@ -481,7 +508,7 @@ int get_module(const PackedHeader *h, const Module **out, bool *was_cached, int 
     std::unique_ptr<Module> m;
     int rc;
     try {
-        rc = build_module(h, m);
+        rc = build_module(h, precision, m);
     } catch (const std::bad_alloc &) {
         rc = QMC_ERR_MEMORY;
     }
@@ -502,11 +529,11 @@ uint64_t qmc_family_key(const void *packed_host) {
     return h ? family_key(h) : 0;
 }
 
-int qmc_gen_kernel(const void *packed_host, int cls, const void **eval_kernel) {
+int qmc_gen_kernel(const void *packed_host, int precision, int cls, const void **eval_kernel) {
     const PackedHeader *h = hdr(packed_host);
     if (!h || !eval_kernel || cls < 0 || cls >= QMC_N_CLASSES) return QMC_ERR_ARG;
     const Module *m = nullptr;
-    const int rc = get_module(h, &m, nullptr);
+    const int rc = get_module(h, precision, &m, nullptr);
     if (rc) return rc;
     if (!m->eval[cls]) return QMC_ERR_ARG;
     *eval_kernel = reinterpret_cast<const void *>(m->eval[cls]);
@@ -533,11 +560,11 @@ int qmc_gen_launch_eval(const void *kernel, const JobTable &t, int grid, int blo
 /* ---------------------------------------------------------------- public entry points */
 extern "C" {
 
-int qmc_gen_source(const void *packed_host, char *buf, size_t cap, size_t *len) {
+int qmc_gen_source(const void *packed_host, int32_t precision, char *buf, size_t cap, size_t *len) {
     const PackedHeader *h = hdr(packed_host);
-    if (!h) return QMC_ERR_ARG;
+    if (!h || (precision != QMC_PREC_FP64 && precision != QMC_PREC_MIXED)) return QMC_ERR_ARG;
     try {
-        const std::string s = generate(h);
+        const std::string s = generate(h, lang_of(precision));
         if (len) *len = s.size() + 1;
         if (buf) {
             if (cap < s.size() + 1) return QMC_ERR_MEMORY;
@@ -549,14 +576,14 @@ int qmc_gen_source(const void *packed_host, char *buf, size_t cap, size_t *len) 
     }
 }
 
-int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info) {
+int qmc_gen_compile(const void *packed_host, int32_t precision, int32_t load, qmc_gen_info *info) {
     const PackedHeader *h = hdr(packed_host);
-    if (!h) return QMC_ERR_ARG;
+    if (!h || (precision != QMC_PREC_FP64 && precision != QMC_PREC_MIXED)) return QMC_ERR_ARG;
     try {
         if (info) std::memset(info, 0, sizeof(*info));
         if (info) info->family = family_key(h);
         if (!load) {
-            const std::string src = generate(h);
+            const std::string src = generate(h, lang_of(precision));
             Compiled cc;
             const int rc = compile(src, cc);
             if (info) {
@@ -570,7 +597,7 @@ int qmc_gen_compile(const void *packed_host, int32_t load, qmc_gen_info *info) {
         bool cached = false;
         int device = 0;
         if (load == 2 && cudaGetDevice(&device) != cudaSuccess) return QMC_ERR_NO_DEVICE;
-        const int rc = get_module(h, &m, &cached, load == 2 ? 1 : 0, device);
+        const int rc = get_module(h, precision, &m, &cached, load == 2 ? 1 : 0, device);
         if (rc) return rc;
         if (info) {
             info->compile_ms = m->compile_ms;

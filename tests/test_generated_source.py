@@ -230,6 +230,108 @@ def test_generated_functions_evaluate_the_table_polynomials(cfg):
     assert worst < 2e-6
 
 
+SHIM64 = r"""
+#include <math.h>
+#define DEV static inline
+#define __device__
+#define __noinline__ static
+#define __restrict__
+struct cd { double x, y; };
+static inline cd mk(double x, double y) { return cd{x, y}; }
+static inline cd cmul(cd a, cd b) { return cd{fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x)}; }
+struct PackedTerm { double c; unsigned char e[8]; };
+"""
+
+
+def host_harness64(src, h):
+    i0 = src.index('#include "qmc_dev.cuh"') + len('#include "qmc_dev.cuh"')
+    body = src[i0:src.index("struct QdPol")]
+    S = h.dim
+    NP = S * (S + 1) // 2
+    ool = "struct QdGH" in body
+    out = [SHIM64, body]
+    ufr, gh, ufc = [], [], []
+    ta = ", ".join(f"t[{j}]" for j in range(S))
+    za = ", ".join(f"z[{j}].x, z[{j}].y" for j in range(S))
+    for k in range(h.n_sectors):
+        if h.class_begin[0] <= k < h.class_end[0]:
+            ufr.append(f"case {k}: {{ QdR r = qd_ufr_{k}(C, {ta}); U[0] = r.U; U[1] = r.F; return; }}" if ool else
+                       f"case {k}: qd_ufr_{k}(C, t, U[0], U[1]); return;")
+        else:
+            gh.append(f"case {k}: {{ QdGH r = qd_gh_{k}(C, {ta}); for (int j = 0; j < {S}; ++j) g[j] = r.g[j]; "
+                      f"for (int q = 0; q < {NP}; ++q) hh[q] = r.h[q]; return; }}" if ool else
+                      f"case {k}: qd_gh_{k}(C, t, g, hh); return;")
+            ufc.append(f"case {k}: {{ QdC r = qd_ufc_{k}(C, {za}); UF[0] = r.U; UF[1] = r.F; return; }}" if ool else
+                       f"case {k}: qd_ufc_{k}(C, z, UF[0], UF[1]); return;")
+    out.append('extern "C" void h_ufr(int s, const PackedTerm *C, const double *t, double *U) { switch (s) { '
+               + " ".join(ufr) + " } }")
+    out.append('extern "C" void h_gh(int s, const PackedTerm *C, const double *t, double *g, double *hh) { switch (s) { '
+               + " ".join(gh) + " } }")
+    out.append('extern "C" void h_ufc(int s, const PackedTerm *C, const cd *z, cd *UF) { switch (s) { '
+               + " ".join(ufc) + " } }")
+    return "\n".join(out)
+
+
+TERM_D = np.dtype([("c", "<f8"), ("e", "u1", (8,))])
+
+
+@pytest.mark.parametrize("cfg", [W.CONFIG1, W.CONFIG2], ids=lambda c: c.name)
+def test_generated_fp64_functions_evaluate_the_table_polynomials(cfg):
+    prep = prepared(cfg)
+    h, secs, _ = image(prep)
+    terms = np.frombuffer(bytes(prep.packed), dtype=TERM_D, count=h.n_terms_total, offset=h.terms_off)
+    src = api.gen_source(prep, N.QMC_PREC_FP64)
+    os.makedirs(WORK, exist_ok=True)
+    cpp = os.path.join(WORK, f"gen64_{cfg.name}.cpp")
+    so = os.path.join(WORK, f"gen64_{cfg.name}.so")
+    open(cpp, "w").write(host_harness64(src, h))
+    subprocess.check_call(["g++", "-O1", "-ffp-contract=off", "-shared", "-fPIC", "-o", so, cpp])
+    L = ctypes.CDLL(so)
+    S = h.dim
+    NP = S * (S + 1) // 2
+    rng = np.random.Generator(np.random.PCG64(12))
+    dptr = ctypes.POINTER(ctypes.c_double)
+    worst = 0.0
+
+    def ref(T_s, lo, hi, x):
+        v, mag = 0.0, 0.0
+        for tt in T_s[lo:hi]:
+            m = 1.0 + 0.0j if np.iscomplexobj(x) else 1.0
+            for j in range(len(x)):
+                m = m * x[j] ** int(tt["e"][j])
+            v += tt["c"] * m
+            mag += abs(tt["c"] * m)
+        return v, mag
+
+    for k, s in enumerate(secs):
+        T_s = np.ascontiguousarray(terms[s.term0: s.term0 + s.n_terms])
+        Cp = T_s.ctypes.data_as(ctypes.c_void_p)
+        U, F, G, H = blocks(h, s)
+        t = rng.uniform(0.0, 1.0, S)
+        tp = t.ctypes.data_as(dptr)
+        if h.class_begin[0] <= k < h.class_end[0]:
+            outv = np.zeros(2)
+            L.h_ufr(k, Cp, tp, outv.ctypes.data_as(dptr))
+            refs, got = [ref(T_s, *U, t), ref(T_s, *F, t)], list(outv)
+        else:
+            g = np.zeros(S)
+            hh = np.zeros(NP)
+            L.h_gh(k, Cp, tp, g.ctypes.data_as(dptr), hh.ctypes.data_as(dptr))
+            refs = [ref(T_s, lo, hi, t) for lo, hi in G + H]
+            got = list(g) + list(hh)
+            zc = t * (1 - 0.3j * rng.uniform(0, 1, S))
+            zf = np.ascontiguousarray(np.stack([zc.real, zc.imag], -1))
+            uf = np.zeros(4)
+            L.h_ufc(k, Cp, zf.ctypes.data_as(dptr), uf.ctypes.data_as(dptr))
+            refs += [ref(T_s, *U, zc), ref(T_s, *F, zc)]
+            got += [complex(uf[0], uf[1]), complex(uf[2], uf[3])]
+        for (rv, mag), gv in zip(refs, got):
+            worst = max(worst, abs(complex(gv) - rv) / max(mag, 1e-300))
+    print(f"{cfg.name}: worst |generated FP64 - table| / sum|terms| = {worst:.2e}")
+    assert worst < 1e-14
+
+
 def test_nvrtc_compiles_generated_source_without_a_device():
-    info = api.gen_compile(prepared(W.CONFIG1), load=False)
-    assert info.cubin_bytes > 0 and info.source_bytes > 0 and info.compile_ms > 0
+    for precision in (N.QMC_PREC_MIXED, N.QMC_PREC_FP64):
+        info = api.gen_compile(prepared(W.CONFIG1), load=False, precision=precision)
+        assert info.cubin_bytes > 0 and info.source_bytes > 0 and info.compile_ms > 0

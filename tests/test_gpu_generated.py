@@ -93,3 +93,23 @@ def test_generated_module_is_cached_per_family():
     blob = T.compile_integral(W.CONFIG1.topology, T.zero_invariants_of(W.CONFIG1.topology, W.CONFIG1.point))
     b = api.gen_compile(api.prepare(blob, kin2, 0, 0))
     assert b.cached == 1 and b.family == a.family
+
+
+@pytest.mark.parametrize("cfg", [W.CONFIG0, W.CONFIG1, W.CONFIG2], ids=lambda c: c.name)
+def test_generated_fp64_sums_match_oracle_to_1e12(cfg):
+    prep, dev = setup(cfg)
+    info = api.gen_compile(prep, precision=N.QMC_PREC_FP64)
+    print(f"{cfg.name}: FP64 generated evaluator compiled in {info.compile_ms:.0f} ms")
+    n = 1021 if cfg.topology.loops == 2 else 4093
+    z = OL.cbc_plain(n, 6)
+    shifts = W.shifts(29, 2 if cfg.topology.loops == 2 else 4)
+    lams = [cfg.lam if cfg.lam > 0 else 0.0] * prep.info.n_sectors
+    gen, gf = run(dev, api.make_pass(n, z, len(shifts), 3, evaluator=N.QMC_EVAL_GENERATED), shifts, lams)
+    tab, tf = run(dev, api.make_pass(n, z, len(shifts), 3, evaluator=N.QMC_EVAL_TABLE), shifts, lams)
+    assert np.array_equal(gf, tf)
+    worst = 0.0
+    for s, (o, l1c) in enumerate(oracle_sums(cfg, n, z, shifts, lams)):
+        k = o.shape[1]
+        worst = max(worst, float((np.abs(gen[s, :, :k] - o) / np.maximum(l1c, 1e-300)).max()))
+    print(f"{cfg.name}: FP64 generated |gpu-oracle| / term magnitudes = {worst:.2e}")
+    assert worst <= 1e-12
