@@ -191,6 +191,13 @@ CONFIG3 = Workload("nonplanar_dbox_physical", double_box_nonplanar(True), dict(s
                    16, tuple(range(16, 27)), 3, 0.5)
 CONFIGS = (CONFIG0, CONFIG1, CONFIG2, CONFIG3)
 
+# The kinematic point of the paper's two-loop examples in the physical region (Sec. IV, gg -> HH): p1^2 = p2^2
+# = 0, p3^2 = p4^2 = M_H^2, s = 160000 GeV^2, t = -6000 GeV^2, in units of M_t = 172 GeV (M_t^2 = 1 on the four
+# massive lines); M_H = 125 GeV.
+M_T_GEV, M_H_GEV = 172.0, 125.0
+PAPER_HH_POINT = dict(s=160000.0 / M_T_GEV ** 2, t=-6000.0 / M_T_GEV ** 2, pp3=(M_H_GEV / M_T_GEV) ** 2,
+                      pp4=(M_H_GEV / M_T_GEV) ** 2, msq=1.0)
+
 
 def shifts(seed: int, m: int, dim: int = 6) -> np.ndarray:
     """m random shift vectors, uniform in [0,1)^dim, from numpy's PCG64 seeded by `seed` (paper Sec. III,
