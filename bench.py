@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-accuracy and CPU baseline")
     ap.add_argument("--integral", choices=sorted(INTEGRALS), default="massive_box",
                     help="integral of the timed pass (default: the massive one-loop box)")
+    ap.add_argument("--evaluator", choices=["auto", "table", "generated"], default="auto",
+                    help="polynomial evaluator of the FP64 pass (the mixed pass always uses the generated one)")
     ap.add_argument("--log2n", type=int, default=0, help="lattice size: largest prime below 2^log2n (default "
                                                          "24 one-loop, 18 two-loop)")
     ap.add_argument("--profile-pass", action="store_true",
@@ -241,7 +243,10 @@ def main_ours(args):
     n = max(k for k in lat if k < (1 << log2n))
     z = lat[n]
     shifts = W.shifts(cfg.seed + rank, N_SHIFTS)
-    p = api.make_pass(n, z, N_SHIFTS, 3)
+    evaluator = {"auto": N.QMC_EVAL_AUTO, "table": N.QMC_EVAL_TABLE, "generated": N.QMC_EVAL_GENERATED}[args.evaluator]
+    if evaluator != N.QMC_EVAL_TABLE:
+        api.gen_compile(prep, precision=N.QMC_PREC_FP64)  # generated FP64 evaluator compiled before any timing
+    p = api.make_pass(n, z, N_SHIFTS, 3, evaluator=evaluator)
     ns = prep.info.n_sectors
     stream = torch.cuda.Stream(device=dev_name)
     sh = torch.tensor(shifts, device=dev_name)
@@ -422,7 +427,8 @@ def main_ours(args):
             "gpu_launches": 2 * args.steps,  # per step: qmc_eval_kernel + qmc_finalize_kernel
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "kernel": f"qmc_eval_kernel<{prep.info.dim},deform,{maxm_of(prep)}>",
+                         "kernel": ("qd_eval_c1 (generated FP64 evaluator)" if evaluator != N.QMC_EVAL_TABLE
+                                    else f"qmc_eval_kernel<{prep.info.dim},deform,{maxm_of(prep)}>"),
                          "flops_per_eval": prep.info.flops_per_eval, "sign_failures": sign_failures,
                          "eval_kernel_ms": statistics.mean(eval_ms), "pass_ms": statistics.mean(pass_ms),
                          "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz (recipe FP64 1.25 TFLOP/s)",

@@ -52,8 +52,7 @@ extern "C" {
 enum { QMC_PREC_FP64 = 0, QMC_PREC_MIXED = 1 };
 
 /* Polynomial evaluator of a pass:
- *   QMC_EVAL_AUTO (0)      generated for FP32 evaluation; for FP64 evaluation generated when the sectors have
- *                          at most 3 variables, the table otherwise (measured faster there on GB300)
+ *   QMC_EVAL_AUTO (0)      = QMC_EVAL_GENERATED
  *   QMC_EVAL_TABLE         the kernels walk each sector's staged term table and decode its exponents per point
  *   QMC_EVAL_GENERATED     straight-line code generated for the family of sector tables (same exponents) and
  *                          compiled at run time with NVRTC on first use (qmc_gen_compile), in each precision

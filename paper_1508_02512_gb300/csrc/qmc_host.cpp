@@ -816,10 +816,8 @@ struct LaunchKey {
 };
 
 bool use_generated(const qmc_pass &p) { return p.precision == QMC_PREC_MIXED && p.evaluator != QMC_EVAL_TABLE; }
-/* FP64 jobs: generated when asked for, or by default for sectors of at most 3 variables */
-bool use_generated64(const qmc_pass &p, const PackedHeader *h) {
-    return p.evaluator == QMC_EVAL_GENERATED || (p.evaluator == QMC_EVAL_AUTO && h->dim <= 3);
-}
+/* FP64 jobs: generated unless the pass asks for the table */
+bool use_generated64(const qmc_pass &p, const PackedHeader *) { return p.evaluator != QMC_EVAL_TABLE; }
 
 /* Evaluation launches of a batch: every (pass, class, precision) becomes a job; jobs sharing a kernel
    instantiation and launch shape go into one persistent launch (tables of up to QMC_MAX_JOBS jobs). */
@@ -1950,11 +1948,9 @@ int admit(Serving *S, qmc_ctx *c, Request &r) {
 
 /* generated evaluators the request's passes may use: compiled in the background; QMC_OK once all are loaded */
 int gen_ready(const Request &r) {
-    const PackedHeader *h = header_of(r.packed.data());
     int rc = QMC_OK;
     if (r.opt.precision == QMC_PREC_MIXED) rc = qmc_gen_compile(r.packed.data(), QMC_PREC_MIXED, 2, nullptr);
-    if (rc == QMC_OK && (r.opt.evaluator == QMC_EVAL_GENERATED || h->dim <= 3))
-        rc = qmc_gen_compile(r.packed.data(), QMC_PREC_FP64, 2, nullptr);
+    if (rc == QMC_OK) rc = qmc_gen_compile(r.packed.data(), QMC_PREC_FP64, 2, nullptr);
     return rc;
 }
 
