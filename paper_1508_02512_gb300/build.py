@@ -21,7 +21,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmcfi.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_host.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"] + [f"qmc_kern_d{d}.cu" for d in range(1, 7)]
+SOURCES = (["qmc_kernels.cu", "qmc_prepare.cpp", "qmc_pass.cpp", "qmc_context.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"] +
+           [f"qmc_kern_d{d}.cu" for d in range(1, 7)])
 # device headers compiled again at run time with the generated evaluators: (C identifier, file)
 EMBEDDED = [("qmc_src_qmcfi_h", os.path.join(ROOT, "include", "qmcfi.h")),
             ("qmc_src_qmc_internal_h", os.path.join(CSRC, "qmc_internal.h")),
@@ -40,7 +41,7 @@ def _cuda_lib_dir(nv: str) -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in SOURCES + ["qmc_internal.h", "qmc_device.cuh", "qmc_dev.cuh", "lattice_table.h"]]
+    files = [os.path.join(CSRC, f) for f in SOURCES + ["qmc_internal.h", "qmc_host_internal.h", "qmc_device.cuh", "qmc_dev.cuh", "lattice_table.h"]]
     files.append(os.path.join(ROOT, "include", "qmcfi.h"))
     return files
 

@@ -1,5 +1,5 @@
 /*
- * Packed device image of a prepared integral, shared by the host runtime (qmc_host.cpp) and the kernels
+ * Packed device image of a prepared integral, shared by the host runtime (qmc_prepare.cpp, qmc_pass.cpp, qmc_context.cpp) and the kernels
  * (qmc_kernels.cu).  One contiguous, relocatable buffer (offsets only):
  *
  *   PackedHeader                      kinematics-independent data, prefactor series, launch classes

@@ -16,7 +16,7 @@ Polynomials are numpy arrays: exponents int32[T, n] and coefficients float64[T, 
 and column 1 + k the coefficient of kinematic invariant k, so one table serves every kinematic point of its
 zero pattern.  All coefficients that arise are dyadic rationals and exact in float64.
 
-Binary table (little-endian, 8-byte aligned), read by csrc/qmc_host.cpp:
+Binary table (little-endian, 8-byte aligned), read by csrc/qmc_prepare.cpp:
   header   "QMCSEC01", int32 version, n_sectors, dim, loops, n_props, n_nu, n_inv, eU0, eU1, eF0, eF1,
            header_bytes, 2 x int32 reserved; int32 nu[n_props] (padded to 8 bytes); char names[n_inv][16]
   sector   int32 nU, nF; int32 A[dim], B[dim] (padded to 8 bytes); double D;
