@@ -216,14 +216,19 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
  *   load = 2: the same in a background thread (current device): returns QMC_PENDING while it runs, QMC_OK once
  *   the module is loaded (the serving loop uses this so that other requests keep running meanwhile).
  *   info (may be NULL) receives the family key, compilation time (of the cached compilation when cached = 1),
- *   source and cubin sizes.  A failed compilation is remembered: later calls return its status.
+ *   source and cubin sizes; cached = 1: the module was already loaded in this process, 2: its cubin came from
+ *   the disk cache.  A failed compilation is remembered: later calls return its status.
+ *   Disk cache (optional): with the environment variable QMC_GEN_CACHE_DIR naming a writable directory, cubins
+ *   are stored there and reused by later processes (file name: family, precision, generator version, embedded
+ *   device sources and NVRTC version; written atomically).
  *   Errors: QMC_ERR_ARG, QMC_ERR_CODEGEN (NVRTC failed; its log goes to stderr), QMC_ERR_CUDA (load failed).
  */
 typedef struct {
     uint64_t family;
     double compile_ms;
     int64_t source_bytes, cubin_bytes;
-    int32_t cached, reserved;
+    int32_t cached;  /* 0: compiled now, 1: loaded earlier in this process, 2: read from the disk cache */
+    int32_t reserved;
 } qmc_gen_info;
 
 int qmc_gen_source(const void *packed_host, int32_t precision, char *buf, size_t cap, size_t *len);

@@ -26,8 +26,10 @@
 
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <condition_variable>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -364,6 +366,7 @@ struct Compiled {
     std::string log;
     double ms = 0.0;
     size_t source_bytes = 0;
+    bool from_disk = false;
 };
 
 int compile(const std::string &src, Compiled &out) {
@@ -405,6 +408,7 @@ int compile(const std::string &src, Compiled &out) {
 struct Module {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t eval[QMC_N_CLASSES] = {nullptr, nullptr};
+    bool from_disk = false;
     double compile_ms = 0.0;
     int64_t source_bytes = 0, cubin_bytes = 0;
 };
@@ -436,9 +440,69 @@ uint64_t module_key(const PackedHeader *h, int precision) {
 }
 
 /* compile and load (no lock held) */
+/* ---------------------------------------------------------------- optional disk cache of compiled modules
+ * With QMC_GEN_CACHE_DIR set, cubins are kept in that directory under a name that covers everything they
+ * depend on: the module key (family, precision), the generator version, the embedded device sources and the
+ * NVRTC version.  A file is written to a temporary name and renamed, so concurrent processes never read a
+ * partial cubin. */
+uint64_t sources_hash() {
+    Fnv f;
+    for (const char *s : {qmc_src_qmcfi_h, qmc_src_qmc_internal_h, qmc_src_qmc_dev_cuh}) f.add(s, std::strlen(s));
+    int maj = 0, mnr = 0;
+    nvrtcVersion(&maj, &mnr);
+    f.add_i(maj * 1000 + mnr);
+    f.add_i(QMC_JIT_GENERATOR_VERSION);
+    return f.v;
+}
+
+std::string cache_path(uint64_t key) {
+    const char *dir = std::getenv("QMC_GEN_CACHE_DIR");
+    if (!dir || !*dir) return std::string();
+    char name[96];
+    std::snprintf(name, sizeof(name), "/qmcfi-%016llx-%016llx.cubin", (unsigned long long)key,
+                  (unsigned long long)sources_hash());
+    return std::string(dir) + name;
+}
+
+/* compile the family's source, or read its cubin from the disk cache */
+int compile_cached(const PackedHeader *h, int precision, Compiled &cc) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const std::string path = cache_path(module_key(h, precision));
+    if (!path.empty()) {
+        if (FILE *f = std::fopen(path.c_str(), "rb")) {
+            std::fseek(f, 0, SEEK_END);
+            const long sz = std::ftell(f);
+            std::fseek(f, 0, SEEK_SET);
+            if (sz > 0) {
+                cc.cubin.resize((size_t)sz);
+                if (std::fread(cc.cubin.data(), 1, (size_t)sz, f) == (size_t)sz) {
+                    std::fclose(f);
+                    cc.from_disk = true;
+                    cc.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                    return QMC_OK;
+                }
+            }
+            std::fclose(f);
+            cc.cubin.clear();
+        }
+    }
+    const int rc = compile(generate(h, lang_of(precision)), cc);
+    if (!rc && !path.empty()) {
+        const std::string tmp =
+            path + "." + std::to_string((unsigned long long)std::hash<std::thread::id>()(std::this_thread::get_id())) +
+            ".tmp";
+        if (FILE *f = std::fopen(tmp.c_str(), "wb")) {
+            const bool ok = std::fwrite(cc.cubin.data(), 1, cc.cubin.size(), f) == cc.cubin.size();
+            std::fclose(f);
+            if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+        }
+    }
+    return rc;
+}
+
 int build_module(const PackedHeader *h, int precision, std::unique_ptr<Module> &out) {
     Compiled cc;
-    int rc = compile(generate(h, lang_of(precision)), cc);
+    int rc = compile_cached(h, precision, cc);
     if (rc) return rc;
     std::unique_ptr<Module> m(new Module());
     if (cudaLibraryLoadData(&m->lib, cc.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
@@ -452,6 +516,7 @@ int build_module(const PackedHeader *h, int precision, std::unique_ptr<Module> &
         }
     }
     m->compile_ms = cc.ms;
+    m->from_disk = cc.from_disk;
     m->source_bytes = (int64_t)cc.source_bytes;
     m->cubin_bytes = (int64_t)cc.cubin.size();
     out = std::move(m);
@@ -583,13 +648,13 @@ int qmc_gen_compile(const void *packed_host, int32_t precision, int32_t load, qm
         if (info) std::memset(info, 0, sizeof(*info));
         if (info) info->family = family_key(h);
         if (!load) {
-            const std::string src = generate(h, lang_of(precision));
             Compiled cc;
-            const int rc = compile(src, cc);
+            const int rc = compile_cached(h, precision, cc);
             if (info) {
                 info->compile_ms = cc.ms;
                 info->source_bytes = (int64_t)cc.source_bytes;
                 info->cubin_bytes = (int64_t)cc.cubin.size();
+                info->cached = cc.from_disk ? 2 : 0;
             }
             return rc;
         }
@@ -603,7 +668,7 @@ int qmc_gen_compile(const void *packed_host, int32_t precision, int32_t load, qm
             info->compile_ms = m->compile_ms;
             info->source_bytes = m->source_bytes;
             info->cubin_bytes = m->cubin_bytes;
-            info->cached = cached ? 1 : 0;
+            info->cached = cached ? 1 : (m->from_disk ? 2 : 0);
         }
         return QMC_OK;
     } catch (const std::bad_alloc &) {

@@ -335,3 +335,19 @@ def test_nvrtc_compiles_generated_source_without_a_device():
     for precision in (N.QMC_PREC_MIXED, N.QMC_PREC_FP64):
         info = api.gen_compile(prepared(W.CONFIG1), load=False, precision=precision)
         assert info.cubin_bytes > 0 and info.source_bytes > 0 and info.compile_ms > 0
+
+
+def test_disk_cache_of_compiled_modules(tmp_path, monkeypatch):
+    """QMC_GEN_CACHE_DIR: the first compilation writes the cubin, the next one (another family member, another
+    kinematic point) reads it instead of running NVRTC; other precisions and families get their own files."""
+    monkeypatch.setenv("QMC_GEN_CACHE_DIR", str(tmp_path))
+    a = api.gen_compile(prepared(W.CONFIG1), load=False)
+    files = sorted(os.listdir(tmp_path))
+    assert a.cached == 0 and len(files) == 1 and files[0].endswith(".cubin")
+    b = api.gen_compile(prepared(W.CONFIG1, s=7.0, t=-2.5), load=False)
+    assert b.cached == 2 and b.cubin_bytes == a.cubin_bytes and b.compile_ms < a.compile_ms
+    c = api.gen_compile(prepared(W.CONFIG1), load=False, precision=N.QMC_PREC_FP64)
+    assert c.cached == 0 and len(os.listdir(tmp_path)) == 2
+    monkeypatch.delenv("QMC_GEN_CACHE_DIR")
+    d = api.gen_compile(prepared(W.CONFIG1), load=False)
+    assert d.cached == 0
