@@ -50,10 +50,11 @@ METRIC = "integrand evals/s"
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
-# DRAM bytes per launch of the evaluation kernel from ncu (profiles/qmc_eval_kernel_massive_box.md), valid
-# while the device code hashes to KERNEL_HASH; null otherwise
-TRAFFIC_BYTES = None
-KERNEL_HASH = None
+# DRAM bytes per launch of the FP64 evaluation kernel (qd_eval_c1) of the bench step, from one single-pass ncu
+# capture of that launch (profiles/qmc_eval_kernel_massive_box.md); valid while the device code and the
+# generator hash to KERNEL_HASH, null otherwise
+TRAFFIC_BYTES = 664064 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
+KERNEL_HASH = "550271491d84d20e"
 
 
 INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3}
@@ -61,7 +62,7 @@ INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("qmc_dev.cuh", "qmc_kern_d3.cu"):
+    for f in ("qmc_dev.cuh", "qmc_jit.cpp"):
         with open(os.path.join(ROOT, "paper_1508_02512_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
