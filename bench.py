@@ -169,6 +169,16 @@ def dist_setup(args):
     return world, rank, local, dist
 
 
+def max_over_ranks(value, dist, device="cpu"):
+    """The largest of the ranks' values (timing of the slowest replica); the value itself on one rank."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def korobov_vector(n, a=76):
     """An admissible generating vector (1, a, a^2, ...) mod n for timing the oracle: the cost of an evaluation
     does not depend on which vector the lattice uses."""
@@ -198,7 +208,9 @@ def cpu_baseline(cfg=None, n_log2=0):
 
 def main_reference(args):
     world, rank, local, dist = dist_setup(args)
-    if rank != 0:
+    if rank != 0:  # the oracle runs once, on rank 0; the other ranks leave without work
+        if dist:
+            dist.destroy_process_group()
         return
     from oracle import integrate as OI
     from oracle import lattice as OL
@@ -220,10 +232,12 @@ def main_reference(args):
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": workload_config(n),
+                      "data": "synthetic", "config": workload_config(W.CONFIG1, n, len(prob.sectors), f"{LAMBDA}"),
                       "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    if dist:
+        dist.destroy_process_group()
 
 
 def main_ours(args):
@@ -303,9 +317,7 @@ def main_ours(args):
     clocks = sampler.stop()
     elapsed = t1 - t0
     if dist:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev_name)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dist, dev_name)
     eval_ms = [a.elapsed_time(b) for a, b, c in evs]
     pass_ms = [a.elapsed_time(c) for a, b, c in evs]
     sign_failures = int(fails.sum().item())
@@ -348,9 +360,7 @@ def main_ours(args):
     torch.cuda.synchronize()
     tmix = time.perf_counter() - tm0
     if dist:
-        t = torch.tensor([tmix], dtype=torch.float64, device=dev_name)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmix = float(t.item())
+        tmix = max_over_ranks(tmix, dist, dev_name)
     mix_eval_ms = statistics.mean(a.elapsed_time(b) for a, b, c in evs_m)
     s64 = sums.cpu().numpy()
     s32 = sums_m.cpu().numpy()
@@ -404,9 +414,7 @@ def main_ours(args):
         e2e_step()
     te = time.perf_counter() - te0
     if dist:
-        t = torch.tensor([te], dtype=torch.float64, device=dev_name)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+        te = max_over_ranks(te, dist, dev_name)
     h2d = len(prep.packed) + sh_pinned.numel() * 8 + lam_pinned.numel() * 8
     d2h = sums_h.numel() * 8 + fails_h.numel() * 8
     ctx.close()
