@@ -239,8 +239,8 @@ int qmc_gen_compile(const void *packed_host, int32_t precision, int32_t load, qm
  * evaluation launch of `pass` (qmc_eval_partials semantics, synchronous on `stream`) once per candidate shape,
  * block in {64, 128, 256} threads (those the pass allows) x points_per_thread in {4, 8, 16, 32}, times each
  * with CUDA events (one untimed launch first), returns the timings and the fastest shape in *out, and records
- * that shape for the
- * family of the image, the pass's precision and evaluator and the lattice-size bucket (smallest 2^k >= n).
+ * that shape for the family of the image, the pass's precision and evaluator and the lattice-size bucket
+ * (smallest 2^k >= n).
  * From then on, in this process, passes of that key whose block and points_per_thread are both 0 use the
  * recorded shape: qmc_scratch_bytes, qmc_eval_sums, qmc_integrate and the serving loop included.  Results
  * depend on the shape only through the summation order.  pass->block/points_per_thread are ignored.
@@ -339,7 +339,7 @@ typedef struct {
     int32_t order_min, n_orders;
     double value[QMC_MAX_ORDERS][2];  /* Laurent coefficients (re, im), order_min + k */
     double error[QMC_MAX_ORDERS][2];  /* standard errors of re and im (Eq. 20) */
-    int64_t n_final;                  /* lattice size of the last pass */
+    int64_t n_final;                  /* largest lattice size any sector reached */
     int64_t evals;                    /* sector x shift x point evaluations, all passes */
     double seconds;                   /* wall time of qmc_integrate */
     double kernel_ms;                 /* device time of the evaluation kernels, all passes */
@@ -374,9 +374,14 @@ int qmc_set_kinematics(qmc_ctx *ctx, int32_t integral_id, const double *invarian
 int qmc_eval_sums_host(qmc_ctx *ctx, const void *packed_host, const qmc_pass *pass, const double *shifts_host,
                        const double *lambda_host, double *sums_host, int64_t *fails_host);
 
-/* Blocking: climbs the lattice ladder, running one pass per size (all sectors and shifts), halving lambda of
- * sectors that fail the sign check, until every order meets the tolerance (or a limit is reached).
- * Returns the status also stored in out->status. */
+/* Blocking: integrates to the requested accuracy (Sec. III: shifted rank-1 lattice rules of growing size, Eqs.
+ * 19-20 for the value and its error).  Each step evaluates the sectors that need it (all shifts): lambda of
+ * sectors failing the sign check of Eq. (14) is halved and they are re-run; otherwise, unless opt->lock_step,
+ * only the sectors holding most of the remaining variance per unit of cost move to the next lattice size
+ * (per-sector lattices; the paper lets all sectors climb together, as lock_step does).  Mixed precision runs a
+ * step in FP32 only where its FP64 cost would exceed ~1e8 flop, after the FP32/FP64 probe of
+ * qmc_probe_precision.  Stops when every order meets the tolerance, or at max_n, max_seconds or the end of the
+ * ladder.  Returns the status also stored in out->status. */
 int qmc_integrate(qmc_ctx *ctx, int32_t integral_id, const qmc_options *opt, qmc_result *out);
 
 /* ------------------------------------------------------------------ serving (continuous batching) */
