@@ -8,7 +8,20 @@ Paper Sec. II.
     at t = 0, pick a set S' of variables on which one of them vanishes identically and split the sector into
     |S'| subsectors t_j -> t_k t_j (j in S' \\ {k}, Jacobian t_k^{|S'|-1}).  S' is the smallest such set,
     ties broken by the lexicographically smallest index tuple.  A depth cap turns non-termination into an
-    error.  The geometric strategy that the paper prefers (Sec. II, after Eq. 9) is not used.
+    error.
+  * Geometric decomposition (the strategy the paper prefers, Sec. II after Eq. 9; Kaneko and Ueda): by the
+    Cheng-Wu theorem the delta function may keep x_N = 1 alone, leaving x_1..x_{N-1} in (0, inf).  In the
+    logarithms u_j = log x_j, the normal fan of the Newton polytope of U F (exponents of x_1..x_{N-1}) covers
+    R^{N-1}; on a simplicial cone with integer generators m_1..m_{N-1} (u = -sum_i m_i log y_i, y in (0,1]) every
+    monomial x^v becomes prod_i y_i^{-<m_i, v>}, and the term v* of U (of F) maximising <m, .> over the whole
+    cone is the same for all of it, so U = prod_i y_i^{-<m_i, vU*>} Ut(y) with Ut(0) = c_{vU*} != 0.  The
+    measure prod_j x_j^{nu_j - 1} dx_j becomes |det m| prod_i y_i^{-<m_i, nu> - 1} dy_i.  Cones of the fan with
+    more generators than the dimension are split by the pulling triangulation.  Ordering rules that fix the
+    sector list: facets are named by their primitive outer normals, vertices are visited in lexicographic
+    order, a vertex cone's generators are listed lexicographically, the pulling apex is the first generator,
+    the facets of a cone are visited in lexicographic order of their generator index tuples, and a sector's
+    variables follow its generators' lexicographic order.  scipy's convex hull only proposes the polytope's
+    facets; each is rebuilt and checked in exact arithmetic.
   * Exponents, Eq. (9): each leaf is D * prod_j t_j^{A_j + B_j eps} * Ut^{eU(eps)} / Ft^{eF(eps)} with
     eU = N_nu - (L+1)(2 - eps), eF = N_nu - L(2 - eps); the monomials pulled out of U and F are folded into
     A and B.  Ut and Ft keep their constant term (they are C(1+H) and C'(1+H') of Eqs. (7)-(8)).
@@ -23,6 +36,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 from fractions import Fraction
 from itertools import combinations, permutations
+from math import gcd
 from typing import Dict, List, Tuple
 
 from . import feynman as fy
@@ -118,6 +132,163 @@ def _iterate(sec: Sector, eU, eF, depth, max_depth, out):
         _iterate(sub, eU, eF, depth + 1, max_depth, out)
 
 
+# ---------------------------------------------------------------- geometric strategy: exact linear algebra
+def _q_rank(rows) -> int:
+    """Rank of a list of rational vectors (Gaussian elimination in Fractions)."""
+    A = [[Fraction(x) for x in r] for r in rows]
+    rank, ncol = 0, len(A[0]) if A else 0
+    for c in range(ncol):
+        p = next((i for i in range(rank, len(A)) if A[i][c] != 0), None)
+        if p is None:
+            continue
+        A[rank], A[p] = A[p], A[rank]
+        for i in range(rank + 1, len(A)):
+            f = A[i][c] / A[rank][c]
+            if f:
+                A[i] = [a - f * b for a, b in zip(A[i], A[rank])]
+        rank += 1
+    return rank
+
+
+def _q_det(rows) -> Fraction:
+    A = [[Fraction(x) for x in r] for r in rows]
+    n, det = len(A), Fraction(1)
+    for c in range(n):
+        p = next((i for i in range(c, n) if A[i][c] != 0), None)
+        if p is None:
+            return Fraction(0)
+        if p != c:
+            A[c], A[p] = A[p], A[c]
+            det = -det
+        det *= A[c][c]
+        for i in range(c + 1, n):
+            f = A[i][c] / A[c][c]
+            if f:
+                A[i] = [a - f * b for a, b in zip(A[i], A[c])]
+    return det
+
+
+def _cross(rows):
+    """Generalised cross product of k-1 vectors in Q^k: the form x -> det(rows; x), by cofactors."""
+    k = len(rows) + 1
+    return [(-1) ** (k - 1 + j) * _q_det([[r[c] for c in range(k) if c != j] for r in rows]) for j in range(k)]
+
+
+def _primitive(v):
+    den = 1
+    for x in v:
+        den = den * Fraction(x).denominator // gcd(den, Fraction(x).denominator)
+    w = [int(Fraction(x) * den) for x in v]
+    g = 0
+    for x in w:
+        g = gcd(g, abs(x))
+    return tuple(x // g for x in w)
+
+
+def _independent(vectors, want):
+    """Indices of the first `want` linearly independent vectors (greedy, in order)."""
+    chosen = []
+    for i, v in enumerate(vectors):
+        if _q_rank([vectors[j] for j in chosen] + [v]) == len(chosen) + 1:
+            chosen.append(i)
+            if len(chosen) == want:
+                break
+    return chosen
+
+
+def _polytope_facets(points):
+    """[(primitive outer normal m, h)] with <m, p> <= h on all points, equality on a facet."""
+    import numpy as np
+    from scipy.spatial import ConvexHull
+
+    d = len(points[0])
+    hull = ConvexHull(np.array(points, dtype=float))
+    out = {}
+    for eq in hull.equations:
+        on = [p for p in points if abs(sum(a * b for a, b in zip(p, eq[:-1])) + eq[-1]) <= 1e-7]
+        diffs = [[a - b for a, b in zip(p, on[0])] for p in on[1:]]
+        basis = _independent(diffs, d - 1)
+        if len(basis) != d - 1 or _q_rank(diffs) != d - 1:
+            raise DecompositionError("degenerate facet")
+        m = _primitive(_cross([diffs[i] for i in basis]))
+        if sum(a * b for a, b in zip(m, eq[:-1])) < 0:
+            m = tuple(-x for x in m)
+        h = sum(a * b for a, b in zip(m, on[0]))
+        vals = [sum(a * b for a, b in zip(m, p)) for p in points]
+        if max(vals) != h or sorted(p for p, v in zip(points, vals) if v == h) != sorted(on):
+            raise DecompositionError("inexact facet")
+        out[m] = h
+    return sorted(out.items())
+
+
+def _facets_of_cone(gens, idx, dim):
+    """Facets of the dim-dimensional cone spanned by gens[idx] (sorted tuples of indices), found in coordinates
+    of a basis of its span: the cofactor form of every dim - 1 independent generators must have one sign."""
+    basis = [idx[i] for i in _independent([gens[i] for i in idx], dim)]
+    # coordinates c with gens[i] = sum_b c_b gens[basis[b]]: solve by Cramer's rule on `dim` independent rows
+    cols = _independent([[gens[b][j] for b in basis] for j in range(len(gens[0]))], dim)
+    Bm = [[gens[b][j] for b in basis] for j in cols]            # dim x dim, invertible
+    detB = _q_det(Bm)
+
+    def coords(g):
+        rhs = [g[j] for j in cols]
+        return [_q_det([[rhs[r] if c == b else Bm[r][c] for c in range(dim)] for r in range(dim)]) / detB
+                for b in range(dim)]
+
+    C = {i: coords(gens[i]) for i in idx}
+    found = set()
+    for comb in combinations(idx, dim - 1):
+        if _q_rank([C[i] for i in comb]) != dim - 1:
+            continue
+        form = _cross([C[i] for i in comb])
+        vals = {i: sum(a * b for a, b in zip(form, C[i])) for i in idx}
+        if all(v >= 0 for v in vals.values()) or all(v <= 0 for v in vals.values()):
+            found.add(tuple(i for i in idx if vals[i] == 0))
+    return sorted(found)
+
+
+def _pulling(gens, idx, dim):
+    if len(idx) == dim:
+        return [tuple(idx)]
+    out = []
+    for face in _facets_of_cone(gens, idx, dim):
+        if idx[0] not in face:
+            out += [(idx[0],) + c for c in _pulling(gens, list(face), dim - 1)]
+    return out
+
+
+def geometric_sectors(U, F, nu: List[int], eU, eF):
+    """Sectors of the geometric strategy (module docstring), final: Ut and Ft have nonzero constant terms."""
+    n = len(nu)
+    d = n - 1
+    for poly in (U, F):
+        if len({sum(e) for e in poly}) != 1:
+            raise DecompositionError("polynomial is not homogeneous")
+    points = sorted({tuple(a + b for a, b in zip(eu[:d], ef[:d])) for eu in U for ef in F})
+    facets = _polytope_facets(points)
+    secs = []
+    for p in points:
+        gens = sorted(m for m, h in facets if sum(a * b for a, b in zip(m, p)) == h)
+        if len(gens) < d or _q_rank(gens) != d:
+            continue
+        for cone in _pulling(gens, list(range(len(gens))), d):
+            ms = [gens[i] for i in sorted(cone)]
+            D = abs(_q_det(ms))
+            new, shift = [], []
+            for poly in (U, F):
+                pair = {e: [sum(m[j] * e[j] for j in range(d)) for m in ms] for e in poly}
+                top = [max(v[i] for v in pair.values()) for i in range(d)]
+                if sum(1 for v in pair.values() if v == top) != 1:
+                    raise DecompositionError("cone not inside one vertex's normal cone")
+                new.append({tuple(t - x for t, x in zip(top, v)): poly[e] for e, v in pair.items()})
+                shift.append([-t for t in top])
+            A = [-sum(m[j] * nu[j] for j in range(d)) - 1 + shift[0][i] * eU[0] - shift[1][i] * eF[0]
+                 for i, m in enumerate(ms)]
+            B = [shift[0][i] * eU[1] - shift[1][i] * eF[1] for i in range(d)]
+            secs.append(Sector(("geometric", p, tuple(ms)), A, B, new[0], new[1], D))
+    return secs
+
+
 def exponents_eU_eF(n_nu: int, loops: int):
     """(eU0, eU1), (eF0, eF1) with U^{eU0 + eU1 eps} / F^{eF0 + eF1 eps}, D = 4 - 2 eps (Eq. 2)."""
     return (n_nu - 2 * (loops + 1), loops + 1), (n_nu - 2 * loops, loops)
@@ -171,13 +342,16 @@ def decompose(topo, zero_invariants=(), strategy="iterated", max_depth=40):
     F = drop_zero_invariants(F, zero)
     nu = [p.nu for p in topo.props]
     eU, eF = exponents_eU_eF(sum(nu), topo.loops)
-    if strategy == "iterated":
+    leaves: List[Sector] = []
+    if strategy == "geometric":
+        leaves = geometric_sectors(U, F, nu, eU, eF)
+        start = []
+    elif strategy == "iterated":
         start = primary_sectors(U, F, nu)
     elif strategy == "hepp":
         start = hepp_sectors(U, F, nu)
     else:
         raise ValueError(strategy)
-    leaves: List[Sector] = []
     for sec in start:
         _iterate(sec, eU, eF, 0, max_depth, leaves)
     for sec in leaves:

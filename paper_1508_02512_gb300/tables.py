@@ -9,6 +9,10 @@ form of the paper's Eq. (1) into the table that `qmc_prepare` / `qmc_load_sector
   * iterated decomposition (Eqs. 7-9): while U or F fails to have a nonzero constant term after its monomial
     factor is pulled out, take the smallest variable set S (lexicographically first) on which one of them
     vanishes identically and split into |S| subsectors t_j -> t_k t_j (j in S, j != k), Jacobian t_k^{|S|-1};
+  * or the geometric decomposition the paper prefers (Sec. II, after Eq. 9; Kaneko and Ueda): x_N = 1, the other
+    x_j range over (0, inf), and the normal fan of the Newton polytope of U F, triangulated into unimodular or
+    simplicial cones, splits that range into sectors x_j = prod_i y_i^{-m_ij} (m_i the cone's generators),
+    y in (0, 1]^{N-1}, on each of which U and F factorise with a nonzero constant term;
   * exponents of Eq. (9): prod_j t_j^{A_j + B_j eps} with A, B collecting nu_j - 1, the Jacobians and the
     monomials of U^{eU0 + eU1 eps} / F^{eF0 + eF1 eps}, eU = N_nu - (L+1)(2 - eps), eF = N_nu - L(2 - eps).
 
@@ -24,8 +28,10 @@ Binary table (little-endian, 8-byte aligned), read by csrc/qmc_prepare.cpp:
 """
 from __future__ import annotations
 
+import math
 import struct
 from dataclasses import dataclass
+from fractions import Fraction
 from itertools import combinations, permutations
 from typing import List, Sequence, Tuple
 
@@ -216,8 +222,155 @@ def _leaves(U0: Poly, F0: Poly, A0, B0, eU, eF, max_depth: int) -> List[SectorRe
     return out
 
 
-def decompose(topo, zero_invariants: Sequence[str] = (), max_depth: int = 40) -> Tuple[List[SectorRecord], dict]:
-    """Leaf sectors of the iterated decomposition and the integral's metadata."""
+# ------------------------------------------------------------------------------------------- geometric strategy
+# Ordering rules (they fix the table, sector by sector):
+#   * facets of the Newton polytope are identified by their primitive integer outer normals m (<m, p> <= h);
+#   * vertices are taken in lexicographic order of their exponent vectors; a vertex's normal cone is spanned by
+#     the normals of the facets through it, listed in lexicographic order;
+#   * a cone with more generators than its dimension is split by the pulling triangulation from its first
+#     generator: the cone over each facet not containing it (facets in lexicographic order of their generator
+#     index tuples), recursively;
+#   * the variables y_1..y_{N-1} of a sector follow its generators in lexicographic order.
+
+
+def _null_basis(rows: np.ndarray, d: int) -> List[np.ndarray]:
+    """Primitive integer basis of {x in Q^d : rows x = 0}, one vector per free column of the exact reduced row
+    echelon form.  Its length is d - rank(rows)."""
+    R = [[Fraction(int(v)) for v in r] for r in np.asarray(rows).reshape(-1, d)]
+    piv: List[int] = []
+    for c in range(d):
+        r = len(piv)
+        p = next((i for i in range(r, len(R)) if R[i][c] != 0), None)
+        if p is None:
+            continue
+        R[r], R[p] = R[p], R[r]
+        lead = R[r][c]
+        R[r] = [v / lead for v in R[r]]
+        for i in range(len(R)):
+            if i != r and R[i][c] != 0:
+                f = R[i][c]
+                R[i] = [a - f * b for a, b in zip(R[i], R[r])]
+        piv.append(c)
+    out = []
+    for f in [c for c in range(d) if c not in piv]:
+        v = [Fraction(0)] * d
+        v[f] = Fraction(1)
+        for i, c in enumerate(piv):
+            v[c] = -R[i][f]
+        scale = math.lcm(*(x.denominator for x in v))
+        w = np.array([int(x * scale) for x in v], np.int64)
+        out.append(w // np.gcd.reduce(np.abs(w)))
+    return out
+
+
+def _int_det(M: np.ndarray) -> int:
+    """Exact determinant of a small integer matrix (fraction-free Bareiss elimination)."""
+    A = [[int(v) for v in r] for r in M]
+    n, sign, prev = len(A), 1, 1
+    for k in range(n - 1):
+        if A[k][k] == 0:
+            p = next((i for i in range(k + 1, n) if A[i][k] != 0), None)
+            if p is None:
+                return 0
+            A[k], A[p] = A[p], A[k]
+            sign = -sign
+        for i in range(k + 1, n):
+            for j in range(k + 1, n):
+                A[i][j] = (A[i][j] * A[k][k] - A[i][k] * A[k][j]) // prev
+        prev = A[k][k]
+    return sign * A[n - 1][n - 1]
+
+
+def _cone_facets(G: np.ndarray, idx: List[int], dim: int) -> List[Tuple[int, ...]]:
+    """Facets of the dim-dimensional cone spanned by the rows G[idx], as sorted tuples of the generator indices
+    they contain.  A facet is the zero set of a linear form that vanishes on dim - 1 independent generators and
+    has one sign on all of them."""
+    d = G.shape[1]
+    found = set()
+    for comb in combinations(idx, dim - 1):
+        ns = _null_basis(G[list(comb)], d)
+        if d - len(ns) != dim - 1:
+            continue
+        vals = next(v for v in (G[idx] @ b for b in ns) if np.any(v))  # the form, up to sign, on span(G[idx])
+        if np.all(vals >= 0) or np.all(vals <= 0):
+            found.add(tuple(i for i, x in zip(idx, vals) if x == 0))
+    return sorted(found)
+
+
+def _pulling_triangulation(G: np.ndarray, idx: List[int], dim: int) -> List[Tuple[int, ...]]:
+    """Simplicial cones (generator index tuples) of the pulling triangulation of cone(G[idx]) from G[idx[0]]."""
+    if len(idx) == dim:
+        return [tuple(idx)]
+    apex = idx[0]
+    cones: List[Tuple[int, ...]] = []
+    for face in _cone_facets(G, idx, dim):
+        if apex not in face:
+            cones.extend((apex,) + c for c in _pulling_triangulation(G, list(face), dim - 1))
+    return cones
+
+
+def _newton_facets(pts: np.ndarray) -> List[Tuple[Tuple[int, ...], int]]:
+    """Facets (primitive outer normal m, h = max_p <m, p>) of the convex hull of integer points spanning R^d.
+    scipy's Quickhull proposes the supporting hyperplanes; each is rebuilt exactly from the points on it and
+    checked to bound all points with a point set of affine rank d - 1."""
+    from scipy.spatial import ConvexHull
+
+    d = pts.shape[1]
+    hull = ConvexHull(pts.astype(np.float64))
+    facets = {}
+    for eq in hull.equations:
+        on = np.flatnonzero(np.abs(pts @ eq[:-1] + eq[-1]) <= 1e-7)
+        ns = _null_basis(pts[on[1:]] - pts[on[0]], d) if len(on) >= d else []
+        if len(ns) != 1:
+            raise TableError("degenerate facet of the Newton polytope")
+        m = ns[0] if float(ns[0] @ eq[:-1]) > 0 else -ns[0]
+        h = int(pts[on[0]] @ m)
+        vals = pts @ m
+        if np.any(vals > h) or not np.array_equal(np.flatnonzero(vals == h), on):
+            raise TableError("inexact facet of the Newton polytope")
+        facets[tuple(int(x) for x in m)] = h
+    return sorted(facets.items())
+
+
+def _geometric_leaves(U: Poly, F: Poly, nu: Sequence[int], eU, eF) -> List[SectorRecord]:
+    """Sectors of the geometric strategy for U, F in N variables (x_N = 1)."""
+    n = U.e.shape[1]
+    d = n - 1
+    if len(np.unique(U.e.sum(axis=1))) != 1 or len(np.unique(F.e.sum(axis=1))) != 1:
+        raise TableError("Symanzik polynomial is not homogeneous")
+    Ue, Fe = U.e[:, :d].astype(np.int64), F.e[:, :d].astype(np.int64)
+    pts = np.unique((Ue[:, None, :] + Fe[None, :, :]).reshape(-1, d), axis=0)
+    facets = _newton_facets(pts)
+    NM = np.array([m for m, _ in facets], np.int64)
+    H = np.array([h for _, h in facets], np.int64)
+    nu_d = np.array(nu[:d], np.int64)
+    out: List[SectorRecord] = []
+    for p in pts:  # lexicographic (np.unique sorts rows)
+        G = NM[(NM @ p) == H]
+        if len(G) < d or len(_null_basis(G, d)) != 0:
+            continue  # p is not a vertex
+        for cone in _pulling_triangulation(G, list(range(len(G))), d):
+            M = G[sorted(cone)]
+            det = abs(_int_det(M))
+            if det == 0:
+                raise TableError("degenerate cone in the triangulation")
+            polys, b = [], []
+            for P, E in ((U, Ue), (F, Fe)):
+                ev = E @ M.T                       # <m_i, v> for every term v
+                top = ev.max(axis=0)
+                if np.count_nonzero(np.all(ev == top, axis=1)) != 1:
+                    raise TableError("cone is not inside the normal cone of one vertex")
+                polys.append(Poly((top - ev).astype(np.int32), P.c.copy()).simplified())
+                b.append(-top)
+            A = -(M @ nu_d) - 1 + b[0] * eU[0] - b[1] * eF[0]
+            B = b[0] * eU[1] - b[1] * eF[1]
+            out.append(SectorRecord(A.astype(np.int32), B.astype(np.int32), polys[0], polys[1], float(det)))
+    return out
+
+
+def decompose(topo, zero_invariants: Sequence[str] = (), max_depth: int = 40,
+              strategy: str = "iterated") -> Tuple[List[SectorRecord], dict]:
+    """Leaf sectors of the iterated (default) or geometric decomposition and the integral's metadata."""
     U, F = symanzik(topo)
     K = len(topo.invariants)
     for name in zero_invariants:
@@ -232,7 +385,11 @@ def decompose(topo, zero_invariants: Sequence[str] = (), max_depth: int = 40) ->
     eU = (n_nu - 2 * (L + 1), L + 1)
     eF = (n_nu - 2 * L, L)
     leaves: List[SectorRecord] = []
-    for l in range(n):
+    if strategy == "geometric":
+        leaves = _geometric_leaves(U, F, nu, eU, eF)
+    elif strategy != "iterated":
+        raise ValueError(f"unknown decomposition strategy {strategy!r}")
+    for l in range(n if strategy == "iterated" else 0):
         keep = [j for j in range(n) if j != l]
         Ul = Poly(U.e[:, keep], U.c)
         Fl = Poly(F.e[:, keep], F.c)
@@ -311,9 +468,9 @@ def read_table(blob: bytes):
     return meta, leaves
 
 
-def compile_integral(topo, zero_invariants: Sequence[str] = ()) -> bytes:
+def compile_integral(topo, zero_invariants: Sequence[str] = (), strategy: str = "iterated") -> bytes:
     """Sector table (bytes) of `topo` for the kinematic class in which `zero_invariants` vanish."""
-    leaves, meta = decompose(topo, zero_invariants)
+    leaves, meta = decompose(topo, zero_invariants, strategy=strategy)
     return write_table(leaves, meta)
 
 

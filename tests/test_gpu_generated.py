@@ -113,3 +113,27 @@ def test_generated_fp64_sums_match_oracle_to_1e12(cfg):
         worst = max(worst, float((np.abs(gen[s, :, :k] - o) / np.maximum(l1c, 1e-300)).max()))
     print(f"{cfg.name}: FP64 generated |gpu-oracle| / term magnitudes = {worst:.2e}")
     assert worst <= 1e-12
+
+
+def test_generated_fp32_on_geometric_sectors_with_four_poles():
+    """Mixed-precision (FP32) generated evaluation of the massless double box of Table 2 (geometric strategy,
+    sectors with up to four singular variables) against the FP64 oracle, at the FP32 bound."""
+    topo, pt = W.double_box_planar(False), W.PAPER_IB_POINTS["-1,0,0,-1"]
+    blob = T.compile_integral(topo, T.zero_invariants_of(topo, pt), strategy="geometric")
+    prep = api.prepare(blob, W.kinematics(topo, **pt), -4, 0)
+    dev = api.DeviceIntegral(prep)
+    n = 251
+    z = OL.cbc_plain(n, 6)
+    shifts = W.shifts(29, 2)
+    lams = [0.0] * prep.info.n_sectors
+    gen, fails = run(dev, api.make_pass(n, z, len(shifts), 3, precision=N.QMC_PREC_MIXED,
+                                        evaluator=N.QMC_EVAL_GENERATED), shifts, lams)
+    assert not fails.any()
+    prob = OI.make_problem(topo, pt, -4, 0, "geometric")
+    worst = 0.0
+    for s, sec in enumerate(prob.sectors):
+        o, l1, _, l1c = OI.lattice_sums(sec, prob.e4, n, z, shifts, 0.0, 3, prob.kmax, with_scale=True)
+        k = o.shape[1]
+        worst = max(worst, float((np.abs(gen[s, :, :k] - o) / np.maximum(l1c, 1e-300)).max()))
+    print(f"massless double box, FP32 generated: worst |gen-oracle|/mag {worst:.2e}")
+    assert worst < MIXED_L1_BOUND

@@ -50,3 +50,34 @@ def test_two_loop_physical_matches_paper(name, topo, precision):
         assert agrees(ours[i], q, 5.0) or agrees(ours[i], table[(name, "vegas")][i], 4.0)
     print(f"{name} {'fp64' if precision == 0 else 'mixed'}: {dt:.2f} s to 2e-4 ({r.evals:.3e} evaluations, "
           f"largest lattice {r.n_final}, {r.fp64_reruns} sectors in FP64)")
+
+
+@pytest.mark.parametrize("precision", [N.QMC_PREC_FP64, N.QMC_PREC_MIXED], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("tag", sorted(W.PAPER_IB_POINTS))
+def test_massless_double_box_euclidean_matches_table2(tag, precision):
+    """Table 2: the massless planar double box I_B with two off-shell legs (geometric sector decomposition,
+    poles to eps^-4), integrated to 1e-4 relative error per order; every printed P_i must agree with the paper's
+    QMC column within 5 combined errors or with its Vegas column within 4."""
+    from paper_tables import agrees_real, golden_table2, to_paper_euclid
+
+    topo, pt = W.double_box_planar(False), W.PAPER_IB_POINTS[tag]
+    blob = T.compile_integral(topo, T.zero_invariants_of(topo, pt), strategy="geometric")
+    ctx = api.Context(0, 8 << 30)
+    iid = ctx.load_sectors(blob)
+    ctx.set_kinematics(iid, W.kinematics(topo, **pt), -4, 0)
+    ctx.integrate(iid, rel_tol=1e-2, n_shifts=16, seed=99, lam=0.0, precision=precision)  # compiles here
+    t0 = time.perf_counter()
+    r = ctx.integrate(iid, rel_tol=1e-4, n_shifts=16, seed=5, lam=0.0, max_seconds=300, precision=precision)
+    dt = time.perf_counter() - t0
+    ctx.close()
+    assert r.status == 0
+    val, err = api.result_arrays(r)
+    assert np.all(np.abs(val.imag) <= 1e-12 * np.max(np.abs(val)))
+    ours = to_paper_euclid(val.real, np.hypot(err[:, 0], err[:, 1]), pt["s"])
+    table = golden_table2()
+    for i in (4, 3, 2, 1, 0):
+        q = table[(tag, "qmc")][i]
+        print(f"{tag} P_{i}: ours {ours[i][0]:.6f} +- {ours[i][1]:.6f}   paper QMC {q[0]} +- {q[1]}")
+        assert agrees_real(ours[i], q, 5.0) or agrees_real(ours[i], table[(tag, "vegas")][i], 4.0)
+    print(f"I_B {tag} {'fp64' if precision == 0 else 'mixed'}: {dt:.2f} s to 1e-4 ({r.evals:.3e} evaluations, "
+          f"largest lattice {r.n_final}, {r.fp64_reruns} sectors in FP64)")

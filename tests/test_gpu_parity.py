@@ -26,6 +26,7 @@ from paper_1508_02512_gb300 import tables as T  # noqa: E402
 
 LEGS0 = dict(pp1=0.0, pp2=0.0, pp3=0.0, pp4=0.0)
 TOL = 1e-12
+N_EVAL_TABLE, N_EVAL_GENERATED = 1, 2   # qmc_pass.evaluator: QMC_EVAL_TABLE, QMC_EVAL_GENERATED
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -36,12 +37,12 @@ def _cuda():
     _native.lib()
 
 
-def setup_pair(topo, point, omin, omax):
-    blob = T.compile_integral(topo, T.zero_invariants_of(topo, point))
+def setup_pair(topo, point, omin, omax, strategy="iterated"):
+    blob = T.compile_integral(topo, T.zero_invariants_of(topo, point), strategy=strategy)
     kin = W.kinematics(topo, **point)
     prep = api.prepare(blob, kin, omin, omax)
     dev = api.DeviceIntegral(prep)
-    prob = OI.make_problem(topo, point, omin, omax)
+    prob = OI.make_problem(topo, point, omin, omax, strategy)
     assert prep.info.n_sectors == len(prob.sectors)
     return prep, dev, prob
 
@@ -113,6 +114,33 @@ def test_sums_match_oracle(name, topo, pt, orders, lam, n, block, P):
     sums = apply_kind1_phase(prep, prob, sums)
     worst = compare(prep, prob, sums, lams, n, z, shifts)
     print(f"{name}: worst |gpu-oracle|/L1 = {worst:.2e}")
+
+
+GEOMETRIC_CASES = [
+    # name, topology, point, orders, lambda, lattice size, block, points/thread
+    ("massless_dbox_table2", W.double_box_planar(False), W.PAPER_IB_POINTS["-1,0,0,-1"], (-4, 0), 0.0, 251, 64, 2),
+    ("massless_dbox_table2_col2", W.double_box_planar(False), W.PAPER_IB_POINTS["0,-1,0,-1"], (-4, 0), 0.0, 127,
+     128, 1),
+    ("planar_dbox", W.double_box_planar(True), dict(s=6.0, t=-2.0, msq=1.0, **LEGS0), (-2, 0), 0.25, 251, 64, 2),
+]
+
+
+@pytest.mark.parametrize("evaluator", [N_EVAL_TABLE, N_EVAL_GENERATED], ids=["table", "generated"])
+@pytest.mark.parametrize("name,topo,pt,orders,lam,n,block,P", GEOMETRIC_CASES, ids=[c[0] for c in GEOMETRIC_CASES])
+def test_geometric_sectors_match_oracle(name, topo, pt, orders, lam, n, block, P, evaluator):
+    """Tables of the geometric strategy (poles to eps^-4 in the massless double box: up to 16 subtraction
+    subsets per point, five series slots) through both FP64 evaluators."""
+    prep, dev, prob = setup_pair(topo, pt, *orders, strategy="geometric")
+    z = OL.cbc_plain(n, 6)
+    shifts = W.shifts(13, 3)
+    lams = [lam] * prep.info.n_sectors
+    p = api.make_pass(n, z, len(shifts), 3, block=block, points_per_thread=P, evaluator=evaluator)
+    sums, fails = gpu_sums(dev, p, shifts, lams)
+    assert not fails.any()
+    sums = apply_kind1_phase(prep, prob, sums)
+    worst = compare(prep, prob, sums, lams, n, z, shifts)
+    print(f"{name} ({'table' if evaluator == N_EVAL_TABLE else 'generated'}): {prep.info.n_sectors} sectors, "
+          f"worst |gpu-oracle|/L1 = {worst:.2e}")
 
 
 def test_edge_single_shift_tiny_lattice_and_transforms():

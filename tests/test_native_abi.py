@@ -72,6 +72,23 @@ def test_table_compiler_matches_oracle_decomposition(cfg):
     assert mine == ref
 
 
+GEOMETRIC_CASES = [(c.topology, T.zero_invariants_of(c.topology, c.point), c.name) for c in W.CONFIGS[:3]] + [
+    (W.double_box_planar(False), T.zero_invariants_of(W.double_box_planar(False), W.PAPER_IB_POINTS["0,-1,0,-1"]),
+     "massless_dbox_table2")]
+
+
+@pytest.mark.parametrize("topo,zero,name", GEOMETRIC_CASES, ids=[c[2] for c in GEOMETRIC_CASES])
+def test_geometric_table_matches_oracle_sector_by_sector(topo, zero, name):
+    """The geometric strategy, written twice (product: integer elimination; oracle: rational cofactors), must give
+    the same sectors in the same order: exponents, Jacobian D and both polynomials."""
+    meta, leaves = T.read_table(T.compile_integral(topo, zero, strategy="geometric"))
+    ref = OS.decompose(topo, zero, "geometric")
+    assert len(leaves) == len(ref)
+    for a, b in zip(leaves, ref):
+        assert canon_product([a], meta) == OS.canonical([b])
+        assert a.D == float(b.D)
+
+
 def test_symanzik_matches_oracle_for_all_topologies():
     from oracle import feynman as fy
     for topo in (W.bubble(True), W.triangle_massive(), W.box(True), W.double_box_planar(True),
@@ -115,6 +132,21 @@ def test_prepare_matches_oracle(cfg):
         d = prep.sector(s)
         assert (d.kind, d.sigma) == (sec.kind, sec.sigma)
     assert prep.info.flops_per_eval > 0
+
+
+def test_prepare_geometric_table_with_four_poles():
+    """qmc_prepare on the geometric table of the massless double box (Table 2): sector kinds, singular-variable
+    counts up to four, five series slots for eps^-4..eps^0, and the prefactor Gamma(3 + 2 eps)."""
+    topo, pt = W.double_box_planar(False), W.PAPER_IB_POINTS["-1,0,0,-1"]
+    blob = T.compile_integral(topo, T.zero_invariants_of(topo, pt), strategy="geometric")
+    prep = api.prepare(blob, W.kinematics(topo, **pt), -4, 0)
+    prob = OI.make_problem(topo, pt, -4, 0, "geometric")
+    assert prep.info.n_sectors == len(prob.sectors) == 143
+    assert prep.info.max_sigma == 4 and prep.info.n_slots == 5 and prep.info.pre_low == prob.pre_low == 0
+    assert np.allclose(list(prep.info.pre)[:5], prob.pre[:5], rtol=1e-14, atol=1e-15)
+    for s, sec in enumerate(prob.sectors):
+        d = prep.sector(s)
+        assert (d.kind, d.sigma) == (sec.kind, sec.sigma) == (0, sec.sigma)
 
 
 def test_prefactor_with_pole_matches_oracle():

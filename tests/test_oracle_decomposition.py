@@ -4,7 +4,10 @@
 * the massless bubble's sectors carry t^{-eps} (alpha = 0, beta = -1) and (1+t)^{-2+2eps};
 * the sum over sectors of the (finite) undecomposed integrand equals a direct adaptive cubature of the
   Feynman-parameter integral over the simplex (Eq. 2), for the Euclidean massive box and triangle;
-* each leaf polynomial has a nonzero constant term (the factorised form of Eqs. 7-8).
+* each leaf polynomial has a nonzero constant term (the factorised form of Eqs. 7-8);
+* geometric strategy: its simplicial cones tile the space of log x (every random direction lies inside exactly
+  one of them), its sectors sum to the simplex integral like the iterated ones, and it terminates (with
+  exponents >= -1) on the massless double box, where the iterated strategy does not.
 """
 from collections import Counter
 
@@ -41,7 +44,7 @@ def test_bubble_exponents():
         assert fy.substitute_invariants(s.U, {}) == {(0,): 1, (1,): 1}
 
 
-@pytest.mark.parametrize("strategy", ["iterated", "hepp"])
+@pytest.mark.parametrize("strategy", ["iterated", "hepp", "geometric"])
 def test_leaves_factorised(strategy):
     for topo in (W.box(False), W.box(True)):
         for s in sd.decompose(topo, MASSLESS_LEGS, strategy):
@@ -81,13 +84,14 @@ def _sector_integrand_eps0(sec, e4):
     return f
 
 
+@pytest.mark.parametrize("strategy", ["iterated", "geometric"])
 @pytest.mark.parametrize("case", ["box", "triangle"])
-def test_sectors_sum_to_simplex_integral(case):
+def test_sectors_sum_to_simplex_integral(case, strategy):
     if case == "box":
         topo, pt = W.box(True), dict(s=-3.0, t=-2.0, msq=1.0)
     else:
         topo, pt = W.triangle_massive(), dict(pp3=-3.0, msq=1.0)
-    prob = OI.make_problem(topo, pt, 0, 0)
+    prob = OI.make_problem(topo, pt, 0, 0, strategy)
     assert all(s.sigma == 0 for s in prob.sectors)
     total = sum(_gauss_cube(_sector_integrand_eps0(s, prob.e4), s.dim) for s in prob.sectors)
     # direct: Gamma(N - LD/2)/prod Gamma * int_simplex U^{eU0} / F^{eF0}, eps = 0 (prefactor = 1 here)
@@ -109,3 +113,43 @@ def test_sectors_sum_to_simplex_integral(case):
         ref, _ = si.dblquad(lambda x2, x1: integrand(x1, x2), 0, 1, 0, lambda x1: 1 - x1, epsabs=1e-14,
                             epsrel=1e-12)
     assert abs(total - ref) <= 1e-9 * abs(ref)
+
+
+def _cone_generators(sec):
+    """Generator rows m_i of a geometric sector (x_j = prod_i y_i^(-m_ij))."""
+    assert sec.label[0] == "geometric"
+    return np.array(sec.label[2], dtype=float)
+
+
+@pytest.mark.parametrize("topo,zero", [(W.box(False), MASSLESS_LEGS), (W.box(True), MASSLESS_LEGS),
+                                       (W.double_box_planar(False), ("pp2", "pp3")),
+                                       (W.double_box_nonplanar(True), MASSLESS_LEGS)],
+                         ids=["massless_box", "massive_box", "massless_dbox_2offshell", "nonplanar_dbox"])
+def test_geometric_cones_tile_log_space(topo, zero):
+    """The sectors' cones must cover R^(N-1) without overlap: a random direction u = log x lies in the interior
+    of exactly one cone, u = -sum_i s_i m_i with all s_i > 0 (brute force over all cones).  A missing facet of
+    the Newton polytope or a wrong triangulation leaves gaps or double cover; and each cone must be a unit of
+    Jacobian |det m| = D."""
+    secs = sd.decompose(topo, zero, "geometric")
+    rng = np.random.default_rng(11)
+    gens = [_cone_generators(s) for s in secs]
+    for s, g in zip(secs, gens):
+        assert abs(abs(np.linalg.det(g)) - float(s.D)) < 1e-9
+    for u in rng.standard_normal((300, gens[0].shape[1])):
+        inside = 0
+        for g in gens:
+            coef = np.linalg.solve(g.T, -u)
+            inside += bool(np.all(coef > 1e-12))
+        assert inside == 1
+
+
+def test_geometric_terminates_on_massless_double_box():
+    topo = W.double_box_planar(False)
+    with pytest.raises(sd.DecompositionError):
+        sd.decompose(topo, ("pp2", "pp3"), "iterated", max_depth=25)
+    secs = sd.decompose(topo, ("pp2", "pp3"), "geometric")
+    assert len(secs) == 143
+    assert max(len(s.singular) for s in secs) == 4 and min(min(s.A) for s in secs) == -1
+    for s in secs:
+        assert (0,) * 6 in s.U and (0,) * 6 in s.F
+        assert all(min(e) >= 0 for e in s.U) and all(min(e) >= 0 for e in s.F)

@@ -84,11 +84,11 @@ def massless_box_closed(s, t):
     return laurent(f, 0, 2)
 
 
-@pytest.mark.parametrize("strategy", ["iterated", "hepp"])
+@pytest.mark.parametrize("strategy", ["iterated", "hepp", "geometric"])
 def test_massless_box_config0(z4093, strategy):
     cfg = W.CONFIG0
     mean, err, fails, prob = run(cfg.topology, {**cfg.point, **LEGS0}, -2, 0, z4093, lam=0.0, strategy=strategy)
-    assert len(prob.sectors) == (12 if strategy == "iterated" else 32)
+    assert len(prob.sectors) == {"iterated": 12, "hepp": 32, "geometric": 12}[strategy]
     ref = massless_box_closed(-3.0, -2.0)
     assert abs(ref[0] - 2.0 / 3.0) < 1e-14  # 4/(st)
     assert close(mean, err, ref) and np.max(np.abs(mean - ref)) < 1e-7, (mean, ref, err)
@@ -100,6 +100,8 @@ def test_massive_box_lambda_and_strategy_independence(z4093):
     res = [run(cfg.topology, pt, 0, 0, z4093, m=16, lam=lam) for lam in (0.5, 0.25, 0.125)]
     res.append(run(cfg.topology, pt, 0, 0, z4093, m=16, lam=0.5, strategy="hepp"))
     assert len(res[-1][3].sectors) == 24 and len(res[0][3].sectors) == 4
+    res.append(run(cfg.topology, pt, 0, 0, z4093, m=16, lam=0.5, strategy="geometric"))
+    assert len(res[-1][3].sectors) == 4
     for mean, err, fails, _ in res:
         assert fails == 0
     m0, e0 = res[0][0], res[0][1]

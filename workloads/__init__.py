@@ -216,3 +216,11 @@ def serving_arrivals(n_requests: int, rate_per_s: float = 50.0, seed: int = 0):
     s = rng.uniform(4.5, 12.0, size=n_requests)
     t = rng.uniform(-4.0, -0.5, size=n_requests)
     return [(float(a), int(c), float(x), float(y)) for a, c, x, y in zip(times, cfg, s, t)]
+
+# The Euclidean points of the paper's Table 2 (Sec. IV): the massless planar double box with two off-shell legs,
+# s = t = u = -2/3 (so that pp1 + pp2 + pp3 + pp4 = -2), one point per pair of off-shell legs.
+PAPER_IB_POINTS = {
+    "-1,0,0,-1": dict(s=-2.0 / 3.0, t=-2.0 / 3.0, pp1=-1.0, pp4=-1.0),
+    "0,-1,0,-1": dict(s=-2.0 / 3.0, t=-2.0 / 3.0, pp2=-1.0, pp4=-1.0),
+    "0,0,-1,-1": dict(s=-2.0 / 3.0, t=-2.0 / 3.0, pp3=-1.0, pp4=-1.0),
+}
