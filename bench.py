@@ -57,7 +57,8 @@ TRAFFIC_BYTES = 664064 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of on
 KERNEL_HASH = "550271491d84d20e"
 
 
-INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3}
+INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3,
+             "massless_dbox_table2": W.PAPER_IB}
 
 
 def kernel_hash() -> str:
@@ -86,6 +87,9 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
     ap.add_argument("--serving", type=int, default=0,
                     help="run only the serving workload with this many requests and print its JSON line")
+    ap.add_argument("--paper-table2", action="store_true",
+                    help="run only the paper's Table 2 points (massless double box, Euclidean) to 1e-4 and print "
+                         "their JSON line")
     ap.add_argument("--serving-baseline", action="store_true",
                     help="with --serving: also run the requests one at a time through the plain FP64 path")
     return ap.parse_args()
@@ -94,6 +98,9 @@ def parse():
 def workload_config(cfg, n, ns, lam_desc):
     if cfg is W.CONFIG1:
         what = f"massive one-loop box, physical s=5 t=-1.5 m^2=1, lambda={lam_desc}, {ns} sectors"
+    elif cfg is W.PAPER_IB:
+        what = (f"massless planar double box (the paper's Table 2, legs p1^2 = p4^2 = -1), Euclidean s=t=u=-2/3, "
+                f"eps^-4..eps^0, geometric decomposition, {ns} six-dimensional sectors")
     else:
         what = (f"{'planar' if cfg is W.CONFIG2 else 'non-planar'} two-loop double box, physical s=6 t=-2, "
                 f"m^2=1 on four lines, eps^-2..eps^0, lambda={lam_desc}, {ns} six-dimensional sectors")
@@ -192,7 +199,7 @@ def cpu_baseline(cfg=None, n_log2=0):
     from oracle import lattice as OL
     cfg = cfg or W.CONFIG1
     n_log2 = n_log2 or (18 if cfg.topology.loops == 1 else 12)
-    prob = OI.make_problem(cfg.topology, {**cfg.point}, cfg.order_min, cfg.order_max)
+    prob = OI.make_problem(cfg.topology, {**cfg.point}, cfg.order_min, cfg.order_max, cfg.strategy)
     n = OL.prime_below(1 << n_log2)
     z = korobov_vector(n)
     shifts = W.shifts(12345, N_SHIFTS)
@@ -251,7 +258,7 @@ def main_ours(args):
     torch.cuda.set_device(local)
     dev_name = f"cuda:{local}"
     cfg = INTEGRALS[args.integral]
-    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point), strategy=cfg.strategy)
     prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
     di = api.DeviceIntegral(prep, dev_name)
     lat = dict(api.builtin_lattices())
@@ -564,6 +571,52 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0, lock
             "lattices": "one ladder for all sectors" if lock_step else "per sector"}
 
 
+def paper_table2(seeds=8, rel_tol=1e-4, device=0):
+    """The paper's Table 2 (massless planar double box with two off-shell legs, Euclidean, geometric
+    decomposition): qmc_integrate of each of its three points to `rel_tol` per order, FP64 and mixed precision,
+    p50 over `seeds` shift seeds after a warm-up integration (which compiles the generated evaluators); the
+    converted P_i of the first seed beside the paper's printed QMC values."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from paper_tables import golden_table2, to_paper_euclid
+    from paper_1508_02512_gb300 import _native as N
+    from paper_1508_02512_gb300 import api
+    from paper_1508_02512_gb300 import tables as T
+    torch.cuda.set_device(device)
+    topo = W.double_box_planar(False)
+    table = golden_table2()
+    out = {}
+    for tag, pt in W.PAPER_IB_POINTS.items():
+        blob = T.compile_integral(topo, T.zero_invariants_of(topo, pt), strategy="geometric")
+        row = {}
+        for prec, name in ((N.QMC_PREC_FP64, "fp64"), (N.QMC_PREC_MIXED, "mixed")):
+            ctx = api.Context(device, 4 << 30)
+            iid = ctx.load_sectors(blob)
+            ctx.set_kinematics(iid, W.kinematics(topo, **pt), -4, 0)
+            kw = dict(rel_tol=rel_tol, n_shifts=N_SHIFTS, lam=0.0, precision=prec, max_seconds=120)
+            t0 = time.perf_counter()
+            ctx.integrate(iid, seed=999, **kw)
+            first = time.perf_counter() - t0
+            ts, res = [], []
+            for s in range(seeds):
+                t0 = time.perf_counter()
+                r = ctx.integrate(iid, seed=1000 + s, **kw)
+                ts.append(time.perf_counter() - t0)
+                res.append(r)
+            ctx.close()
+            val, err = api.result_arrays(res[0])
+            P = to_paper_euclid(val.real, np.hypot(err[:, 0], err[:, 1]), pt["s"])
+            row[name] = {"p50_s": statistics.median(ts), "max_s": max(ts), "first_call_s": first,
+                         "converged": sum(r.status == 0 for r in res), "median_evals": int(statistics.median(
+                             r.evals for r in res)), "P": {f"P{i}": [P[i][0], P[i][1]] for i in (4, 3, 2, 1, 0)}}
+        row["sectors"] = api.prepare(blob, W.kinematics(topo, **pt), -4, 0).info.n_sectors
+        row["paper_qmc_gpu"] = {f"P{i}": list(table[(tag, "qmc")][i]) for i in (4, 3, 2, 1, 0)}
+        out[f"legs {tag}"] = row
+    return {"metric": f"time to {rel_tol:g} relative error per order, Table 2 points", "rel_tol": rel_tol,
+            "shifts": N_SHIFTS, "seeds": seeds, "points": out,
+            "paper_times_s": {"legs -1,0,0,-1": 2.2, "legs 0,-1,0,-1": 0.84, "legs 0,0,-1,-1": 2.2}}
+
+
 def profile_pass(precision="fp64", integral="massive_box"):
     """Two passes of the benchmark integral at n = 1048573 (largest prime below 2^20; 65521 for a two-loop
     integral), 16 shifts: the small case for ncu captures."""
@@ -572,7 +625,7 @@ def profile_pass(precision="fp64", integral="massive_box"):
     from paper_1508_02512_gb300 import api
     from paper_1508_02512_gb300 import tables as T
     cfg = INTEGRALS[integral]
-    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point))
+    blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point), strategy=cfg.strategy)
     prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
     dev = api.DeviceIntegral(prep)
     n = 1048573 if cfg.topology.loops == 1 else 65521
@@ -591,6 +644,8 @@ if __name__ == "__main__":
     a = parse()
     if a.serving:
         print(json.dumps({"metric": "serving time-to-1e-3", **serving_run(a.serving, baseline=a.serving_baseline)}))
+    elif a.paper_table2:
+        print(json.dumps(paper_table2()))
     elif a.profile_pass:
         profile_pass(a.precision, a.integral)
     elif a.impl == "reference":

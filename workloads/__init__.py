@@ -176,6 +176,7 @@ class Workload:
     lam: float = 0.5                   # contour-deformation parameter lambda
     rel_tol: float = 1e-3
     seed: int = 0
+    strategy: str = "iterated"         # sector decomposition strategy ("iterated" or "geometric")
 
     @property
     def kin(self) -> np.ndarray:
@@ -224,3 +225,7 @@ PAPER_IB_POINTS = {
     "0,-1,0,-1": dict(s=-2.0 / 3.0, t=-2.0 / 3.0, pp2=-1.0, pp4=-1.0),
     "0,0,-1,-1": dict(s=-2.0 / 3.0, t=-2.0 / 3.0, pp3=-1.0, pp4=-1.0),
 }
+
+# Table 2's first point as a benchmark workload (the iterated strategy does not terminate for this integral).
+PAPER_IB = Workload("massless_dbox_euclid_table2", double_box_planar(False), PAPER_IB_POINTS["-1,0,0,-1"], -4, 0,
+                    16, tuple(range(16, 27)), 3, 0.0, strategy="geometric")
