@@ -57,12 +57,52 @@ DEV double ipow(double v, int e) {
     for (int i = 0; i < k; ++i) r *= v;
     return e < 0 ? __drcp_rn(r) : r;
 }
+/* ------------------------------------------------------------------ table-driven FP64 logarithm */
+/* Tang's method (P. T. P. Tang, ACM Trans. Math. Softw. 16 (1990) 378): x = 2^e m with m in [1, 2); c = 1 + k/128
+   is the grid point nearest m (k = 0..128); log x = e ln2 + log c + log1p(r) with r = (m - c)/c, |r| <= 2^-8,
+   and log1p(r) from its Taylor series through r^7 (the first omitted term is below 2^-67).  m - c is exact.
+   The table {1/c, log c} is filled once per block (library logarithm) by logtab_init and read from shared
+   memory; zero, negative, subnormal and non-finite arguments go to the library. */
+struct LogTable {
+    double inv_c[129];
+    double log_c[129];
+};
+static __shared__ LogTable qmc_logtab;
+
+/* every thread of the block calls it; a __syncthreads() must follow before the first qlog */
+DEV void logtab_init() {
+    for (int k = threadIdx.x; k <= 128; k += blockDim.x) {
+        const double c = 1.0 + k / 128.0;
+        qmc_logtab.inv_c[k] = 1.0 / c;
+        qmc_logtab.log_c[k] = log(c);
+    }
+}
+
+DEV double qlog(double x) {
+    const long long b = __double_as_longlong(x);
+    const long long be = b >> 52; /* biased exponent of a positive number; <= 0 for x <= 0 */
+    if (be <= 0 || be >= 2047) return log(x);
+    const int k = (int)((((b >> 44) & 0xFF) + 1) >> 1);
+    const double m = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    const double c = __longlong_as_double(0x3FF0000000000000LL + ((long long)k << 45));
+    const double r = (m - c) * qmc_logtab.inv_c[k];
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(q, r, 1.0 / 5.0);
+    q = fma(q, r, -1.0 / 4.0);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double p = fma(r * r, q, r);
+    const double e = (double)(int)(be - 1023);
+    const double LN2 = 0.6931471805599453, LN2_LO = 2.3190468138462996e-17; /* ln 2 = LN2 + LN2_LO */
+    return fma(e, LN2, qmc_logtab.log_c[k]) + fma(e, LN2_LO, p);
+}
+
 /* principal log */
-DEV cd clog_p(cd z) { return cd{0.5 * log(fma(z.x, z.x, z.y * z.y)), atan2(z.y, z.x)}; }
+DEV cd clog_p(cd z) { return cd{0.5 * qlog(fma(z.x, z.x, z.y * z.y)), atan2(z.y, z.x)}; }
 /* log(F - i0): a negative real F lies at arg -pi */
 DEV cd clog_mi0(cd z) {
     double arg = (z.y == 0.0) ? (z.x < 0.0 ? -QMC_PI : 0.0) : atan2(z.y, z.x);
-    return cd{0.5 * log(fma(z.x, z.x, z.y * z.y)), arg};
+    return cd{0.5 * qlog(fma(z.x, z.x, z.y * z.y)), arg};
 }
 
 /* ------------------------------------------------------------------ periodising transform (Eq. 21, order r) */
@@ -279,7 +319,7 @@ DEV void eval_G(const PackedSector &s, const Pol &P, const double *tt, const dou
         X = mk(0.0, 0.0);
         if (MAXM > 0 && M > 0) {
             /* eU1 log U - eF1 log F as one logarithm: both are real and positive on this path */
-            double x = log(ipow(U, ex.eU1) * ipow(F, -ex.eF1));
+            double x = qlog(ipow(U, ex.eU1) * ipow(F, -ex.eF1));
 #pragma unroll
             for (int j = 0; j < S; ++j)
                 if (s.A[j] != -1 && s.B[j] != 0) x = fma((double)s.B[j], Lt[j], x);
@@ -370,7 +410,7 @@ DEV void point_integrand(const PackedSector &s, const Pol &P, const double *x, i
     if (MAXM > 0 && M > 0) {
 #pragma unroll
         for (int j = 0; j < S; ++j)
-            if (((smask >> j) & 1u) || s.B[j] != 0) Lt[j] = log(t[j]);
+            if (((smask >> j) & 1u) || s.B[j] != 0) Lt[j] = qlog(t[j]);
     }
     unsigned Y = 0;
     do {
@@ -480,6 +520,7 @@ DEV void eval_f64_body(const JobTable &jt) {
     const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     int cur = -1, cur_job = -1;
+    logtab_init(); /* made visible by the __syncthreads() after the first item fetch */
     for (;;) {
         if (threadIdx.x == 0) {
             const long long it = (long long)atomicAdd(jt.counter, 1ull);
@@ -1201,6 +1242,7 @@ DEV void probe_body(const ProbeArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[4][4 * (MAXM + 1)];
     const int psec = a.sector_begin + blockIdx.x;
+    logtab_init();
     /* FP64 record + terms, then the FP32 terms */
     stage_sector(a.packed, a.sectors_off, a.terms_off, psec, smem);
     const PackedSector *gps = reinterpret_cast<const PackedSector *>(a.packed + a.sectors_off) + psec;
@@ -1281,6 +1323,7 @@ __global__ void __launch_bounds__(128) qmc_probe_kernel(ProbeArgs a) {
 template <int S, bool DEF, int MAXM>
 __global__ void __launch_bounds__(256) qmc_points_kernel(PointArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    logtab_init();
     stage_sector(a.packed, a.sectors_off, a.terms_off, a.sector, smem);
     __syncthreads();
     const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
