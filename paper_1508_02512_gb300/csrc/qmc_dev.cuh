@@ -57,25 +57,52 @@ DEV double ipow(double v, int e) {
     for (int i = 0; i < k; ++i) r *= v;
     return e < 0 ? __drcp_rn(r) : r;
 }
-/* ------------------------------------------------------------------ table-driven FP64 logarithm */
-/* Tang's method (P. T. P. Tang, ACM Trans. Math. Softw. 16 (1990) 378): x = 2^e m with m in [1, 2); c = 1 + k/128
-   is the grid point nearest m (k = 0..128); log x = e ln2 + log c + log1p(r) with r = (m - c)/c, |r| <= 2^-8,
-   and log1p(r) from its Taylor series through r^7 (the first omitted term is below 2^-67).  m - c is exact.
-   The table {1/c, log c} is filled once per block (library logarithm) by logtab_init and read from shared
-   memory; zero, negative, subnormal and non-finite arguments go to the library. */
+/* ------------------------------------------------------------------ table-driven FP64 log and atan2 */
+/* Logarithm after Tang (P. T. P. Tang, ACM Trans. Math. Softw. 16 (1990) 378): x = 2^e m with m in [1, 2);
+   c = 1 + k/128 is the grid point nearest m (k = 0..128); log x = e ln2 + log c + log1p(r) with r = (m - c)/c,
+   |r| <= 2^-8, and log1p(r) from its Taylor series through r^7 (the first omitted term is below 2^-67).  m - c
+   is exact.  For k >= 64 the split is recentred on 1, log x = (e + 1) ln2 + log(c/2) + log1p(r), so that
+   arguments just below 1 meet no cancellation between e ln2 and log c.
+   Arctangent by the same table-driven reduction: for 0 <= u = lo/hi <= 1 and the grid point c = k/128 nearest u,
+   atan u = atan c + atan(d) with d = (u - c)/(1 + u c) = (lo - c hi)/(hi + c lo), |d| <= 2^-8 + 2^-20, and atan d
+   from its Taylor series through d^7 (omitted term below 2^-77); k comes from an FP32 estimate of u, which only
+   has to land on the nearest or a neighbouring grid point.  Octants follow from the signs and the swap.
+   The tables {1/c, log c} and {k/128, atan(k/128)} are filled once per block (library functions) by
+   logtab_init and read from shared memory; arguments outside the fast paths go to the library. */
 struct LogTable {
     double inv_c[129];
     double log_c[129];
+    double grid[129];
+    double atan_c[129];
 };
 static __shared__ LogTable qmc_logtab;
 
-/* every thread of the block calls it; a __syncthreads() must follow before the first qlog */
+/* every thread of the block calls it; a __syncthreads() must follow before the first qlog / qatan2 */
 DEV void logtab_init() {
     for (int k = threadIdx.x; k <= 128; k += blockDim.x) {
         const double c = 1.0 + k / 128.0;
         qmc_logtab.inv_c[k] = 1.0 / c;
-        qmc_logtab.log_c[k] = log(c);
+        qmc_logtab.log_c[k] = k < 64 ? log(c) : log(0.5 * c);
+        qmc_logtab.grid[k] = k / 128.0;
+        qmc_logtab.atan_c[k] = atan(k / 128.0);
     }
+}
+
+DEV double qatan2(double y, double x) {
+    const double a = fabs(x), b = fabs(y);
+    const bool swap = b > a;
+    const double hi = swap ? b : a, lo = swap ? a : b;
+    if (!(hi > 1e-30 && hi < 1e30 && lo <= hi)) return atan2(y, x); /* zero, tiny, huge or not a number */
+    const int k = min(max(__float2int_rn(128.f * __fdividef((float)lo, (float)hi)), 0), 128);
+    const double c = qmc_logtab.grid[k];
+    const double d = fma(-c, hi, lo) * __drcp_rn(fma(c, lo, hi));
+    const double d2 = d * d;
+    double q = fma(d2, -1.0 / 7.0, 1.0 / 5.0);
+    q = fma(q, d2, -1.0 / 3.0);
+    double th = qmc_logtab.atan_c[k] + fma(d * d2, q, d);
+    if (swap) th = 0.5 * QMC_PI - th;
+    if (x < 0.0) th = QMC_PI - th;
+    return copysign(th, y);
 }
 
 DEV double qlog(double x) {
@@ -92,16 +119,16 @@ DEV double qlog(double x) {
     q = fma(q, r, 1.0 / 3.0);
     q = fma(q, r, -0.5);
     const double p = fma(r * r, q, r);
-    const double e = (double)(int)(be - 1023);
+    const double e = (double)(int)(be - 1023 + (k >= 64));
     const double LN2 = 0.6931471805599453, LN2_LO = 2.3190468138462996e-17; /* ln 2 = LN2 + LN2_LO */
     return fma(e, LN2, qmc_logtab.log_c[k]) + fma(e, LN2_LO, p);
 }
 
 /* principal log */
-DEV cd clog_p(cd z) { return cd{0.5 * qlog(fma(z.x, z.x, z.y * z.y)), atan2(z.y, z.x)}; }
+DEV cd clog_p(cd z) { return cd{0.5 * qlog(fma(z.x, z.x, z.y * z.y)), qatan2(z.y, z.x)}; }
 /* log(F - i0): a negative real F lies at arg -pi */
 DEV cd clog_mi0(cd z) {
-    double arg = (z.y == 0.0) ? (z.x < 0.0 ? -QMC_PI : 0.0) : atan2(z.y, z.x);
+    double arg = (z.y == 0.0) ? (z.x < 0.0 ? -QMC_PI : 0.0) : qatan2(z.y, z.x);
     return cd{0.5 * qlog(fma(z.x, z.x, z.y * z.y)), arg};
 }
 
