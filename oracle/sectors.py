@@ -202,6 +202,8 @@ def _polytope_facets(points):
     from scipy.spatial import ConvexHull
 
     d = len(points[0])
+    if d == 1:
+        return [((-1,), -min(p[0] for p in points)), ((1,), max(p[0] for p in points))]
     hull = ConvexHull(np.array(points, dtype=float))
     out = {}
     for eq in hull.equations:

@@ -316,6 +316,8 @@ def _newton_facets(pts: np.ndarray) -> List[Tuple[Tuple[int, ...], int]]:
     from scipy.spatial import ConvexHull
 
     d = pts.shape[1]
+    if d == 1:  # an interval: its two end points
+        return [((-1,), -int(pts[:, 0].min())), ((1,), int(pts[:, 0].max()))]
     hull = ConvexHull(pts.astype(np.float64))
     facets = {}
     for eq in hull.equations:

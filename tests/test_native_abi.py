@@ -89,6 +89,17 @@ def test_geometric_table_matches_oracle_sector_by_sector(topo, zero, name):
         assert a.D == float(b.D)
 
 
+def test_table_compiler_rejects_alpha_minus_two():
+    """The massless box with a squared propagator has alpha = -2 sectors (Taylor subtraction beyond Eq. 11 with
+    p = 0): the table compiler refuses it under both strategies."""
+    import dataclasses
+    topo = W.box(False)
+    dotted = dataclasses.replace(topo, props=(dataclasses.replace(topo.props[0], nu=2),) + topo.props[1:])
+    for strategy in ("iterated", "geometric"):
+        with pytest.raises(T.TableError, match="alpha <= -2"):
+            T.compile_integral(dotted, ("pp1", "pp2", "pp3", "pp4"), strategy=strategy)
+
+
 def test_symanzik_matches_oracle_for_all_topologies():
     from oracle import feynman as fy
     for topo in (W.bubble(True), W.triangle_massive(), W.box(True), W.double_box_planar(True),

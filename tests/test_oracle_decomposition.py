@@ -143,6 +143,17 @@ def test_geometric_cones_tile_log_space(topo, zero):
         assert inside == 1
 
 
+def test_alpha_below_minus_one_is_rejected_by_both_strategies():
+    """A squared propagator of the massless box gives a sector exponent alpha = -2, which needs Taylor
+    subtraction beyond Eq. (11) with p = 0; both strategies must refuse it rather than mis-integrate."""
+    import dataclasses
+    topo = W.box(False)
+    dotted = dataclasses.replace(topo, props=(dataclasses.replace(topo.props[0], nu=2),) + topo.props[1:])
+    for strategy in ("iterated", "geometric"):
+        with pytest.raises(sd.DecompositionError, match="alpha=-2"):
+            sd.decompose(dotted, MASSLESS_LEGS, strategy)
+
+
 def test_geometric_terminates_on_massless_double_box():
     topo = W.double_box_planar(False)
     with pytest.raises(sd.DecompositionError):

@@ -50,17 +50,19 @@ def close(mean, err, ref, nsig=5.0, floor=1e-12):
     return np.all(np.abs(mean - ref) <= nsig * err + floor * (1 + np.abs(ref)))
 
 
-def test_massless_bubble_all_orders(z4093):
+@pytest.mark.parametrize("strategy", ["iterated", "geometric"])
+def test_massless_bubble_all_orders(z4093, strategy):
     p2 = -2.0
-    mean, err, fails, _ = run(W.bubble(False), dict(pp1=p2), -1, 2, z4093)
+    mean, err, fails, _ = run(W.bubble(False), dict(pp1=p2), -1, 2, z4093, strategy=strategy)
     ref = laurent(lambda e: sp.gamma(e) * sp.gamma(1 - e) ** 2 / sp.gamma(2 - 2 * e) * (-p2) ** (-e), -1, 2)
     assert close(mean, err, ref), (mean, ref, err)
     assert np.max(np.abs(mean - ref)) < 1e-9
 
 
-def test_massive_bubble_above_threshold_deformed(z4093):
+@pytest.mark.parametrize("strategy", ["iterated", "geometric"])
+def test_massive_bubble_above_threshold_deformed(z4093, strategy):
     p2 = 5.0
-    mean, err, fails, prob = run(W.bubble(True), dict(pp1=p2, msq=1.0), -1, 0, z4093, lam=0.5)
+    mean, err, fails, prob = run(W.bubble(True), dict(pp1=p2, msq=1.0), -1, 0, z4093, lam=0.5, strategy=strategy)
     assert all(s.kind == OI.KIND_DEFORM for s in prob.sectors) and fails == 0
     b = cmath.sqrt(1 - 4 / complex(p2, 1e-300))
     ref = np.array([1.0, -GAMMA_E + 2 - b * cmath.log((b + 1) / (b - 1))])
