@@ -229,3 +229,18 @@ PAPER_IB_POINTS = {
 # Table 2's first point as a benchmark workload (the iterated strategy does not terminate for this integral).
 PAPER_IB = Workload("massless_dbox_euclid_table2", double_box_planar(False), PAPER_IB_POINTS["-1,0,0,-1"], -4, 0,
                     16, tuple(range(16, 27)), 3, 0.0, strategy="geometric")
+
+# The paper's one-loop example I_A (Sec. IV, gg -> HH box with four top-quark lines): on-shell gluons
+# p1^2 = p2^2 = 0, Higgs legs p3^2 = p4^2 = M_H^2 (outgoing), t = (p2 - p3)^2 = -6000 GeV^2 fixed and a scan of
+# s = (p1 + p2)^2 from 70000 to 500000 GeV^2.  Its propagators k, k+p1, k+p1-p4, k-p2 are box(True) with the
+# incoming legs (q1, q2, q3, q4) = (p1, -p4, -p3, p2), so box(True)'s s = (q1+q2)^2 is the paper's t, its
+# t = (q2+q3)^2 the paper's s, and pp2 = pp3 = M_H^2.  Units M_t = 1.  The paper's measure d^Dk/(2 pi)^D makes
+# I_A = i/(16 pi^2) I at eps^0 (in GeV^-4 after dividing by M_t^4).
+PAPER_IA_T_GEV2 = -6000.0
+PAPER_IA_S_RANGE_GEV2 = (70000.0, 500000.0)
+
+
+def paper_ia_point(s_gev2: float) -> Dict[str, float]:
+    """Kinematic point of box(True) for the paper's I_A at s = s_gev2 (GeV^2)."""
+    mh2 = (M_H_GEV / M_T_GEV) ** 2
+    return dict(s=PAPER_IA_T_GEV2 / M_T_GEV ** 2, t=s_gev2 / M_T_GEV ** 2, pp2=mh2, pp3=mh2, msq=1.0)
