@@ -218,6 +218,7 @@ def serving_arrivals(n_requests: int, rate_per_s: float = 50.0, seed: int = 0):
     t = rng.uniform(-4.0, -0.5, size=n_requests)
     return [(float(a), int(c), float(x), float(y)) for a, c, x, y in zip(times, cfg, s, t)]
 
+
 # The Euclidean points of the paper's Table 2 (Sec. IV): the massless planar double box with two off-shell legs,
 # s = t = u = -2/3 (so that pp1 + pp2 + pp3 + pp4 = -2), one point per pair of off-shell legs.
 PAPER_IB_POINTS = {
