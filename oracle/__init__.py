@@ -11,7 +11,8 @@ What it computes, following Li, Wang, Yan, Zhao, "Efficient Numerical Evaluation
   feynman.py    U and F from the momentum representation (Sec. II, Eq. 2), exact rational arithmetic;
                  plus the spanning-tree / 2-forest construction from the graph (cited in Sec. II)
   sectors.py    primary sectors (Eqs. 3-6), iterated decomposition until U and F factorise (Eqs. 7-9),
-                 the exponents alpha + beta*eps of Eq. (9); Hepp sectors as a second strategy
+                 the exponents alpha + beta*eps of Eq. (9); the geometric decomposition the paper prefers
+                 (normal fan of the Newton polytope, Sec. II after Eq. 9); Hepp sectors as a third strategy
   prefactor.py  Gamma(N_nu - L D/2)/prod Gamma(nu_j) as a truncated Laurent series in eps (Eq. 2)
   lattice.py    primes, the rank-1 lattice rule (Eq. 17), random shifts (Eqs. 18-20), a plain CBC search
   qmc_oracle.c  the per-point sector integrand: periodising transform (Eq. 21), contour deformation (Eq. 14)
@@ -22,5 +23,6 @@ Pins (tests/test_oracle_*.py): textbook U/F forms and the graph construction; cl
 and massive bubble, the massive triangle and the massless box; direct simplex cubature of the undecomposed
 integrand; the unexpanded subtracted integrand's Laurent coefficients by contour integration in eps;
 exactness of the lattice rule on trigonometric polynomials; brute-force CBC; error-estimator coverage;
-independence of the total from the decomposition strategy and from lambda.
+independence of the total from the decomposition strategy and from lambda; the geometric cones tiling the
+space of log x; and the paper's printed Laurent coefficients of Tables 2 and 3 (tests/golden/).
 """
