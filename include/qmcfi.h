@@ -130,15 +130,17 @@ int qmc_version(void);
 
 /*
  * qmc_prepare -- host only; no CUDA call.
- * Parses and validates a sector table (Sec. II, Eq. 9: per sector the exponents A_j + B_j eps and the
- * polynomials Ut, Ft with coefficients linear in the kinematic invariants), evaluates the coefficients at
+ * Parses and validates a sector table (Sec. II, Eq. 9: per sector the exponents A_j + B_j eps, a constant
+ * Jacobian factor D and the polynomials Ut, Ft with coefficients linear in the kinematic invariants; tables of
+ * the iterated and of the geometric decomposition have the same form), evaluates the coefficients at
  * `invariants` (n_invariants values in the table's invariant order), classifies every sector by the signs of
  * Ft's coefficients (kind 0/1/2), derives for deformed sectors the gradient and Hessian polynomials of Ft that
  * Eq. (14) and its Jacobian need, computes the Gamma prefactor series of Eq. (2), and writes the packed image
  * that the kernels read (relocatable: offsets only; copy it to device memory as is).
  *   order_min..order_max: Laurent orders of the integral the image must serve (order_max - order_min < 8).
  *   packed: output buffer of packed_capacity bytes, or NULL to query info->packed_bytes only.
- * Errors: QMC_ERR_ARG, QMC_ERR_TABLE, QMC_ERR_UNSUPPORTED, QMC_ERR_KINEMATICS, QMC_ERR_MEMORY (capacity).
+ * Errors: QMC_ERR_ARG, QMC_ERR_TABLE, QMC_ERR_UNSUPPORTED (among others: an exponent A_j <= -2, which needs
+ * Taylor subtraction beyond Eq. 11 with p = 0), QMC_ERR_KINEMATICS, QMC_ERR_MEMORY (capacity).
  */
 int qmc_prepare(const void *table, size_t table_bytes, const double *invariants, int32_t n_invariants,
                 int32_t order_min, int32_t order_max, void *packed, size_t packed_capacity, qmc_info *info);
