@@ -392,7 +392,9 @@ int qmc_integrate(qmc_ctx *ctx, int32_t integral_id, const qmc_options *opt, qmc
  * context admits requests while its device-memory budget has room and runs batched rounds: each active request
  * contributes the pass at its current lattice size to shared launches (qmc_eval_batch); requests that arrive
  * meanwhile join at the next round.  A request's result is the same, bit for bit, as qmc_integrate with the same
- * options would give alone.  The paper has no serving loop; this is the library's deployment layer. */
+ * options would give alone.  opt->max_seconds counts from submission: a request whose limit passes while it
+ * is still queued finishes with QMC_ERR_TIMEOUT without running.  The paper has no serving loop; this is the
+ * library's deployment layer. */
 int qmc_submit(qmc_ctx *ctx, int32_t integral_id, const double *invariants, int32_t n_invariants, int32_t order_min,
                int32_t order_max, const qmc_options *opt, int64_t *request_id);
 

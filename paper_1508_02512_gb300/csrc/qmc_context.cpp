@@ -678,7 +678,7 @@ void serve_loop(qmc_ctx *c) {
     Serving *S = c->serving;
     cudaSetDevice(c->device);
     for (;;) {
-        std::vector<std::shared_ptr<Request>> fresh, cancelled;
+        std::vector<std::shared_ptr<Request>> fresh, cancelled, expired;
         /* lock order: the context mutex is never taken while the serving mutex is held */
         size_t in_use;
         {
@@ -711,6 +711,16 @@ void serve_loop(qmc_ctx *c) {
                     S->stats.completed += 1;
                     continue;
                 }
+                if (r->opt.max_seconds > 0 &&
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - r->t_submit).count() >
+                        r->opt.max_seconds) {
+                    /* its deadline passed in the queue: it leaves without work (finished below, outside this
+                       lock), which keeps an overloaded loop's device time for requests that can still finish */
+                    S->queue.pop_front();
+                    r->t_admit = std::chrono::steady_clock::now();
+                    expired.push_back(r);
+                    continue;
+                }
                 const size_t est = 2 * r->table.size() + ((size_t)8 << 20);
                 if (!S->active.empty() && in_use + est > c->budget) break;
                 S->queue.pop_front();
@@ -723,6 +733,7 @@ void serve_loop(qmc_ctx *c) {
         {
             std::lock_guard<std::mutex> g(c->mu);
             for (auto &r : cancelled) finish(S, c, *r, QMC_ERR_CANCELLED);
+            for (auto &r : expired) finish(S, c, *r, QMC_ERR_TIMEOUT);
             for (auto &r : fresh) {
                 r->t_admit = std::chrono::steady_clock::now();
                 const int rc = admit(S, c, *r);

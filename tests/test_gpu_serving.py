@@ -136,6 +136,19 @@ def test_serving_cancel():
     ctx.close()
 
 
+def test_serving_deadline_passed_in_queue_finishes_without_work():
+    """max_seconds counts from submission: a request whose limit has passed by the time the loop would admit
+    it leaves with QMC_ERR_TIMEOUT and no evaluations; a request with room to run is unaffected."""
+    ctx = api.Context(0, 1 << 30)
+    iid = ctx.load_sectors(table(W.CONFIG1))
+    late = ctx.submit(iid, point(W.CONFIG1), 0, 0, rel_tol=1e-3, n_shifts=8, seed=3, max_seconds=1e-9)
+    ok = ctx.submit(iid, point(W.CONFIG1), 0, 0, rel_tol=1e-3, n_shifts=8, seed=3, max_seconds=60.0)
+    r = ctx.wait(late, timeout=60)
+    assert r.status == N.QMC_ERR_TIMEOUT and r.evals == 0, (r.status, r.evals)
+    assert ctx.wait(ok, timeout=60).status == 0
+    ctx.close()
+
+
 def test_serving_admission_by_memory():
     """A budget that holds only a few requests at a time: the rest wait in the queue, all complete, and the
     context never holds more device memory than its budget."""
