@@ -42,7 +42,7 @@
 
 namespace {
 
-#define QMC_JIT_GENERATOR_VERSION 3u
+#define QMC_JIT_GENERATOR_VERSION 4u
 #define QMC_GEN_INLINE_TERMS 2048 /* families with more terms get out-of-line sector functions */
 
 const PackedHeader *hdr(const void *p) {
@@ -341,9 +341,13 @@ std::string generate(const PackedHeader *h, const Lang &L) {
         if (h->class_end[c] <= h->class_begin[c]) continue;
         const char *def = c == 1 ? "true" : "false";
         const int mm = maxm_of(h, c);
-        /* FP32, 5- and 6-dimensional deformed sectors: 3 blocks of 128 threads per SM (<= 170 registers, no
-           spills) measured 13 % faster than the register-unbounded build (2 blocks); the rest keep 256 */
-        const std::string lb = (!L.f64 && qmc_gen_max_block(S) == 128) ? "__launch_bounds__(128, 3)" : "__launch_bounds__(256)";
+        /* FP32, 5- and 6-dimensional sectors, 128-thread blocks: the deformed class at 3 blocks per SM (<= 170
+           registers, no spills; 13 % faster than 2 blocks, 3 % faster than 4, which spills); the undeformed class
+           at 4 blocks per SM (17 % faster than 3 on the four-pole sectors of the massless double box, which are
+           latency-bound); the rest keep 256 */
+        const std::string lb = (!L.f64 && qmc_gen_max_block(S) == 128)
+                                   ? (c == 1 ? "__launch_bounds__(128, 3)" : "__launch_bounds__(128, 4)")
+                                   : "__launch_bounds__(256)";
         std::snprintf(b, sizeof(b),
                       "extern \"C\" __global__ void %s %s_eval_c%d(const __grid_constant__ JobTable jt) {\n"
                       "    %s<%d, %s, %d, %s>(jt);\n}\n",
