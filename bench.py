@@ -53,8 +53,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # DRAM bytes per launch of the FP64 evaluation kernel (qd_eval_c1) of the bench step, from one single-pass ncu
 # capture of that launch (profiles/qmc_eval_kernel_massive_box.md); valid while the device code and the
 # generator hash to KERNEL_HASH, null otherwise
-TRAFFIC_BYTES = 713216 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
-KERNEL_HASH = "340623252b0d1b1a"
+TRAFFIC_BYTES = 767488 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
+KERNEL_HASH = "d66e517bc472468f"
 
 
 INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3,
