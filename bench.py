@@ -11,12 +11,16 @@ Output: one JSON line (rank 0).  `value` = evaluations/s of the whole job with t
 already resident on the device; `e2e` = the same metric through qmc_eval_sums_host (host buffers, copies inside
 the timed region); `roofline` = algorithmic FP64 throughput of the evaluation kernel against the FP64 peak
 derived from the SM count, FP64 units and clock; `cpu_baseline` = the oracle (plain C, all host cores) on a
-bounded sample of the same workload; `time_to_1e-3` = qmc_integrate to 1e-3 relative error over 32 seeds.
+bounded sample of the same workload; `time_to_1e-3` = qmc_integrate to 1e-3 relative error over 32 seeds;
+`paper_ia_scan` and `paper_table2` = the paper's own workloads (its one-loop s-scan of 1000 points through the
+serving loop, and the three points of its Table 2) with its printed timings beside them.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --integral planar_dbox|nonplanar_dbox [--log2n 18]   the same measurement on a two-loop
-        double box (46/48 six-dimensional sectors, eps^-2..eps^0, lambda adapted per sector beforehand)
+    python bench.py --integral planar_dbox|nonplanar_dbox|massless_dbox_table2 [--log2n 18]   the same
+        measurement on a two-loop double box (46/48/143 six-dimensional sectors, eps^-2 or eps^-4 ..eps^0,
+        lambda adapted per sector beforehand)
     python bench.py --serving N   the serving workload: N Poisson arrivals of random integrals
+    python bench.py --paper-ia-scan N | --paper-table2   only those workloads
 Multi-GPU (torchrun, one rank per GPU): every rank integrates its own replica with its own shifts (weak
 scaling, no data-path collective); the barrier and max-over-ranks timing use torch.distributed.
 """
@@ -436,6 +440,15 @@ def main_ours(args):
         extras["time_to_1e-3_fp64_per_sector"] = time_to_accuracy(api, blob, cfg, local, stream, seeds)
         extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, seeds,
                                                          precision=N.QMC_PREC_MIXED)
+        if cfg is W.CONFIG1:
+            # the paper's own workloads beside the headline: its one-loop scan through the serving loop and its
+            # Table 2 points (each guarded, so that a failure there cannot cost the line)
+            for key, fn in (("paper_ia_scan", lambda: paper_ia_scan(1000, device=local)),
+                            ("paper_table2", lambda: paper_table2(seeds=4, device=local))):
+                try:
+                    extras[key] = fn()
+                except Exception as exc:  # noqa: BLE001
+                    extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
