@@ -57,7 +57,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # DRAM bytes per launch of the FP64 evaluation kernel (qd_eval_c1) of the bench step, from one single-pass ncu
 # capture of that launch (profiles/qmc_eval_kernel_massive_box.md); valid while the device code and the
 # generator hash to KERNEL_HASH, null otherwise
-TRAFFIC_BYTES = 767488 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
+TRAFFIC_BYTES = 771584 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
 KERNEL_HASH = "c71d0d47b057653d"
 
 
