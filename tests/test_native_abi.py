@@ -72,7 +72,7 @@ def test_table_compiler_matches_oracle_decomposition(cfg):
     assert mine == ref
 
 
-GEOMETRIC_CASES = [(c.topology, T.zero_invariants_of(c.topology, c.point), c.name) for c in W.CONFIGS[:3]] + [
+GEOMETRIC_CASES = [(c.topology, T.zero_invariants_of(c.topology, c.point), c.name) for c in W.CONFIGS] + [
     (W.double_box_planar(False), T.zero_invariants_of(W.double_box_planar(False), W.PAPER_IB_POINTS["0,-1,0,-1"]),
      "massless_dbox_table2")]
 
