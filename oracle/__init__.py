@@ -18,11 +18,15 @@ What it computes, following Li, Wang, Yan, Zhao, "Efficient Numerical Evaluation
   qmc_oracle.c  the per-point sector integrand: periodising transform (Eq. 21), contour deformation (Eq. 14)
                  with its Jacobian, endpoint subtraction (Eqs. 10-12), eps expansion; and plain lattice sums
   integrate.py  sector sums -> per-shift estimates Q_k -> mean and error (Eqs. 16, 18-20)
+  taylor.py     Eq. (11) for endpoint exponents alpha <= -1 of any order (undeformed sectors, numpy, slow):
+                 the groundwork for squared propagators, which the GPU path does not take yet
 
 Pins (tests/test_oracle_*.py): textbook U/F forms and the graph construction; closed forms of the massless
 and massive bubble, the massive triangle and the massless box; direct simplex cubature of the undecomposed
 integrand; the unexpanded subtracted integrand's Laurent coefficients by contour integration in eps;
 exactness of the lattice rule on trigonometric polynomials; brute-force CBC; error-estimator coverage;
 independence of the total from the decomposition strategy and from lambda; the geometric cones tiling the
-space of log x; and the paper's printed Laurent coefficients of Tables 2 and 3 (tests/golden/).
+space of log x; the paper's printed Laurent coefficients of Tables 2 and 3 (tests/golden/); and, for taylor.py,
+the closed forms of massless bubbles with raised powers (alpha = -2, -3) at every order, the C oracle on
+alpha = -1 sectors, and strategy independence of the massless box with a squared propagator.
 """

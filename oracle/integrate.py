@@ -36,7 +36,8 @@ class NumSector:
 
     @property
     def sigma(self) -> int:
-        return int(np.sum(self.A == -1))
+        """Variables with an endpoint singularity (alpha <= -1; the C integrand takes alpha = -1 only)."""
+        return int(np.sum(self.A <= -1))
 
 
 def numeric_sectors(sectors: List[sd.Sector], point: Dict[str, float]) -> List[NumSector]:

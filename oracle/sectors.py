@@ -336,8 +336,9 @@ def hepp_sectors(U, F, nu: List[int]):
     return secs
 
 
-def decompose(topo, zero_invariants=(), strategy="iterated", max_depth=40):
-    """Leaf sectors of `topo` for the kinematic class in which `zero_invariants` vanish."""
+def decompose(topo, zero_invariants=(), strategy="iterated", max_depth=40, allow_higher_poles=False):
+    """Leaf sectors of `topo` for the kinematic class in which `zero_invariants` vanish.  Exponents alpha <= -2
+    are refused unless allow_higher_poles (for the Taylor-subtraction oracle, oracle.taylor)."""
     U, F = fy.symanzik_momentum(topo)
     zero = set(zero_invariants)
     U = drop_zero_invariants(U, zero)
@@ -358,9 +359,9 @@ def decompose(topo, zero_invariants=(), strategy="iterated", max_depth=40):
         _iterate(sec, eU, eF, 0, max_depth, leaves)
     for sec in leaves:
         for a, b in zip(sec.A, sec.B):
-            if a <= -2:
+            if a <= -2 and not allow_higher_poles:
                 raise DecompositionError(f"exponent alpha={a} <= -2 needs higher Taylor subtraction")
-            if a == -1 and b == 0:
+            if a <= -1 and b == 0:
                 raise DecompositionError("unregulated endpoint singularity (alpha=-1, beta=0)")
     return leaves
 
