@@ -370,9 +370,11 @@ def _geometric_leaves(U: Poly, F: Poly, nu: Sequence[int], eU, eF) -> List[Secto
     return out
 
 
-def decompose(topo, zero_invariants: Sequence[str] = (), max_depth: int = 40,
-              strategy: str = "iterated") -> Tuple[List[SectorRecord], dict]:
-    """Leaf sectors of the iterated (default) or geometric decomposition and the integral's metadata."""
+def decompose(topo, zero_invariants: Sequence[str] = (), max_depth: int = 40, strategy: str = "iterated",
+              allow_higher_poles: bool = False) -> Tuple[List[SectorRecord], dict]:
+    """Leaf sectors of the iterated (default) or geometric decomposition and the integral's metadata.  Exponents
+    alpha <= -2 (Taylor subtraction beyond Eq. 11 with p = 0) are refused unless allow_higher_poles; the binary
+    table carries them, and qmc_prepare answers QMC_ERR_UNSUPPORTED."""
     U, F = symanzik(topo)
     K = len(topo.invariants)
     for name in zero_invariants:
@@ -400,9 +402,9 @@ def decompose(topo, zero_invariants: Sequence[str] = (), max_depth: int = 40,
         A0 = [nu[j] - 1 for j in keep]
         leaves.extend(_leaves(Ul, Fl, A0, [0] * (n - 1), eU, eF, max_depth))
     for s in leaves:
-        if np.any(s.A <= -2):
+        if np.any(s.A <= -2) and not allow_higher_poles:
             raise TableError("exponent alpha <= -2 needs higher-order subtraction (not supported)")
-        if np.any((s.A == -1) & (s.B == 0)):
+        if np.any((s.A <= -1) & (s.B == 0)):
             raise TableError("unregulated endpoint singularity (alpha = -1, beta = 0)")
     meta = dict(dim=n - 1, loops=L, nu=nu, n_nu=n_nu, eU=eU, eF=eF, invariants=tuple(topo.invariants))
     return leaves, meta
@@ -470,9 +472,10 @@ def read_table(blob: bytes):
     return meta, leaves
 
 
-def compile_integral(topo, zero_invariants: Sequence[str] = (), strategy: str = "iterated") -> bytes:
+def compile_integral(topo, zero_invariants: Sequence[str] = (), strategy: str = "iterated",
+                     allow_higher_poles: bool = False) -> bytes:
     """Sector table (bytes) of `topo` for the kinematic class in which `zero_invariants` vanish."""
-    leaves, meta = decompose(topo, zero_invariants, strategy=strategy)
+    leaves, meta = decompose(topo, zero_invariants, strategy=strategy, allow_higher_poles=allow_higher_poles)
     return write_table(leaves, meta)
 
 

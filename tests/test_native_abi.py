@@ -100,6 +100,23 @@ def test_table_compiler_rejects_alpha_minus_two():
             T.compile_integral(dotted, ("pp1", "pp2", "pp3", "pp4"), strategy=strategy)
 
 
+def test_squared_propagator_tables_match_the_oracle_and_prepare_refuses_them():
+    """With allow_higher_poles the table compiler writes the alpha = -2 sectors of the squared-propagator box,
+    sector for sector equal to the oracle's (which integrates them with oracle.taylor); qmc_prepare refuses
+    them until the kernels take Taylor subtraction beyond p = 0."""
+    import dataclasses
+    topo = W.box(False)
+    dotted = dataclasses.replace(topo, props=(dataclasses.replace(topo.props[0], nu=2),) + topo.props[1:])
+    zero = ("pp1", "pp2", "pp3", "pp4")
+    for strategy in ("iterated", "geometric"):
+        blob = T.compile_integral(dotted, zero, strategy=strategy, allow_higher_poles=True)
+        meta, leaves = T.read_table(blob)
+        ref = OS.decompose(dotted, zero, strategy, allow_higher_poles=True)
+        assert canon_product(leaves, meta) == OS.canonical(ref)
+        assert min(int(s.A.min()) for s in leaves) == -2
+        assert _prep_status(blob, W.kinematics(dotted, s=-3.0, t=-2.0)) == N.QMC_ERR_UNSUPPORTED
+
+
 def test_symanzik_matches_oracle_for_all_topologies():
     from oracle import feynman as fy
     for topo in (W.bubble(True), W.triangle_massive(), W.box(True), W.double_box_planar(True),
