@@ -1,25 +1,34 @@
 #!/usr/bin/env python
-"""Benchmark of the QMC sector-integration hot path on GB300: integrand evaluations per second.
+"""Benchmark of the QMC sector-integration hot path on GB300: integrand evaluations per second and
+time-to-1e-3 relative error, mixed precision beside FP64.
 
-A step is one pass of the whole hot path over the massive one-loop box in the physical region (4 sectors,
-contour deformation lambda = 0.5, s = 5, t = -1.5, m = 1, massless legs): every sector x 16 random shifts x
-every point of the rank-1 lattice of size n = 16777213 (largest prime below 2^24), Korobov transform r = 3,
-FP64 -- 1.07e9 integrand evaluations, reduced per (sector, shift) -- through qmc_eval_partials +
-qmc_reduce_partials (the two launches of qmc_eval_sums).
+Default workload: the two-loop non-planar double box in the physical region (7 propagators, m^2 = 1 on four
+lines, massless legs, s = 6, t = -2, u = -4; eps^-2..eps^0; 48 six-dimensional sectors of the iterated
+decomposition, every one contour-deformed with lambda = 0.5, halved per sector where the sign check of Eq. 14
+fails).  A step is one pass of the whole hot path over it: every sector x 16 random shifts x every point of the
+rank-1 lattice of size n = 1048573 (largest prime below 2^20), Korobov transform r = 3 -- 8.05e8 integrand
+evaluations, reduced per (sector, shift) -- in mixed precision as the library runs it: the FP32/FP64 probe
+(qmc_probe_precision, 4096 points per sector) keeps a sector in FP32 unless its FP32 error exceeds 1e-4 of its
+magnitude, and the sectors it flags run in FP64 in the same step.
 
-Output: one JSON line (rank 0).  `value` = evaluations/s of the whole job with the table, shifts and lambda
-already resident on the device; `e2e` = the same metric through qmc_eval_sums_host (host buffers, copies inside
-the timed region); `roofline` = algorithmic FP64 throughput of the evaluation kernel against the FP64 peak
-derived from the SM count, FP64 units and clock; `cpu_baseline` = the oracle (plain C, all host cores) on a
-bounded sample of the same workload; `time_to_1e-3` = qmc_integrate to 1e-3 relative error over 32 seeds;
-`paper_ia_scan` and `paper_table2` = the paper's own workloads (its one-loop s-scan of 1000 points through the
-serving loop, and the three points of its Table 2) with its printed timings beside them.
+Output: one JSON line (rank 0).
+  value      evaluations/s of the mixed step, with the table, shifts and lambda already resident on the device
+  e2e        the same metric through qmc_eval_sums_host (host buffers; copies inside the timed region)
+  roofline   algorithmic FP32 throughput of the FP32 evaluation kernel (flop counted per sector from the tables by
+             the library, times the evaluations of one launch, over its CUDA-event time) against the FP32 peak
+             derived from the SM count, FP32 lanes and clock
+  fp64       the same pass in FP64 alone (n = 262139), with its roofline against the derived FP64 peak
+  mixed_error_vs_fp64   per order, the mixed pass's deviation from the FP64 pass on identical points
+  time_to_1e-3          qmc_integrate to 1e-3 relative error over 32 seeds: mixed with per-sector lattices (the
+                        library's default), FP64 with per-sector lattices, and the plain FP64 per-integral path
+                        (all sectors on one lattice ladder)
+  serving    a bounded sample of the serving workload (Poisson arrivals at 50/s of random integrals)
+  paper_table2, paper_ia_scan   the paper's own workloads with its printed timings beside them
+  cpu_baseline   the oracle (plain C, all host cores) on a bounded sample of the same workload
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --integral planar_dbox|nonplanar_dbox|massless_dbox_table2 [--log2n 18]   the same
-        measurement on a two-loop double box (46/48/143 six-dimensional sectors, eps^-2 or eps^-4 ..eps^0,
-        lambda adapted per sector beforehand)
-    python bench.py --serving N   the serving workload: N Poisson arrivals of random integrals
+    python bench.py --integral massive_box|planar_dbox|nonplanar_dbox|massless_dbox_table2 [--log2n 20]
+    python bench.py --serving N [--serving-baseline]   the serving workload: N Poisson arrivals
     python bench.py --paper-ia-scan N | --paper-table2   only those workloads
 Multi-GPU (torchrun, one rank per GPU): every rank integrates its own replica with its own shifts (weak
 scaling, no data-path collective); the barrier and max-over-ranks timing use torch.distributed.
@@ -44,21 +53,23 @@ import numpy as np  # noqa: E402
 
 import workloads as W  # noqa: E402
 
-LOG2_N = 24
 N_PREC_FP64 = 0
 N_PREC_MIXED = 1
 N_SHIFTS = 16
 LAMBDA = 0.5
+REL_TOL = 1e-3
+FP32_BUDGET = 0.1  # the library's default: a sector stays in FP32 while its probe error <= 0.1 * rel_tol
 METRIC = "integrand evals/s"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock per SM (4 flop) x 2070 MHz maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 4 * 2070e6 / 1e12
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
-# DRAM bytes per launch of the FP64 evaluation kernel (qd_eval_c1) of the bench step, from one single-pass ncu
-# capture of that launch (profiles/qmc_eval_kernel_massive_box.md); valid while the device code and the
-# generator hash to KERNEL_HASH, null otherwise
-TRAFFIC_BYTES = 771584 + 0  # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch
-KERNEL_HASH = "c71d0d47b057653d"
+# DRAM bytes per launch of the FP32 evaluation kernel of the default step (the generated qg_eval_c1 of the
+# non-planar family at n = 1048573, 16 shifts), dram__bytes_read.sum + dram__bytes_write.sum from one
+# single-pass ncu capture of a full-size launch; valid while the device code and the generator hash to
+# KERNEL_HASH, null otherwise
+TRAFFIC_BYTES = None
+KERNEL_HASH = ""
 
 
 INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3,
@@ -80,15 +91,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip time-to-accuracy and CPU baseline")
-    ap.add_argument("--integral", choices=sorted(INTEGRALS), default="massive_box",
-                    help="integral of the timed pass (default: the massive one-loop box)")
+    ap.add_argument("--integral", choices=sorted(INTEGRALS), default="nonplanar_dbox",
+                    help="integral of the timed pass (default: the non-planar two-loop double box)")
     ap.add_argument("--evaluator", choices=["auto", "table", "generated"], default="auto",
                     help="polynomial evaluator of the FP64 pass (the mixed pass always uses the generated one)")
-    ap.add_argument("--log2n", type=int, default=0, help="lattice size: largest prime below 2^log2n (default "
-                                                         "24 one-loop, 18 two-loop)")
+    ap.add_argument("--log2n", type=int, default=0, help="lattice size of the timed step: largest prime below "
+                                                         "2^log2n (default 24 one-loop, 20 two-loop)")
+    ap.add_argument("--tta-seeds", type=int, default=32, help="seeds per path of the time-to-1e-3 figures")
+    ap.add_argument("--serving-sample", type=int, default=48,
+                    help="requests of the bounded serving sample in the default run (0 = none)")
     ap.add_argument("--profile-pass", action="store_true",
                     help="run two passes of the same integral at n = 1048573 and exit (small case for ncu)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
+    ap.add_argument("--profile-log2n", type=int, default=0,
+                    help="lattice size of --profile-pass (default 2^20 one-loop, 2^16 two-loop)")
     ap.add_argument("--serving", type=int, default=0,
                     help="run only the serving workload with this many requests and print its JSON line")
     ap.add_argument("--paper-ia-scan", type=int, default=0,
@@ -102,16 +118,21 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(cfg, n, ns, lam_desc):
+def workload_config(cfg, n, ns, lam_desc, precision="mixed"):
     if cfg is W.CONFIG1:
         what = f"massive one-loop box, physical s=5 t=-1.5 m^2=1, lambda={lam_desc}, {ns} sectors"
     elif cfg is W.PAPER_IB:
         what = (f"massless planar double box (the paper's Table 2, legs p1^2 = p4^2 = -1), Euclidean s=t=u=-2/3, "
                 f"eps^-4..eps^0, geometric decomposition, {ns} six-dimensional sectors")
+    elif cfg is W.CONFIG2:
+        what = (f"planar two-loop double box, physical s=6 t=-2, m^2=1 on four lines, massless legs, "
+                f"eps^-2..eps^0, lambda={lam_desc}, {ns} six-dimensional sectors")
     else:
-        what = (f"{'planar' if cfg is W.CONFIG2 else 'non-planar'} two-loop double box, physical s=6 t=-2, "
-                f"m^2=1 on four lines, eps^-2..eps^0, lambda={lam_desc}, {ns} six-dimensional sectors")
-    return {"workload": f"{what} x {N_SHIFTS} shifts x n={n} rank-1 lattice, Korobov r=3",
+        what = (f"non-planar two-loop double box, physical s=6 t=-2 u=-4, m^2=1 on four lines, massless legs, "
+                f"eps^-2..eps^0, lambda={lam_desc}, {ns} six-dimensional sectors")
+    prec = ("mixed precision (FP32 evaluation of the sectors the FP32/FP64 probe keeps, FP64 for the others; FP64 "
+            "lattice arithmetic and accumulation)" if precision == "mixed" else "FP64")
+    return {"workload": f"{what} x {N_SHIFTS} shifts x n={n} rank-1 lattice, Korobov r=3, {prec}",
             "integral": cfg.name, "sectors": ns, "shifts": N_SHIFTS, "lattice_n": n,
             "l2": "inputs (the sector table, shifts) live in shared memory; a 256 MiB buffer is written between "
                   "steps to flush L2"}
@@ -201,11 +222,11 @@ def korobov_vector(n, a=76):
 
 def cpu_baseline(cfg=None, n_log2=0):
     """The oracle as it stands (plain C, OpenMP over all host cores) on a bounded sample of the workload:
-    n = largest prime below 2^18 for the one-loop box, 2^12 for a double box (about 10-20 s of CPU work)."""
+    n = largest prime below 2^18 for the one-loop box, 2^14 for a double box (about 10-20 s of CPU work)."""
     from oracle import integrate as OI
     from oracle import lattice as OL
-    cfg = cfg or W.CONFIG1
-    n_log2 = n_log2 or (18 if cfg.topology.loops == 1 else 12)
+    cfg = cfg or W.CONFIG3
+    n_log2 = n_log2 or (18 if cfg.topology.loops == 1 else 14)
     prob = OI.make_problem(cfg.topology, {**cfg.point}, cfg.order_min, cfg.order_max, cfg.strategy)
     n = OL.prime_below(1 << n_log2)
     z = korobov_vector(n)
@@ -221,6 +242,8 @@ def cpu_baseline(cfg=None, n_log2=0):
 
 
 def main_reference(args):
+    """The oracle on the same integral as our arm (default: the non-planar double box), each step a bounded
+    sample: n = largest prime below 2^16 (one-loop) or 2^12 (two-loop), 16 shifts, all sectors."""
     world, rank, local, dist = dist_setup(args)
     if rank != 0:  # the oracle runs once, on rank 0; the other ranks leave without work
         if dist:
@@ -228,25 +251,29 @@ def main_reference(args):
         return
     from oracle import integrate as OI
     from oracle import lattice as OL
-    cfg = W.CONFIG1
-    prob = OI.make_problem(cfg.topology, {**cfg.point}, 0, 0)
-    n = OL.prime_below(1 << 16)
+    cfg = INTEGRALS[args.integral]
+    prob = OI.make_problem(cfg.topology, {**cfg.point}, cfg.order_min, cfg.order_max, cfg.strategy)
+    lg = 16 if cfg.topology.loops == 1 else 12
+    n = OL.prime_below(1 << lg)
     z = korobov_vector(n)
     shifts = W.shifts(12345, N_SHIFTS)
     cores = os.cpu_count() or 1
+    lam = LAMBDA if cfg.lam > 0 else 0.0
     for _ in range(args.warmup):
-        OI.integrate(prob, n, z, shifts, LAMBDA, 3, nthreads=cores)
+        OI.integrate(prob, n, z, shifts, lam, 3, nthreads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        OI.integrate(prob, n, z, shifts, LAMBDA, 3, nthreads=cores)
+        OI.integrate(prob, n, z, shifts, lam, 3, nthreads=cores)
     dt = time.perf_counter() - t0
-    evals = len(prob.sectors) * N_SHIFTS * n
+    ns = len(prob.sectors)
+    evals = ns * N_SHIFTS * n
     v = evals * args.steps / dt
-    sample = f"each step: massive box, n={n} (largest prime < 2^16), {N_SHIFTS} shifts, 4 sectors = {evals} evals"
+    sample = (f"each step: {cfg.name}, n={n} (largest prime < 2^{lg}), {N_SHIFTS} shifts, {ns} sectors = {evals} "
+              f"evals, FP64")
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": workload_config(W.CONFIG1, n, len(prob.sectors), f"{LAMBDA}"),
+                      "data": "synthetic", "config": workload_config(cfg, n, ns, f"{lam}", "fp64"),
                       "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
                                        "sample": sample},
                       "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -254,7 +281,26 @@ def main_reference(args):
         dist.destroy_process_group()
 
 
+def probe_flags(L, N, prep, di, p_mixed, sh, lam, budget):
+    """Per-sector precision of a mixed pass, decided as qmc_integrate decides it: the FP32/FP64 probe
+    (qmc_probe_precision, 4096 strided points of the first shift) sends a sector to FP64 when, in any slot, the
+    summed |v32 - v64| exceeds budget * sum |v64|.  Returns (fp32 mask, probe ratios), table order."""
+    import ctypes
+    import torch
+    ns, slots = prep.info.n_sectors, prep.info.n_slots
+    out = torch.zeros((ns, slots, 4), dtype=torch.float64, device=sh.device)
+    N.check(L.qmc_probe_precision(prep.packed, di.dpacked.data_ptr(), ctypes.byref(p_mixed), sh.data_ptr(),
+                                  lam.data_ptr(), 4096, out.data_ptr(), None), "qmc_probe_precision")
+    torch.cuda.synchronize()
+    pr = out.cpu().numpy()
+    ratio = pr[:, :, 1] / np.maximum(pr[:, :, 0], 1e-300)
+    bad = np.any(pr[:, :, 1] > budget * pr[:, :, 0], axis=1) | ~np.all(np.isfinite(pr[:, :, 1]), axis=1)
+    return (~bad).astype(np.int32), ratio.max(axis=1)
+
+
 def main_ours(args):
+    import ctypes
+
     import torch
 
     from paper_1508_02512_gb300 import _native as N
@@ -268,156 +314,198 @@ def main_ours(args):
     blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point), strategy=cfg.strategy)
     prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
     di = api.DeviceIntegral(prep, dev_name)
-    lat = dict(api.builtin_lattices())
-    log2n = args.log2n or (LOG2_N if cfg.topology.loops == 1 else 18)
-    n = max(k for k in lat if k < (1 << log2n))
-    z = lat[n]
-    shifts = W.shifts(cfg.seed + rank, N_SHIFTS)
-    evaluator = {"auto": N.QMC_EVAL_AUTO, "table": N.QMC_EVAL_TABLE, "generated": N.QMC_EVAL_GENERATED}[args.evaluator]
-    if evaluator != N.QMC_EVAL_TABLE:
-        api.gen_compile(prep, precision=N.QMC_PREC_FP64)  # generated FP64 evaluator compiled before any timing
-    p = api.make_pass(n, z, N_SHIFTS, 3, evaluator=evaluator)
+    L = N.lib()
     ns = prep.info.n_sectors
+    lat = dict(api.builtin_lattices())
+    two_loop = cfg.topology.loops == 2
+    log2n = args.log2n or (20 if two_loop else 24)
+    n = max(k for k in lat if k < (1 << log2n))
+    n64 = max(k for k in lat if k < (1 << (18 if two_loop else 24)))  # lattice of the FP64-alone pass
+    evaluator = {"auto": N.QMC_EVAL_AUTO, "table": N.QMC_EVAL_TABLE, "generated": N.QMC_EVAL_GENERATED}[args.evaluator]
+    # generated evaluators (FP32 and FP64) compiled before any timing
+    compile_ms = {"fp32": api.gen_compile(prep, precision=N.QMC_PREC_MIXED).compile_ms}
+    if evaluator != N.QMC_EVAL_TABLE:
+        compile_ms["fp64"] = api.gen_compile(prep, precision=N.QMC_PREC_FP64).compile_ms
+    shifts = W.shifts(cfg.seed + rank, N_SHIFTS)
     stream = torch.cuda.Stream(device=dev_name)
     sh = torch.tensor(shifts, device=dev_name)
-    lam = torch.full((ns,), LAMBDA, dtype=torch.float64, device=dev_name)
-    sums, fails = di.outputs(p)
-    scr, scr_bytes = di.scratch(p)
-    # lambda per sector: halved where the sign check of Eq. 14 fails on this workload (as qmc_integrate does)
+    lam0 = LAMBDA if cfg.lam > 0 else 0.0
+    lam = torch.full((ns,), lam0, dtype=torch.float64, device=dev_name)
+    flops = np.array([prep.sector(s).flops for s in range(ns)])
+
+    def mkpass(nn, prec, active=None):
+        p = api.make_pass(nn, lat[nn], N_SHIFTS, 3, precision=prec,
+                          evaluator=evaluator if prec == N.QMC_PREC_FP64 else N.QMC_EVAL_GENERATED)
+        keep = None
+        if active is not None:
+            keep = (ctypes.c_int32 * ns)(*[int(v) for v in active])
+            p.sector_active = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int32))
+        return p, keep
+
+    # lambda per sector: halved where the sign check of Eq. 14 fails (as qmc_integrate does), checked by the FP64
+    # pass and by the mixed pass of the timed step
     halvings = 0
+    sums, fails = di.outputs(api.make_pass(n, lat[n], N_SHIFTS, 3))
     for _ in range(6):
-        di.eval_sums(p, sh, lam, sums, fails)
-        bad = fails.sum(dim=1) > 0
+        bad = torch.zeros(ns, dtype=torch.bool, device=dev_name)
+        for nn, prec in ((n64, N.QMC_PREC_FP64), (n, N.QMC_PREC_MIXED)):
+            p, _k = mkpass(nn, prec)
+            di.eval_sums(p, sh, lam, sums, fails)
+            bad |= fails.sum(dim=1) > 0
         if not bool(bad.any()):
             break
         lam[bad] *= 0.5
         halvings += int(bad.sum().item())
-    lam_desc = f"{LAMBDA}" if halvings == 0 else f"{LAMBDA} halved per failing sector ({halvings} halvings)"
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev_name)
-    L = N.lib()
-    evals_per_step = ns * N_SHIFTS * n
+    lam_desc = f"{lam0}" if halvings == 0 else f"{lam0} halved per failing sector ({halvings} halvings)"
 
-    def step(evs):
+    # precision of each sector in the mixed step: the probe's decision at this lattice size
+    p_probe, _k = mkpass(n, N.QMC_PREC_MIXED)
+    keep32, probe_ratio = probe_flags(L, N, prep, di, p_probe, sh, lam, FP32_BUDGET * REL_TOL)
+    keep64 = 1 - keep32
+    n32, n64s = int(keep32.sum()), int(keep64.sum())
+    p32, k32 = mkpass(n, N.QMC_PREC_MIXED, keep32) if n32 else (None, None)
+    p64m, k64 = mkpass(n, N.QMC_PREC_FP64, keep64) if n64s else (None, None)
+    scr = {}
+
+    def scratch(p, tag):
+        need = api.scratch_bytes(prep, p)
+        if tag not in scr or scr[tag].numel() < need + 256:
+            scr[tag] = torch.empty(need + 256, dtype=torch.uint8, device=dev_name)
+        base = scr[tag].data_ptr()
+        return base + (-base) % 256, need
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev_name)
+    sums_m, fails_m = di.outputs(api.make_pass(n, lat[n], N_SHIFTS, 3))
+
+    def launch_eval(p, tag):
+        b, nb = scratch(p, tag)
+        N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), ctypes.byref(p), sh.data_ptr(),
+                                    lam.data_ptr(), b, nb, stream.cuda_stream), "qmc_eval_partials")
+
+    def launch_reduce(p, tag, out_s, out_f):
+        b, nb = scratch(p, tag)
+        N.check(L.qmc_reduce_partials(prep.packed, di.dpacked.data_ptr(), ctypes.byref(p), b, nb, out_s.data_ptr(),
+                                      out_f.data_ptr(), stream.cuda_stream), "qmc_reduce_partials")
+
+    def step_mixed(evs):
         with torch.cuda.stream(stream):
             flush.fill_(1)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), p, sh.data_ptr(), lam.data_ptr(), scr,
-                                        scr_bytes, stream.cuda_stream), "qmc_eval_partials")
-            e1.record(stream)
-            N.check(L.qmc_reduce_partials(prep.packed, di.dpacked.data_ptr(), p, scr, scr_bytes, sums.data_ptr(),
-                                          fails.data_ptr(), stream.cuda_stream), "qmc_reduce_partials")
-            e2.record(stream)
-            evs.append((e0, e1, e2))
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[0].record(stream)
+            if p32 is not None:
+                launch_eval(p32, "32")
+            e[1].record(stream)
+            if p64m is not None:
+                launch_eval(p64m, "64m")
+            e[2].record(stream)
+            if p32 is not None:
+                launch_reduce(p32, "32", sums_m, fails_m)
+            if p64m is not None:
+                launch_reduce(p64m, "64m", sums_m, fails_m)
+            e[3].record(stream)
+            evs.append(e)
 
-    warm = []
-    for _ in range(args.warmup):
-        step(warm)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
+    def timed(step, steps, warmup):
+        for _ in range(warmup):
+            step([])
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            step(evs)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if dist:
+            dist.barrier()
+            el = max_over_ranks(el, dist, dev_name)
+        return el, evs
+
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
-    evs = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step(evs)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop()
-    elapsed = t1 - t0
-    if dist:
-        elapsed = max_over_ranks(elapsed, dist, dev_name)
-    eval_ms = [a.elapsed_time(b) for a, b, c in evs]
-    pass_ms = [a.elapsed_time(c) for a, b, c in evs]
-    sign_failures = int(fails.sum().item())
-    value = world * evals_per_step * args.steps / elapsed
-    flops_launch = prep.info.flops_per_eval * evals_per_step
-    achieved = flops_launch / (statistics.mean(eval_ms) * 1e-3) / 1e12
-    kh = kernel_hash()
-    traffic = TRAFFIC_BYTES if (TRAFFIC_BYTES is not None and kh == KERNEL_HASH) else None
-
-    # the same pass in mixed precision (FP32 evaluation, FP64 lattice arithmetic and accumulation), with the
-    # evaluator generated for this family (compiled here, before any timing) and with the table evaluator
-    gen_info = api.gen_compile(prep)
-    pm = api.make_pass(n, z, N_SHIFTS, 3, precision=N.QMC_PREC_MIXED, evaluator=N.QMC_EVAL_GENERATED)
-    scr_m, scr_m_bytes = di.scratch(pm)
-    sums_m, fails_m = di.outputs(pm)
-
-    def step_mixed(evs_m):
-        with torch.cuda.stream(stream):
-            flush.fill_(1)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record(stream)
-            N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), pm, sh.data_ptr(), lam.data_ptr(), scr_m,
-                                        scr_m_bytes, stream.cuda_stream), "qmc_eval_partials")
-            e1.record(stream)
-            N.check(L.qmc_reduce_partials(prep.packed, di.dpacked.data_ptr(), pm, scr_m, scr_m_bytes,
-                                          sums_m.data_ptr(), fails_m.data_ptr(), stream.cuda_stream),
-                    "qmc_reduce_partials")
-            e2.record(stream)
-            evs_m.append((e0, e1, e2))
-
     for _ in range(args.warmup):
         step_mixed([])
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    evs_m = []
-    tm0 = time.perf_counter()
-    for _ in range(args.steps):
-        step_mixed(evs_m)
-    torch.cuda.synchronize()
-    tmix = time.perf_counter() - tm0
-    if dist:
-        tmix = max_over_ranks(tmix, dist, dev_name)
-    mix_eval_ms = statistics.mean(a.elapsed_time(b) for a, b, c in evs_m)
-    s64 = sums.cpu().numpy()
-    s32 = sums_m.cpu().numpy()
-    mixed_dev = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
-    # table evaluator on the same pass (for comparison; fewer steps)
-    pt = api.make_pass(n, z, N_SHIFTS, 3, precision=N.QMC_PREC_MIXED, evaluator=N.QMC_EVAL_TABLE)
-    evs_t = []
-    for i in range(2 + max(1, args.steps // 2)):
+    elapsed, evs = timed(step_mixed, args.steps, 0)
+    clocks = sampler.stop()
+    evals_step = ns * N_SHIFTS * n
+    value = world * evals_step * args.steps / elapsed
+    ms32 = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    ms64m = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    step_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+    fl32 = float((flops * keep32).sum()) * N_SHIFTS * n
+    fl64m = float((flops * keep64).sum()) * N_SHIFTS * n
+    ach32 = fl32 / (ms32 * 1e-3) / 1e12 if n32 else 0.0
+    kh = kernel_hash()
+    # kernels of our library launched per step: one evaluation launch per (precision, sector class) and one
+    # reduction launch per pass
+    cls = np.array([1 if prep.sector(s).kind == 2 else 0 for s in range(ns)])
+    launches_mixed = sum(len(set(cls[np.asarray(mask) > 0])) + 1 for mask in (keep32, keep64) if np.any(mask))
+
+    # the FP64 pass alone (all sectors) on the smaller lattice, and the mixed pass on the same points
+    p64, _ = mkpass(n64, N.QMC_PREC_FP64)
+    sums64, fails64 = di.outputs(p64)
+
+    def step64(evs_):
         with torch.cuda.stream(stream):
             flush.fill_(1)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            N.check(L.qmc_eval_partials(prep.packed, di.dpacked.data_ptr(), pt, sh.data_ptr(), lam.data_ptr(), scr_m,
-                                        scr_m_bytes, stream.cuda_stream), "qmc_eval_partials")
-            e1.record(stream)
-            if i >= 2:
-                evs_t.append((e0, e1))
-    torch.cuda.synchronize()
-    tab_eval_ms = statistics.mean(a.elapsed_time(b) for a, b in evs_t)
-    mixed = {"value": world * evals_per_step * args.steps / tmix, "unit": "evals/s", "dtype": "f32+f64",
-             "evaluator": "generated", "codegen_compile_ms": gen_info.compile_ms,
-             "table_evaluator": {"eval_kernel_ms": tab_eval_ms, "evals_per_s_kernel": evals_per_step / (tab_eval_ms * 1e-3),
-                                 "frac": flops_launch / (tab_eval_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS},
-             "ms_per_step": 1e3 * tmix / args.steps, "eval_kernel_ms": mix_eval_ms,
-             "roofline": {"bound": "alu", "achieved": flops_launch / (mix_eval_ms * 1e-3) / 1e12,
-                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                          "frac": flops_launch / (mix_eval_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
-                          "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"},
-             "max_rel_dev_from_fp64_sums": mixed_dev, "sign_failures": int(fails_m.sum().item())}
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            launch_eval(p64, "64")
+            e[1].record(stream)
+            launch_reduce(p64, "64", sums64, fails64)
+            e[2].record(stream)
+            evs_.append(e)
 
-    # e2e: the same pass through the host-buffer entry point, copies inside the timed region
+    steps64 = max(2, args.steps // 4)
+    el64, evs64 = timed(step64, steps64, 1)
+    ms64 = statistics.mean(e[0].elapsed_time(e[1]) for e in evs64)
+    ev64 = ns * N_SHIFTS * n64
+    fl64 = float(flops.sum()) * N_SHIFTS * n64
+    fp64 = {"value": world * ev64 * steps64 / el64, "unit": "evals/s", "dtype": "f64", "lattice_n": n64,
+            "steps": steps64, "ms_per_step": 1e3 * el64 / steps64,
+            "roofline": {"bound": "alu", "achieved": fl64 / (ms64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": fl64 / (ms64 * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "kernel": ("qd_eval_c1 (generated FP64 evaluator)" if evaluator != N.QMC_EVAL_TABLE
+                                    else "qmc_eval_kernel (FP64 table evaluator)"),
+                         "eval_kernel_ms": ms64, "flops_per_eval": prep.info.flops_per_eval,
+                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz (recipe FP64 1.25 TFLOP/s)"},
+            "sign_failures": int(fails64.sum().item())}
+    # mixed on the FP64 pass's points: per-order deviation from FP64 (the FP64 sums equal the oracle's to 1e-12)
+    pm32, km32 = mkpass(n64, N.QMC_PREC_MIXED, keep32) if n32 else (None, None)
+    sums_c, fails_c = di.outputs(p64)
+    sums_c.copy_(sums64)
+    if pm32 is not None:
+        di.eval_sums(pm32, sh, lam, sums_c, fails_c)
+    torch.cuda.synchronize()
+    a64 = sums64.cpu().numpy()
+    am = sums_c.cpu().numpy()
+    c64 = a64[..., 0] + 1j * a64[..., 1]
+    cm = am[..., 0] + 1j * am[..., 1]
+    dev_slot = []
+    for k in range(prep.info.n_slots):
+        tot = np.abs(c64[:, :, k]).sum(axis=0).max()
+        dev_slot.append(float(np.abs(cm[:, :, k] - c64[:, :, k]).sum(axis=0).max() / max(tot, 1e-300)))
+    Q64, mean64, err64 = api.combine(prep, p64, a64)
+    Qm, meanm, errm = api.combine(prep, p64, am)
+    order_dev = [float(abs(meanm[o] - mean64[o]) / max(abs(mean64[o]), 1e-300)) for o in range(len(mean64))]
+
+    # e2e: the mixed step through the host-buffer entry point, copies inside the timed region
     ctx = api.Context(local, 1 << 30, stream)
-    import ctypes
-    packed_pinned = torch.frombuffer(bytearray(prep.packed), dtype=torch.uint8).pin_memory()
     sh_pinned = torch.tensor(shifts).pin_memory()
-    lam_pinned = torch.full((ns,), LAMBDA, dtype=torch.float64).pin_memory()
+    lam_pinned = lam.cpu().pin_memory()
     sums_h = torch.zeros((ns, N_SHIFTS, prep.info.n_slots, 2), dtype=torch.float64).pin_memory()
     fails_h = torch.zeros((ns, N_SHIFTS), dtype=torch.int64).pin_memory()
+    packed_pinned = torch.frombuffer(bytearray(prep.packed), dtype=torch.uint8).pin_memory()
+    host_passes = [p for p in (p32, p64m) if p is not None]
 
     def e2e_step():
-        N.check(L.qmc_eval_sums_host(ctx._c, ctypes.c_void_p(packed_pinned.data_ptr()), p, sh_pinned.data_ptr(),
-                                     lam_pinned.data_ptr(), sums_h.data_ptr(), fails_h.data_ptr()),
-                "qmc_eval_sums_host")
+        for p in host_passes:
+            N.check(L.qmc_eval_sums_host(ctx._c, ctypes.c_void_p(packed_pinned.data_ptr()), ctypes.byref(p),
+                                         sh_pinned.data_ptr(), lam_pinned.data_ptr(), sums_h.data_ptr(),
+                                         fails_h.data_ptr()), "qmc_eval_sums_host")
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -429,43 +517,56 @@ def main_ours(args):
     te = time.perf_counter() - te0
     if dist:
         te = max_over_ranks(te, dist, dev_name)
-    h2d = len(prep.packed) + sh_pinned.numel() * 8 + lam_pinned.numel() * 8
-    d2h = sums_h.numel() * 8 + fails_h.numel() * 8
+    h2d = len(host_passes) * (len(prep.packed) + sh_pinned.numel() * 8 + lam_pinned.numel() * 8)
+    d2h = len(host_passes) * (sums_h.numel() * 8 + fails_h.numel() * 8)
     ctx.close()
 
-    extras = {"mixed": mixed}
+    extras = {}
     if not args.no_extras and rank == 0:
-        seeds = 32 if cfg.topology.loops == 1 else 6
-        extras["time_to_1e-3"] = time_to_accuracy(api, blob, cfg, local, stream, seeds, lock_step=1)
-        extras["time_to_1e-3_fp64_per_sector"] = time_to_accuracy(api, blob, cfg, local, stream, seeds)
-        extras["time_to_1e-3_mixed"] = time_to_accuracy(api, blob, cfg, local, stream, seeds,
-                                                         precision=N.QMC_PREC_MIXED)
-        if cfg is W.CONFIG1:
-            # the paper's own workloads beside the headline: its one-loop scan through the serving loop and its
-            # Table 2 points (each guarded, so that a failure there cannot cost the line)
-            for key, fn in (("paper_ia_scan", lambda: paper_ia_scan(1000, device=local)),
-                            ("paper_table2", lambda: paper_table2(seeds=4, device=local))):
-                try:
-                    extras[key] = fn()
-                except Exception as exc:  # noqa: BLE001
-                    extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        seeds = args.tta_seeds
+        tta = {}
+        for key, kw in (("mixed_per_sector", dict(precision=N.QMC_PREC_MIXED)),
+                        ("fp64_per_sector", dict(precision=N.QMC_PREC_FP64)),
+                        ("fp64_per_integral", dict(precision=N.QMC_PREC_FP64, lock_step=1))):
+            tta[key] = time_to_accuracy(api, blob, cfg, local, stream, seeds, **kw)
+        tta["mixed_speedup_p50_vs_fp64_per_integral"] = tta["fp64_per_integral"]["p50_ms"] / tta["mixed_per_sector"]["p50_ms"]
+        extras["time_to_1e-3"] = tta
+        guarded = []
+        if args.serving_sample > 0:
+            guarded.append(("serving", lambda: serving_run(args.serving_sample, device=local, baseline=True,
+                                                           baseline_count=min(16, args.serving_sample))))
+        guarded += [("paper_table2", lambda: paper_table2(seeds=4, device=local)),
+                    ("paper_ia_scan", lambda: paper_ia_scan(1000, device=local))]
+        for key, fn in guarded:
+            try:
+                extras[key] = fn()
+            except Exception as exc:  # noqa: BLE001 -- a failure there must not cost the line
+                extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(cfg, n, ns, lam_desc),
-            "e2e": {"value": world * evals_per_step * args.steps / te, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {**workload_config(cfg, n, ns, lam_desc), "fp32_sectors": n32, "fp64_sectors": n64s,
+                       "fp32_budget": f"{FP32_BUDGET} x rel_tol {REL_TOL}"},
+            "e2e": {"value": world * evals_step * args.steps / te, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,  # per step: qmc_eval_kernel + qmc_finalize_kernel
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "kernel": ("qd_eval_c1 (generated FP64 evaluator)" if evaluator != N.QMC_EVAL_TABLE
-                                    else f"qmc_eval_kernel<{prep.info.dim},deform,{maxm_of(prep)}>"),
-                         "flops_per_eval": prep.info.flops_per_eval, "sign_failures": sign_failures,
-                         "eval_kernel_ms": statistics.mean(eval_ms), "pass_ms": statistics.mean(pass_ms),
-                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2070 MHz (recipe FP64 1.25 TFLOP/s)",
-                         "kernel_hash": kh},
+            "gpu_launches": launches_mixed * args.steps,
+            "roofline": {"bound": "alu", "achieved": ach32, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": ach32 / FP32_PEAK_TFLOPS,
+                         "traffic": TRAFFIC_BYTES if (TRAFFIC_BYTES is not None and kh == KERNEL_HASH) else None,
+                         "kernel": "qg_eval_c1 (generated FP32 evaluator)", "eval_kernel_ms": ms32,
+                         "evals_per_launch": n32 * N_SHIFTS * n,
+                         "flops_per_eval": float((flops * keep32).sum() / max(n32, 1)),
+                         "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x 2070 MHz", "kernel_hash": kh},
+            "fp64_sectors_kernel_ms": ms64m, "fp64_sectors_flop": fl64m, "step_device_ms": step_ms,
+            "probe_max_ratio": {"max": float(probe_ratio.max()), "median": float(np.median(probe_ratio))},
+            "sign_failures": int(fails_m.sum().item()),
+            "codegen_compile_ms": compile_ms,
+            "fp64": fp64,
+            "mixed_error_vs_fp64": {"lattice_n": n64, "per_slot_l1": dev_slot, "per_order_rel": order_dev,
+                                    "fp64_rel_err_per_order": [float(math.hypot(*err64[o]) / max(abs(mean64[o]), 1e-300))
+                                                               for o in range(len(mean64))]},
             "clocks": clocks,
         }
         if not args.no_extras:
@@ -486,13 +587,14 @@ def pct(v, q):
     return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
 
 
-def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0, baseline=False, max_seconds=300.0):
+def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0, baseline=False, max_seconds=300.0,
+                baseline_count=0):
     """Config 4: Poisson arrivals of requests for random integrals (massless box, massive box, planar and
     non-planar double box) at random s ~ U[4.5,12], t ~ U[-4,-0.5], each integrated to 1e-3 relative error with 16
     shifts by the serving loop (continuous batching, per-sector lattices).  Latency = submission to completion.
-    baseline: the same requests afterwards one at a time through the plain FP64 per-integral path (qmc_integrate,
-    FP64, all sectors on one lattice ladder); its latency is the request's own integration time, i.e. as if each
-    arrived at an idle GPU, which favours the baseline."""
+    baseline: the same requests (the first baseline_count of them, all when 0) afterwards one at a time through
+    the plain FP64 per-integral path (qmc_integrate, FP64, all sectors on one lattice ladder); its latency is the
+    request's own integration time, i.e. as if each arrived at an idle GPU, which favours the baseline."""
     from paper_1508_02512_gb300 import api
     from paper_1508_02512_gb300 import tables as T
     arrivals = W.serving_arrivals(n_requests, rate, seed)
@@ -547,7 +649,8 @@ def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0, baselin
         ctx = api.Context(device, 8 << 30)
         ids = [ctx.load_sectors(b) for b in blobs]
         secs, ok_b, evals = [], 0, 0
-        for k, (at, ci, sv, tv) in enumerate(arrivals):
+        nb = baseline_count if baseline_count > 0 else n_requests
+        for k, (at, ci, sv, tv) in enumerate(arrivals[:nb]):
             cfg = W.CONFIGS[ci]
             ctx.set_kinematics(ids[ci], W.kinematics(cfg.topology, **{**cfg.point, "s": sv, "t": tv}),
                                cfg.order_min, cfg.order_max)
@@ -559,7 +662,7 @@ def serving_run(n_requests=24, rate=50.0, seed=0, precision=1, device=0, baselin
         ctx.close()
         out["fp64_per_integral_baseline"] = {
             "path": "qmc_integrate, FP64, one integral at a time, all sectors on one lattice ladder",
-            "converged": ok_b, "max_seconds": max_seconds, "total_s": sum(secs),
+            "requests": nb, "converged": ok_b, "max_seconds": max_seconds, "total_s": sum(secs),
             "p50_s": statistics.median(secs), "p99_s": pct(secs, 0.99), "evals": evals}
     return out
 
@@ -621,18 +724,25 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0, lock
     ctx.set_kinematics(iid, cfg.kin, cfg.order_min, cfg.order_max)
     kw = dict(rel_tol=1e-3, n_shifts=N_SHIFTS, lam=LAMBDA, precision=precision, lock_step=lock_step, max_seconds=120)
     ctx.integrate(iid, seed=999, **kw)  # warm-up (kernels, generated evaluator)
-    ts, ns, ev, ok = [], [], [], 0
+    ts, ns, ev, ok, kms, rr, worst = [], [], [], 0, [], [], 0.0
     for s in range(seeds):
         t0 = time.perf_counter()
         r = ctx.integrate(iid, seed=1000 + s, **kw)
         ts.append(1e3 * (time.perf_counter() - t0))
         ns.append(r.n_final)
         ev.append(r.evals)
+        kms.append(r.kernel_ms)
+        rr.append(r.fp64_reruns)
         ok += r.status == 0
+        val, err = api.result_arrays(r)
+        vmax = float(np.max(np.abs(val)))
+        for o in range(len(val)):
+            worst = max(worst, math.hypot(*err[o]) / max(abs(val[o]), 1e-6 * vmax))
     ctx.close()
     return {"p50_ms": statistics.median(ts), "p99_ms": pct(ts, 0.99), "seeds": seeds, "converged": ok,
             "median_final_n": int(statistics.median(ns)), "median_evals": int(statistics.median(ev)),
-            "precision": "f64" if precision == 0 else "f32+f64",
+            "median_kernel_ms": statistics.median(kms), "median_fp64_sectors": statistics.median(rr),
+            "worst_rel_err": worst, "precision": "f64" if precision == 0 else "f32+f64",
             "lattices": "one ladder for all sectors" if lock_step else "per sector"}
 
 
@@ -642,8 +752,6 @@ def paper_table2(seeds=8, rel_tol=1e-4, device=0):
     p50 over `seeds` shift seeds after a warm-up integration (which compiles the generated evaluators); the
     converted P_i of the first seed beside the paper's printed QMC values."""
     import torch
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from paper_tables import golden_table2, to_paper_euclid
     from paper_1508_02512_gb300 import _native as N
     from paper_1508_02512_gb300 import api
     from paper_1508_02512_gb300 import tables as T
@@ -682,9 +790,35 @@ def paper_table2(seeds=8, rel_tol=1e-4, device=0):
             "paper_times_s": {"legs -1,0,0,-1": 2.2, "legs 0,-1,0,-1": 0.84, "legs 0,0,-1,-1": 2.2}}
 
 
-def profile_pass(precision="fp64", integral="massive_box"):
+def golden_table2():
+    """The paper's printed Table 2 (tests/golden/paper_table_2.txt, a data file): {(column tag, method): {i: (P_i,
+    error)}}."""
+    out = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_table_2.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        tag, i, method, val, err = line.split()
+        out.setdefault((tag, method), {})[int(i)] = (float(val), float(err))
+    return out
+
+
+def to_paper_euclid(c, e, s):
+    """Table 2's normalisation: real coefficients c[k] of eps^(k-4) (k = 0..4) with errors e[k], at s < 0, to
+    P(eps) = exp(2 eps gamma_E) (-s)^(3 + 2 eps) I(eps); returns {4 - k: (P_{4-k}, error)}, errors added
+    linearly."""
+    gamma_e = 0.5772156649015329
+    a = 2.0 * (gamma_e + math.log(-s))
+    out = {}
+    for k in range(5):
+        w = [a ** (k - q) / math.factorial(k - q) for q in range(k + 1)]
+        out[4 - k] = ((-s) ** 3 * sum(w[q] * c[q] for q in range(k + 1)),
+                      (-s) ** 3 * sum(abs(w[q]) * e[q] for q in range(k + 1)))
+    return out
+
+
+def profile_pass(precision="fp64", integral="massive_box", log2n=0):
     """Two passes of the benchmark integral at n = 1048573 (largest prime below 2^20; 65521 for a two-loop
-    integral), 16 shifts: the small case for ncu captures."""
+    integral, or the largest prime below 2^log2n), 16 shifts: the case for ncu captures."""
     import torch
     from paper_1508_02512_gb300 import _native as N
     from paper_1508_02512_gb300 import api
@@ -693,11 +827,12 @@ def profile_pass(precision="fp64", integral="massive_box"):
     blob = T.compile_integral(cfg.topology, T.zero_invariants_of(cfg.topology, cfg.point), strategy=cfg.strategy)
     prep = api.prepare(blob, cfg.kin, cfg.order_min, cfg.order_max)
     dev = api.DeviceIntegral(prep)
-    n = 1048573 if cfg.topology.loops == 1 else 65521
-    p = api.make_pass(n, dict(api.builtin_lattices())[n], N_SHIFTS, 3,
+    lat = dict(api.builtin_lattices())
+    n = max(k for k in lat if k < (1 << log2n)) if log2n else (1048573 if cfg.topology.loops == 1 else 65521)
+    p = api.make_pass(n, lat[n], N_SHIFTS, 3,
                       precision=N.QMC_PREC_MIXED if precision == "mixed" else N.QMC_PREC_FP64)
     sh = torch.tensor(W.shifts(cfg.seed, N_SHIFTS), device="cuda")
-    lam = torch.full((prep.info.n_sectors,), LAMBDA, dtype=torch.float64, device="cuda")
+    lam = torch.full((prep.info.n_sectors,), LAMBDA if cfg.lam > 0 else 0.0, dtype=torch.float64, device="cuda")
     sums, fails = dev.outputs(p)
     for _ in range(2):
         dev.eval_sums(p, sh, lam, sums, fails)
@@ -714,7 +849,7 @@ if __name__ == "__main__":
     elif a.paper_table2:
         print(json.dumps(paper_table2()))
     elif a.profile_pass:
-        profile_pass(a.precision, a.integral)
+        profile_pass(a.precision, a.integral, a.profile_log2n)
     elif a.impl == "reference":
         main_reference(a)
     else:

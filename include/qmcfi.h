@@ -271,9 +271,16 @@ int qmc_autotune_clear(void);
  * deployment convenience.  Same inputs, outputs and results as qmc_eval_sums; the scratch is a fixed 32 MiB
  * array inside the library that every GPU loading the library holds until exit.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress, with the device current), so make it before any
- * stream capture.  Calls share the array: calls that overlap on the GPU race; calls in one stream are ordered.
- * Allocates nothing (no cudaMalloc/cudaFree).  Returns QMC_ERR_MEMORY when the pass needs more scratch than
- * 32 MiB (qmc_scratch_bytes() > 33554432), QMC_ERR_ARG for invalid passes.
+ * stream capture.  The address is kept per device ordinal for the primary context: it does not survive
+ * cudaDeviceReset or a switch to another context on that device.  Calls share the array: calls that overlap on
+ * the GPU race; calls in one stream are ordered.
+ * Allocates nothing (no cudaMalloc/cudaFree).  Code is loaded on first use, though: with the default evaluator
+ * (QMC_EVAL_AUTO = generated) the first pass of a family of sector tables in a process compiles that family's
+ * evaluator with NVRTC and loads the module onto the device, which needs device memory.  Callers that cannot
+ * allow this during their allocation-free phase warm up at start-up (qmc_gen_compile with load = 1 for each
+ * precision the passes use, or one call of this function) or set pass->evaluator = QMC_EVAL_TABLE.
+ * Returns QMC_ERR_MEMORY, without touching sums or fails, when the pass needs more scratch than 32 MiB
+ * (qmc_scratch_bytes() > 33554432), QMC_ERR_ARG for invalid passes.
  */
 int qmc_eval_sums_noalloc(const void *packed_host, const void *packed_dev, const qmc_pass *pass,
                           const double *shifts_dev, const double *lambda_dev, double *sums_dev, int64_t *fails_dev,

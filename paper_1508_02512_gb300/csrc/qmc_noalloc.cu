@@ -9,7 +9,10 @@
  *
  * The array's name is, in host code, a host-side stand-in, not a device address: its device address is taken
  * once per device with cudaGetSymbolAddress (with that device current) on the first call made on that device,
- * so that first call should come before any stream capture.  All calls share the array, so two calls whose
+ * so that first call should come before any stream capture.  The address is cached per device ordinal and
+ * belongs to the context that was current then (the runtime's primary context): it goes stale after
+ * cudaDeviceReset, or when the caller makes another context current on that device, so only the primary
+ * context is supported and the library must not outlive a reset of its device.  All calls share the array, so two calls whose
  * work overlaps on the GPU (different streams, or different host threads) race on it; calls in one stream
  * are serialised by the stream.  The work counters are cleared by every call; partials are overwritten.
  */

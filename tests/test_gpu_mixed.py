@@ -143,3 +143,48 @@ def test_mixed_integrate_massive_box_matches_fp64():
     print("massive box fp64", v64, "mixed", v32, "fp64 sectors in mixed", r32.fp64_reruns)
     assert abs(v32[0] - v64[0]) <= 5 * math.hypot(math.hypot(*e64[0]), math.hypot(*e32[0])) + 1e-5 * abs(v64[0])
     ctx.close()
+
+
+# rel_tol 1e-3 with the library's default fp32_budget of 0.1: a sector stays in FP32 while its probe finds
+# sum |v32 - v64| <= 1e-4 sum |v64| in every slot
+PROBE_BUDGET = 1e-4
+
+
+@pytest.mark.parametrize("cfg", [W.CONFIG2, W.CONFIG3], ids=lambda c: c.name)
+def test_two_loop_mixed_sums_within_the_probe_budget(cfg):
+    """Mixed (FP32, generated evaluator) sums of the two-loop double boxes against the FP64 oracle on identical
+    points.  The probe samples every point of the first shift here (n <= 4096), so for each sector it keeps in
+    FP32 the first shift's sums are guaranteed within the budget of its summed magnitudes per slot, and the second
+    shift is held to twice that.  The error of every sector, kept or not, is printed per order."""
+    blob, prep, dev = setup(cfg)
+    api.gen_compile(prep)
+    ns, slots = prep.info.n_sectors, prep.info.n_slots
+    prob = OI.make_problem(cfg.topology, {**cfg.point, **LEGS0}, cfg.order_min, cfg.order_max)
+    n = 1021
+    z = OL.cbc_plain(n, 6)
+    shifts = W.shifts(37, 2)
+    lams = [cfg.lam] * ns
+    p = api.make_pass(n, z, 2, 3, precision=N.QMC_PREC_MIXED, evaluator=N.QMC_EVAL_GENERATED)
+    out = torch.zeros((ns, slots, 4), dtype=torch.float64, device="cuda")
+    sh = torch.tensor(shifts, device="cuda")
+    lam = torch.tensor(lams, device="cuda", dtype=torch.float64)
+    assert N.lib().qmc_probe_precision(prep.packed, dev.dpacked.data_ptr(), ctypes.byref(p), sh.data_ptr(),
+                                       lam.data_ptr(), 4096, out.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    pr = out.cpu().numpy()
+    keep = np.all(pr[:, :, 1] <= PROBE_BUDGET * pr[:, :, 0], axis=1)
+    sums, fails = run_pass(dev, p, shifts, lams)
+    worst_kept = np.zeros(slots)
+    worst_all = np.zeros(slots)
+    for s, sec in enumerate(prob.sectors):
+        o, l1, _, l1c = OI.lattice_sums(sec, prob.e4, n, z, shifts, lams[s], 3, prob.kmax, with_scale=True)
+        k = o.shape[1]
+        rel = np.abs(sums[s, :, :k] - o) / np.maximum(l1, 1e-300)
+        worst_all[:k] = np.maximum(worst_all[:k], rel.max(axis=0))
+        if keep[s]:
+            worst_kept[:k] = np.maximum(worst_kept[:k], rel.max(axis=0))
+            assert np.all(rel[0] <= PROBE_BUDGET * (1 + 1e-6)), (s, rel[0])
+            assert np.all(rel[1] <= 2 * PROBE_BUDGET), (s, rel[1])
+    print(f"{cfg.name}: {int(keep.sum())}/{ns} sectors kept in FP32; mixed |gpu-oracle| / sum|values| per slot: "
+          f"kept {worst_kept}, all sectors {worst_all}")
+    assert keep.sum() >= ns // 2
