@@ -21,8 +21,10 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmcfi.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = (["qmc_kernels.cu", "qmc_prepare.cpp", "qmc_pass.cpp", "qmc_context.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"] +
-           [f"qmc_kern_d{d}.cu" for d in range(1, 7)])
+SOURCES = ["qmc_kernels.cu", "qmc_prepare.cpp", "qmc_pass.cpp", "qmc_context.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"]
+# the ahead-of-time kernels, one translation unit per sector dimension (built in parallel)
+DIM_SOURCE = "qmc_kern_dim.cu"
+DIMS = range(1, 7)
 # device headers compiled again at run time with the generated evaluators: (C identifier, file)
 EMBEDDED = [("qmc_src_qmcfi_h", os.path.join(ROOT, "include", "qmcfi.h")),
             ("qmc_src_qmc_internal_h", os.path.join(CSRC, "qmc_internal.h")),
@@ -41,7 +43,7 @@ def _cuda_lib_dir(nv: str) -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in SOURCES + ["qmc_internal.h", "qmc_host_internal.h", "qmc_device.cuh", "qmc_dev.cuh", "lattice_table.h"]]
+    files = [os.path.join(CSRC, f) for f in SOURCES + [DIM_SOURCE, "qmc_internal.h", "qmc_host_internal.h", "qmc_device.cuh", "qmc_dev.cuh", "lattice_table.h"]]
     files.append(os.path.join(ROOT, "include", "qmcfi.h"))
     return files
 
@@ -82,6 +84,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         obj = os.path.join(OUT, src.rsplit(".", 1)[0] + f".{tag}.o")
         objs.append(obj)
         cmds.append([nv, "-c", os.path.join(CSRC, src), "-o", obj] + common)
+    for d in DIMS:
+        obj = os.path.join(OUT, f"qmc_kern_d{d}.{tag}.o")
+        objs.append(obj)
+        cmds.append([nv, "-c", os.path.join(CSRC, DIM_SOURCE), "-o", obj, f"-DQMC_S={d}"] + common)
 
     def run(cmd):
         p = subprocess.run(cmd, capture_output=True, text=True)
