@@ -295,22 +295,24 @@ DEV cd det_deform(const double (&A)[S][S], double lam) {
 
 /* ------------------------------------------------------------------ polynomial evaluators (FP64)
    The integrand asks an evaluator for
-     UFr(t, U, F)          U~ and F~ at real t (undeformed sectors, Eqs. 7-8),
-     GH(t, g, h)           g_j = dF~/dt_j and h_p = d2F~/dt_j dt_k (p over j <= k, row-major upper triangle) at
-                           real t, the inputs of the deformation of Eq. 14,
-     UFc(z, needU, U, F)   U~ (1 when needU is false) and F~ at the deformed point z.
-   TabPol walks the staged term table; the generated FP64 evaluator (run-time compiled per family) holds each
-   sector's monomials as straight-line code and reads only the coefficients from the same table. */
+     UFr(Y, t, U, F)          U~ and F~ at real t (undeformed sectors, Eqs. 7-8),
+     GH(Y, t, g, h)           g_j = dF~/dt_j and h_p = d2F~/dt_j dt_k (p over j <= k, row-major upper triangle) at
+                              real t, the inputs of the deformation of Eq. 14,
+     UFc(Y, z, needU, U, F)   U~ (1 when needU is false) and F~ at the deformed point z,
+   where the coordinates in the subset Y (bit j = variable j) of the endpoint subtraction (Eqs. 10-12) are zero.
+   TabPol walks the staged term table (and ignores Y: zero coordinates make those terms vanish); the generated
+   FP64 evaluator (run-time compiled per family) holds each sector's monomials, per zeroed subset without the
+   terms that vanish there, as straight-line code and reads only the coefficients from the same table. */
 template <int S>
 struct TabPol {
     const PackedTerm *T;
     const PackedSector *s;
     DEV static TabPol make(const PackedTerm *T, const PackedSector &s, int) { return TabPol{T, &s}; }
-    DEV void UFr(const double *t, double &U, double &F) const {
+    DEV void UFr(unsigned, const double *t, double &U, double &F) const {
         U = poly_r<S>(T, s->nU, t);
         F = poly_r<S>(T + s->nU, s->nF, t);
     }
-    DEV void GH(const double *t, double *g, double *h) const {
+    DEV void GH(unsigned, const double *t, double *g, double *h) const {
         const PackedTerm *TG = T + s->nU + s->nF;
         const PackedTerm *TH = TG + s->nG;
 #pragma unroll
@@ -318,7 +320,7 @@ struct TabPol {
 #pragma unroll
         for (int p = 0; p < S * (S + 1) / 2; ++p) h[p] = poly_r<S>(TH + s->hstart[p], s->hstart[p + 1] - s->hstart[p], t);
     }
-    DEV void UFc(const cd *z, bool needU, cd &U, cd &F) const {
+    DEV void UFc(unsigned, const cd *z, bool needU, cd &U, cd &F) const {
         U = needU ? poly_c<S>(T, s->nU, z) : mk(1.0, 0.0);
         F = poly_c<S>(T + s->nU, s->nF, z);
     }
@@ -332,11 +334,11 @@ struct Exps {
 /* G at the point tt (t with the subset Y zeroed): returns its eps^0 value G0 and the eps-coefficient X of
    its logarithm, so that G(eps) = G0 exp(X eps) (Sec. II, Eq. 9 with the deformation of Eq. 14). */
 template <int S, bool DEF, int MAXM, class Pol>
-DEV void eval_G(const PackedSector &s, const Pol &P, const double *tt, const double *ttm, const double *Lt, double lam,
-                int M, const Exps &ex, cd &G0, cd &X, uint32_t &fails) {
+DEV void eval_G(const PackedSector &s, const Pol &P, unsigned Y, const double *tt, const double *ttm, const double *Lt,
+                double lam, int M, const Exps &ex, cd &G0, cd &X, uint32_t &fails) {
     if constexpr (!DEF) {
         double U, F;
-        P.UFr(tt, U, F);
+        P.UFr(Y, tt, U, F);
         if (s.kind == 1) F = -F;
         double g = s.D * ipow(U, ex.eU0) * ipow(F, -ex.eF0);
 #pragma unroll
@@ -354,7 +356,7 @@ DEV void eval_G(const PackedSector &s, const Pol &P, const double *tt, const dou
         }
     } else {
         double g[S], h[S * (S + 1) / 2];
-        P.GH(tt, g, h);
+        P.GH(Y, tt, g, h);
         double A[S][S];
         int p = 0;
 #pragma unroll
@@ -378,7 +380,7 @@ DEV void eval_G(const PackedSector &s, const Pol &P, const double *tt, const dou
         }
         const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
         cd U, F;
-        P.UFc(z, needU, U, F);
+        P.UFc(Y, z, needU, U, F);
         fails += (F.y > 0.0) ? 1u : 0u;
         cd G = cscale(detJ, s.D);
         if (ex.eU0 != 0) G = cmul(G, cipow(U, ex.eU0));
@@ -449,7 +451,7 @@ DEV void point_integrand(const PackedSector &s, const Pol &P, const double *x, i
             ttm[j] = zj ? 1.0 : tm[j];
         }
         cd G0, X;
-        eval_G<S, DEF, MAXM>(s, P, tt, ttm, Lt, lam, M, ex, G0, X, fails);
+        eval_G<S, DEF, MAXM>(s, P, Y, tt, ttm, Lt, lam, M, ex, G0, X, fails);
         double V[MAXM + 1];
         V[0] = 1.0;
 #pragma unroll
@@ -811,12 +813,12 @@ struct TabPolF {
     const PackedTermF *T;
     const PackedSector *s;
     DEV static TabPolF make(const PackedTermF *T, const PackedSector &s, int) { return TabPolF{T, &s}; }
-    DEV void UFr(const float *t, float &U, float &F) const {
+    DEV void UFr(unsigned, const float *t, float &U, float &F) const {
         const SmemTabF tab{T};
         U = poly_rf<S>(tab, 0, s->nU, t);
         F = poly_rf<S>(tab, s->nU, s->nF, t);
     }
-    DEV void GH(const float *t, float *g, float *h) const {
+    DEV void GH(unsigned, const float *t, float *g, float *h) const {
         const SmemTabF tab{T};
         const int bG = s->nU + s->nF, bH = bG + s->nG;
 #pragma unroll
@@ -825,7 +827,7 @@ struct TabPolF {
         for (int p = 0; p < S * (S + 1) / 2; ++p)
             h[p] = poly_rf<S>(tab, bH + s->hstart[p], s->hstart[p + 1] - s->hstart[p], t);
     }
-    DEV void UFc(const cf *z, bool needU, cf &U, cf &F) const {
+    DEV void UFc(unsigned, const cf *z, bool needU, cf &U, cf &F) const {
         const SmemTabF tab{T};
         U = needU ? poly_cf<S>(tab, 0, s->nU, z) : mkf(1.f, 0.f);
         F = poly_cf<S>(tab, s->nU, s->nF, z);
@@ -927,12 +929,12 @@ DEV cf det_sym_f(cf (&N)[S * (S + 1) / 2]) {
 #define QMC_F32_SIGN_NOISE 4e-6f
 
 template <int S, bool DEF, int MAXM, class Pol>
-DEV void eval_G_f(const PackedSector &s, const Pol &P, const float *tt, const float *ttm, const float *Lt, float lam,
-                  int M, const Exps &ex, cf &G0, cf &X, uint32_t &fails) {
+DEV void eval_G_f(const PackedSector &s, const Pol &P, unsigned Y, const float *tt, const float *ttm, const float *Lt,
+                  float lam, int M, const Exps &ex, cf &G0, cf &X, uint32_t &fails) {
     const float D = s.Df;
     if constexpr (!DEF) {
         float U, F;
-        P.UFr(tt, U, F);
+        P.UFr(Y, tt, U, F);
         if (s.kind == 1) F = -F;
         float g = D * ipowf_(U, ex.eU0) * ipowf_(F, -ex.eF0);
 #pragma unroll
@@ -949,7 +951,7 @@ DEV void eval_G_f(const PackedSector &s, const Pol &P, const float *tt, const fl
         }
     } else {
         float g[S], h[S * (S + 1) / 2];
-        P.GH(tt, g, h);
+        P.GH(Y, tt, g, h);
         cf detJ;
         if constexpr (S >= 4) {
             float s[S];
@@ -992,7 +994,7 @@ DEV void eval_G_f(const PackedSector &s, const Pol &P, const float *tt, const fl
         }
         const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
         cf U, F;
-        P.UFc(z, needU, U, F);
+        P.UFc(Y, z, needU, U, F);
         fails += (F.y > QMC_F32_SIGN_NOISE * (fabsf(F.x) + fabsf(F.y))) ? 1u : 0u;
         cf G = cscalef(detJ, D);
         if (ex.eU0 != 0) G = cmulf(G, cipowf(U, ex.eU0));
@@ -1060,7 +1062,7 @@ DEV void point_integrand_f(const PackedSector &s, const Pol &P, const float *x, 
             ttm[j] = zj ? 1.f : tm[j];
         }
         cf G0, X;
-        eval_G_f<S, DEF, MAXM>(s, P, tt, ttm, Lt, lam, M, ex, G0, X, fails);
+        eval_G_f<S, DEF, MAXM>(s, P, Y, tt, ttm, Lt, lam, M, ex, G0, X, fails);
         float V[MAXM + 1];
         V[0] = 1.f;
 #pragma unroll

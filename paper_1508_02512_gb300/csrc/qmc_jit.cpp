@@ -42,7 +42,7 @@
 
 namespace {
 
-#define QMC_JIT_GENERATOR_VERSION 5u
+#define QMC_JIT_GENERATOR_VERSION 6u
 #define QMC_GEN_INLINE_TERMS 2048 /* families with more terms get out-of-line sector functions */
 
 const PackedHeader *hdr(const void *p) {
@@ -86,6 +86,7 @@ uint64_t family_key(const PackedHeader *h) {
     const PackedTermF *tf = terms_f(h);
     for (int s = 0; s < h->n_sectors; ++s) {
         const PackedSector &p = ps[s];
+        f.add_i(p.sing_mask);
         f.add_i(p.nU);
         f.add_i(p.nF);
         f.add_i(p.nG);
@@ -133,7 +134,11 @@ struct PolySet {
     std::map<Key, std::vector<Entry>> mono; /* every needed monomial (terms' and their parents), key -> terms */
 };
 
-void add_term(PolySet &P, int acc, int term, const uint8_t *e) {
+/* zeroed: the subset Y of the endpoint subtraction whose coordinates are zero; terms with a positive power of
+   one of them vanish there and are left out (adding c * 0 would change nothing) */
+void add_term(PolySet &P, int acc, int term, const uint8_t *e, unsigned zeroed = 0) {
+    for (int j = 0; j < P.S; ++j)
+        if (((zeroed >> j) & 1u) && e[j]) return;
     Key k = key_of(e, P.S);
     if (k == 0) {
         P.constants.push_back({acc, term});
@@ -249,8 +254,10 @@ std::string generate(const PackedHeader *h, const Lang &L) {
         o += "struct " + SR + " { " + R + " U, F; };\nstruct " + SC + " { " + Cx + " U, F; };\nstruct " + SGH + " { " + R +
              " g[" + std::to_string(S) + "], h[" + std::to_string(NP) + "]; };\n\n";
     }
-    auto head = [&](const char *kind, int s) {
-        const std::string n = std::to_string(s);
+    /* one function per sector, polynomial set and zeroed subset Y of the sector's singular variables (Y = 0: no
+       coordinate zeroed); the name carries both: <pre>_<kind>_<sector>_<Y> */
+    auto head = [&](const char *kind, int s, unsigned Y) {
+        const std::string n = std::to_string(s) + "_" + std::to_string(Y);
         const std::string C = "(const " + TT + " *__restrict__ C";
         if (!out_of_line) {
             if (!std::strcmp(kind, "ufr")) return "DEV void " + pre + "_ufr_" + n + C + ", const " + R + " *t, " + R + " &U, " + R + " &F) {\n";
@@ -263,79 +270,112 @@ std::string generate(const PackedHeader *h, const Lang &L) {
             return "__device__ __noinline__ " + SGH + " " + pre + "_gh_" + n + C + targs + ") {\n    const " + R + " t[] = {" + tvals + "};\n";
         return "__device__ __noinline__ " + SC + " " + pre + "_ufc_" + n + C + zargs + ") {\n    const " + Cx + " z[] = {" + zvals + "};\n";
     };
+    /* the zeroed subsets of a sector that get code of their own: every subset of its singular variables, except in
+       the FP32 code of undeformed sectors, where one function serves every subset (measured: the FP64 passes gain
+       10-12 % from leaving out the terms that vanish, the deformed FP32 class 8 %, while the undeformed FP32 class of
+       the four-pole double box, up to 16 subsets of small polynomials, loses 2 % to instruction fetch) */
+    auto per_subset = [&](int s) { return L.f64 || cls[s] == 1; };
+    auto subsets = [&](int s) {
+        std::vector<unsigned> out;
+        const unsigned mask = per_subset(s) ? (unsigned)ps[s].sing_mask : 0u;
+        unsigned Y = 0;
+        do {
+            out.push_back(Y);
+            Y = (Y - mask) & mask;
+        } while (Y != 0);
+        return out;
+    };
     for (int s = 0; s < h->n_sectors; ++s) {
         const PackedSector &p = ps[s];
         const PackedTermF *T = tf + p.term0;
-        if (cls[s] == 0) {
-            PolySet P;
-            P.S = S;
-            P.n_acc = 2;
-            for (int k = 0; k < p.nU; ++k) add_term(P, 0, k, T[k].e);
-            for (int k = 0; k < p.nF; ++k) add_term(P, 1, p.nU + k, T[p.nU + k].e);
-            o += head("ufr", s);
-            emit_body(o, L, P);
-            o += out_of_line ? "    return " + SR + "{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
-        } else if (cls[s] == 1) {
-            PolySet P;
-            P.S = S;
-            P.n_acc = S + NP;
-            const int bG = p.nU + p.nF, bH = bG + p.nG;
-            for (int j = 0; j < S; ++j)
-                for (int k = bG + p.gstart[j]; k < bG + p.gstart[j + 1]; ++k) add_term(P, j, k, T[k].e);
-            for (int q = 0; q < NP; ++q)
-                for (int k = bH + p.hstart[q]; k < bH + p.hstart[q + 1]; ++k) add_term(P, S + q, k, T[k].e);
-            o += head("gh", s);
-            emit_body(o, L, P);
-            const char *gv = out_of_line ? "    r.g[" : "    g[";
-            const char *hv = out_of_line ? "    r.h[" : "    h[";
-            if (out_of_line) o += "    " + SGH + " r;\n";
-            for (int j = 0; j < S; ++j) o += gv + std::to_string(j) + "] = a" + std::to_string(j) + ";\n";
-            for (int q = 0; q < NP; ++q) o += hv + std::to_string(q) + "] = a" + std::to_string(S + q) + ";\n";
-            o += out_of_line ? "    return r;\n}\n" : "}\n";
-            PolySet Q;
-            Q.S = S;
-            Q.complex_ = true;
-            Q.n_acc = 2;
-            for (int k = 0; k < p.nU; ++k) add_term(Q, 0, k, T[k].e);
-            for (int k = 0; k < p.nF; ++k) add_term(Q, 1, p.nU + k, T[p.nU + k].e);
-            o += head("ufc", s);
-            emit_body(o, L, Q);
-            o += out_of_line ? "    return " + SC + "{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+        for (const unsigned Y : subsets(s)) {
+            if (cls[s] == 0) {
+                PolySet P;
+                P.S = S;
+                P.n_acc = 2;
+                for (int k = 0; k < p.nU; ++k) add_term(P, 0, k, T[k].e, Y);
+                for (int k = 0; k < p.nF; ++k) add_term(P, 1, p.nU + k, T[p.nU + k].e, Y);
+                o += head("ufr", s, Y);
+                emit_body(o, L, P);
+                o += out_of_line ? "    return " + SR + "{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+            } else if (cls[s] == 1) {
+                PolySet P;
+                P.S = S;
+                P.n_acc = S + NP;
+                const int bG = p.nU + p.nF, bH = bG + p.nG;
+                for (int j = 0; j < S; ++j)
+                    for (int k = bG + p.gstart[j]; k < bG + p.gstart[j + 1]; ++k) add_term(P, j, k, T[k].e, Y);
+                for (int q = 0; q < NP; ++q)
+                    for (int k = bH + p.hstart[q]; k < bH + p.hstart[q + 1]; ++k) add_term(P, S + q, k, T[k].e, Y);
+                o += head("gh", s, Y);
+                emit_body(o, L, P);
+                const char *gv = out_of_line ? "    r.g[" : "    g[";
+                const char *hv = out_of_line ? "    r.h[" : "    h[";
+                if (out_of_line) o += "    " + SGH + " r;\n";
+                for (int j = 0; j < S; ++j) o += gv + std::to_string(j) + "] = a" + std::to_string(j) + ";\n";
+                for (int q = 0; q < NP; ++q) o += hv + std::to_string(q) + "] = a" + std::to_string(S + q) + ";\n";
+                o += out_of_line ? "    return r;\n}\n" : "}\n";
+                PolySet Q;
+                Q.S = S;
+                Q.complex_ = true;
+                Q.n_acc = 2;
+                for (int k = 0; k < p.nU; ++k) add_term(Q, 0, k, T[k].e, Y);
+                for (int k = 0; k < p.nF; ++k) add_term(Q, 1, p.nU + k, T[p.nU + k].e, Y);
+                o += head("ufc", s, Y);
+                emit_body(o, L, Q);
+                o += out_of_line ? "    return " + SC + "{a0, a1};\n}\n" : "    U = a0;\n    F = a1;\n}\n";
+            }
         }
     }
-    /* the evaluator: a warp-uniform switch over the packed sector index */
+    /* the evaluator: a warp-uniform switch over (packed sector index, zeroed subset) */
     const std::string Pol = L.pol;
     o += "\nstruct " + Pol + " {\n    const " + TT + " *T;\n    int sec;\n    DEV static " + Pol + " make(const " + TT +
          " *T, const PackedSector &, int psec) { return " + Pol + "{T, psec}; }\n";
-    o += "    DEV void UFr(const " + R + " *t, " + R + " &U, " + R + " &F) const {\n        switch (sec) {\n";
+    /* case labels: sector * 64 + Y; a sector with one function for all subsets gets the labels of every Y */
+    auto labels = [&](int s, unsigned Y) {
+        if (per_subset(s) || ps[s].sing_mask == 0) return "case " + std::to_string(s * 64 + (int)Y) + ":";
+        std::string out;
+        const unsigned mask = (unsigned)ps[s].sing_mask;
+        unsigned Z = 0;
+        do {
+            out += (out.empty() ? "case " : " case ") + std::to_string(s * 64 + (int)Z) + ":";
+            Z = (Z - mask) & mask;
+        } while (Z != 0);
+        return out;
+    };
+    const std::string sel = "sec * 64 + (int)Y";
+    o += "    DEV void UFr(unsigned Y, const " + R + " *t, " + R + " &U, " + R + " &F) const {\n        switch (" + sel + ") {\n";
     for (int s = 0; s < h->n_sectors; ++s)
-        if (cls[s] == 0) {
-            const std::string n = std::to_string(s);
-            o += out_of_line ? "        case " + n + ": { const " + SR + " r = " + pre + "_ufr_" + n + "(T" + tcall + "); U = r.U; F = r.F; return; }\n"
-                             : "        case " + n + ": " + pre + "_ufr_" + n + "(T, t, U, F); return;\n";
-        }
+        if (cls[s] == 0)
+            for (const unsigned Y : subsets(s)) {
+                const std::string n = std::to_string(s) + "_" + std::to_string(Y);
+                o += out_of_line ? "        " + labels(s, Y) + " { const " + SR + " r = " + pre + "_ufr_" + n + "(T" + tcall + "); U = r.U; F = r.F; return; }\n"
+                                 : "        " + labels(s, Y) + " " + pre + "_ufr_" + n + "(T, t, U, F); return;\n";
+            }
     o += "        default: U = 0; F = 0;\n        }\n    }\n";
-    o += "    DEV void GH(const " + R + " *t, " + R + " *g, " + R + " *h) const {\n        switch (sec) {\n";
+    o += "    DEV void GH(unsigned Y, const " + R + " *t, " + R + " *g, " + R + " *h) const {\n        switch (" + sel + ") {\n";
     for (int s = 0; s < h->n_sectors; ++s)
-        if (cls[s] == 1) {
-            const std::string n = std::to_string(s);
-            o += out_of_line ? "        case " + n + ": { const " + SGH + " r = " + pre + "_gh_" + n + "(T" + tcall +
-                                   "); for (int j = 0; j < " + std::to_string(S) + "; ++j) g[j] = r.g[j]; for (int q = 0; q < " +
-                                   std::to_string(NP) + "; ++q) h[q] = r.h[q]; return; }\n"
-                             : "        case " + n + ": " + pre + "_gh_" + n + "(T, t, g, h); return;\n";
-        }
+        if (cls[s] == 1)
+            for (const unsigned Y : subsets(s)) {
+                const std::string n = std::to_string(s) + "_" + std::to_string(Y);
+                o += out_of_line ? "        " + labels(s, Y) + " { const " + SGH + " r = " + pre + "_gh_" + n + "(T" + tcall +
+                                       "); for (int j = 0; j < " + std::to_string(S) + "; ++j) g[j] = r.g[j]; for (int q = 0; q < " +
+                                       std::to_string(NP) + "; ++q) h[q] = r.h[q]; return; }\n"
+                                 : "        " + labels(s, Y) + " " + pre + "_gh_" + n + "(T, t, g, h); return;\n";
+            }
     std::snprintf(b, sizeof(b),
                   "        default:\n            for (int j = 0; j < %d; ++j) g[j] = 0;\n"
                   "            for (int q = 0; q < %d; ++q) h[q] = 0;\n        }\n    }\n",
                   S, NP);
     o += b;
-    o += "    DEV void UFc(const " + Cx + " *z, bool, " + Cx + " &U, " + Cx + " &F) const {\n        switch (sec) {\n";
+    o += "    DEV void UFc(unsigned Y, const " + Cx + " *z, bool, " + Cx + " &U, " + Cx + " &F) const {\n        switch (" + sel + ") {\n";
     for (int s = 0; s < h->n_sectors; ++s)
-        if (cls[s] == 1) {
-            const std::string n = std::to_string(s);
-            o += out_of_line ? "        case " + n + ": { const " + SC + " r = " + pre + "_ufc_" + n + "(T" + zcall + "); U = r.U; F = r.F; return; }\n"
-                             : "        case " + n + ": " + pre + "_ufc_" + n + "(T, z, U, F); return;\n";
-        }
+        if (cls[s] == 1)
+            for (const unsigned Y : subsets(s)) {
+                const std::string n = std::to_string(s) + "_" + std::to_string(Y);
+                o += out_of_line ? "        " + labels(s, Y) + " { const " + SC + " r = " + pre + "_ufc_" + n + "(T" + zcall + "); U = r.U; F = r.F; return; }\n"
+                                 : "        " + labels(s, Y) + " " + pre + "_ufc_" + n + "(T, z, U, F); return;\n";
+            }
     o += std::string("        default: U = ") + L.mk + "(0, 0); F = " + L.mk + "(0, 0);\n        }\n    }\n};\n\n";
     for (int c = 0; c < QMC_N_CLASSES; ++c) {
         if (h->class_end[c] <= h->class_begin[c]) continue;

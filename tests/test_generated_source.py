@@ -94,32 +94,61 @@ def test_family_source_depends_on_structure_only():
     assert fa == fb and fa != fc and fa != 0
 
 
+def subsets(mask):
+    """every subset Y of the singular variables (bit mask), the zeroed coordinates of the endpoint subtraction"""
+    out, Y = [], 0
+    while True:
+        out.append(Y)
+        Y = (Y - mask) & mask
+        if Y == 0:
+            return out
+
+
+def own_subset(pre, h, k, Y):
+    """the zeroed subset whose function serves Y: every subset has its own, except in the FP32 code of undeformed
+    sectors (one function, Y = 0, evaluated with the zeroed coordinates)"""
+    return 0 if (pre == "qg" and h.class_begin[0] <= k < h.class_end[0]) else Y
+
+
+def vanishes(e, Y):
+    """a term with a positive power of a zeroed coordinate is zero on that face"""
+    return any(((Y >> j) & 1) and e[j] for j in range(len(e)))
+
+
 @pytest.mark.parametrize("cfg", W.CONFIGS, ids=lambda c: c.name)
 def test_every_term_enters_its_polynomial_once(cfg):
+    """Per sector and zeroed subset Y: every term that does not vanish at t_Y = 0 enters its own polynomial exactly
+    once, and no other term appears, in both precisions."""
     prep = prepared(cfg)
     h, secs, terms = image(prep)
-    src = api.gen_source(prep)
-    funcs = {}
-    for m in re.finditer(r"\b(qg_(?:ufr|gh|ufc)_(\d+))\(const PackedTermF[^{]*\{(.*?)\n\}", src, flags=re.S):
-        funcs[m.group(1)] = m.group(3)
+    for pre, precision, head in (("qg", N.QMC_PREC_MIXED, "const PackedTermF"), ("qd", N.QMC_PREC_FP64, "const PackedTerm")):
+        src = api.gen_source(prep, precision)
+        funcs = {}
+        for m in re.finditer(rf"\b({pre}_(?:ufr|gh|ufc)_(\d+)_(\d+))\({head}[^{{]*\{{(.*?)\n\}}", src, flags=re.S):
+            funcs[m.group(1)] = m.group(4)
+        check_terms(cfg, h, secs, terms, funcs, pre)
+
+
+def check_terms(cfg, h, secs, terms, funcs, pre):
     for k, s in enumerate(secs):
         U, F, G, H = blocks(h, s)
-        if h.class_begin[0] <= k < h.class_end[0]:
-            groups = {f"qg_ufr_{k}": [U, F]}
-        else:
-            groups = {f"qg_gh_{k}": G + H, f"qg_ufc_{k}": [U, F]}
-        for name, ranges in groups.items():
-            body = funcs[name]
-            # (accumulator, term) of every statement that adds a term; a complex FMA writes .x and .y
-            pairs = re.findall(r"a(\d+)(?:\.[xy])? (?:=|\+=) (?:fmaf\(|cfma2f\()?C\[(\d+)\]\.hi", body)
-            got = {}
-            for acc, term in pairs:
-                got.setdefault(int(term), set()).add(int(acc))
-            want = {i: {a} for a, (lo, hi) in enumerate(ranges) for i in range(lo, hi)}
-            assert got == want, (cfg.name, name)
-            n_stmt = len(pairs)
-            n_expected = len(want)
-            assert n_stmt == n_expected, (cfg.name, name)
+        e = terms[s.term0: s.term0 + s.n_terms]["e"]
+        for Y in sorted({own_subset(pre, h, k, Y) for Y in subsets(s.sing_mask)}):
+            if h.class_begin[0] <= k < h.class_end[0]:
+                groups = {f"{pre}_ufr_{k}_{Y}": [U, F]}
+            else:
+                groups = {f"{pre}_gh_{k}_{Y}": G + H, f"{pre}_ufc_{k}_{Y}": [U, F]}
+            for name, ranges in groups.items():
+                body = funcs[name]
+                # (accumulator, term) of every statement that adds a term; a complex term is one packed FMA (FP32)
+                # or a statement on .x followed by one on .y (FP64)
+                pairs = re.findall(r"a(\d+)(?:\.x)? (?:=|\+=) (?:fmaf?\(|cfma2f\()?C\[(\d+)\]", body)
+                got = {}
+                for acc, term in pairs:
+                    got.setdefault(int(term), set()).add(int(acc))
+                want = {i: {a} for a, (lo, hi) in enumerate(ranges) for i in range(lo, hi) if not vanishes(e[i], Y)}
+                assert got == want, (cfg.name, name)
+                assert len(pairs) == len(want), (cfg.name, name)
 
 
 SHIM = r"""
@@ -138,34 +167,45 @@ struct PackedTermF { float hi, lo; unsigned char e[8]; };
 """
 
 
-def host_harness(src, h, secs):
-    """C++ source: the generated per-sector functions plus extern "C" entry points taking arrays"""
-    i0 = src.index('#include "qmc_dev.cuh"') + len('#include "qmc_dev.cuh"')
-    body = src[i0:src.index("struct QgPol")]
+def dispatch(h, secs, pre, R, Cx, term, ool):
+    """extern "C" entry points h_ufr / h_gh / h_ufc(sector, Y, C, ...) switching over (sector, zeroed subset); ool:
+    the source holds out-of-line functions with by-value results (large families), else inlined void functions."""
     S = h.dim
     NP = S * (S + 1) // 2
-    ool = "struct QgGH" in body
-    out = [SHIM, body]
-    ufr, gh, ufc = [], [], []
     ta = ", ".join(f"t[{j}]" for j in range(S))
     za = ", ".join(f"z[{j}].x, z[{j}].y" for j in range(S))
+    Rr, GH, Cc = ("QgR", "QgGH", "QgC") if pre == "qg" else ("QdR", "QdGH", "QdC")
+    ufr, gh, ufc = [], [], []
     for k in range(h.n_sectors):
-        if h.class_begin[0] <= k < h.class_end[0]:
-            ufr.append(f"case {k}: {{ QgR r = qg_ufr_{k}(C, {ta}); U[0] = r.U; U[1] = r.F; return; }}" if ool else
-                       f"case {k}: qg_ufr_{k}(C, t, U[0], U[1]); return;")
-        else:
-            gh.append(f"case {k}: {{ QgGH r = qg_gh_{k}(C, {ta}); for (int j = 0; j < {S}; ++j) g[j] = r.g[j]; "
-                      f"for (int q = 0; q < {NP}; ++q) hh[q] = r.h[q]; return; }}" if ool else
-                      f"case {k}: qg_gh_{k}(C, t, g, hh); return;")
-            ufc.append(f"case {k}: {{ QgC r = qg_ufc_{k}(C, {za}); UF[0] = r.U; UF[1] = r.F; return; }}" if ool else
-                       f"case {k}: qg_ufc_{k}(C, z, UF[0], UF[1]); return;")
-    out.append('extern "C" void h_ufr(int s, const PackedTermF *C, const float *t, float *U) { switch (s) { '
-               + " ".join(ufr) + " } }")
-    out.append('extern "C" void h_gh(int s, const PackedTermF *C, const float *t, float *g, float *hh) { switch (s) { '
-               + " ".join(gh) + " } }")
-    out.append('extern "C" void h_ufc(int s, const PackedTermF *C, const cf *z, cf *UF) { switch (s) { '
-               + " ".join(ufc) + " } }")
-    return "\n".join(out)
+        for Y in subsets(secs[k].sing_mask):
+            n, lab = f"{k}_{own_subset(pre, h, k, Y)}", k * 64 + Y
+            if h.class_begin[0] <= k < h.class_end[0]:
+                ufr.append(f"case {lab}: {{ {Rr} r = {pre}_ufr_{n}(C, {ta}); U[0] = r.U; U[1] = r.F; return; }}"
+                           if ool else f"case {lab}: {pre}_ufr_{n}(C, t, U[0], U[1]); return;")
+            else:
+                gh.append(f"case {lab}: {{ {GH} r = {pre}_gh_{n}(C, {ta}); for (int j = 0; j < {S}; ++j) g[j] = "
+                          f"r.g[j]; for (int q = 0; q < {NP}; ++q) hh[q] = r.h[q]; return; }}"
+                          if ool else f"case {lab}: {pre}_gh_{n}(C, t, g, hh); return;")
+                ufc.append(f"case {lab}: {{ {Cc} r = {pre}_ufc_{n}(C, {za}); UF[0] = r.U; UF[1] = r.F; return; }}"
+                           if ool else f"case {lab}: {pre}_ufc_{n}(C, z, UF[0], UF[1]); return;")
+    return [f'extern "C" void h_ufr(int s, int Y, const {term} *C, const {R} *t, {R} *U) {{ switch (s * 64 + Y) {{ '
+            + " ".join(ufr) + " } }",
+            f'extern "C" void h_gh(int s, int Y, const {term} *C, const {R} *t, {R} *g, {R} *hh) {{ '
+            f'switch (s * 64 + Y) {{ ' + " ".join(gh) + " } }",
+            f'extern "C" void h_ufc(int s, int Y, const {term} *C, const {Cx} *z, {Cx} *UF) {{ switch (s * 64 + Y) {{ '
+            + " ".join(ufc) + " } }"]
+
+
+def generated_body(src, pol):
+    """the generated per-sector functions (everything between the include and the evaluator struct)"""
+    i0 = src.index('#include "qmc_dev.cuh"') + len('#include "qmc_dev.cuh"')
+    return src[i0:src.index(f"struct {pol}")]
+
+
+def host_harness(src, h, secs):
+    """C++ source: the generated per-sector functions plus extern "C" entry points taking arrays"""
+    body = generated_body(src, "QgPol")
+    return "\n".join([SHIM, body] + dispatch(h, secs, "qg", "float", "cf", "PackedTermF", "struct QgGH" in body))
 
 
 def poly_value(terms, lo, hi, x):
@@ -184,6 +224,8 @@ def poly_value(terms, lo, hi, x):
 
 @pytest.mark.parametrize("cfg", [W.CONFIG0, W.CONFIG1, W.CONFIG2], ids=lambda c: c.name)
 def test_generated_functions_evaluate_the_table_polynomials(cfg):
+    """Each generated FP32 function (per sector and zeroed subset) against the table's terms summed in FP64 at a
+    random point with the subset's coordinates zero."""
     prep = prepared(cfg)
     h, secs, terms = image(prep)
     src = api.gen_source(prep)
@@ -202,29 +244,33 @@ def test_generated_functions_evaluate_the_table_polynomials(cfg):
         T_s = np.ascontiguousarray(terms[s.term0: s.term0 + s.n_terms])
         Cp = T_s.ctypes.data_as(ctypes.c_void_p)
         U, F, G, H = blocks(h, s)
-        for _ in range(3):
+        for Y in subsets(s.sing_mask):
             t = rng.uniform(0.0, 1.0, S).astype(np.float32)
+            t[[j for j in range(S) if (Y >> j) & 1]] = 0.0
             tp = t.ctypes.data_as(fptr)
             if h.class_begin[0] <= k < h.class_end[0]:
                 outv = np.zeros(2, np.float32)
-                L.h_ufr(k, Cp, tp, outv.ctypes.data_as(fptr))
+                L.h_ufr(k, Y, Cp, tp, outv.ctypes.data_as(fptr))
                 refs = [poly_value(T_s, *U, t.astype(np.float64)), poly_value(T_s, *F, t.astype(np.float64))]
                 got = list(outv)
             else:
                 g = np.zeros(S, np.float32)
                 hh = np.zeros(NP, np.float32)
-                L.h_gh(k, Cp, tp, g.ctypes.data_as(fptr), hh.ctypes.data_as(fptr))
+                L.h_gh(k, Y, Cp, tp, g.ctypes.data_as(fptr), hh.ctypes.data_as(fptr))
                 refs = [poly_value(T_s, lo, hi, t.astype(np.float64)) for lo, hi in G + H]
                 got = list(g) + list(hh)
                 zc = (t * (1 - 0.3j * rng.uniform(0, 1, S))).astype(np.complex64)
                 zf = np.ascontiguousarray(np.stack([zc.real, zc.imag], -1).astype(np.float32))
                 uf = np.zeros(4, np.float32)
-                L.h_ufc(k, Cp, zf.ctypes.data_as(fptr), uf.ctypes.data_as(fptr))
+                L.h_ufc(k, Y, Cp, zf.ctypes.data_as(fptr), uf.ctypes.data_as(fptr))
                 z64 = zc.astype(np.complex128)
                 refs += [poly_value(T_s, *U, z64), poly_value(T_s, *F, z64)]
                 got += [complex(uf[0], uf[1]), complex(uf[2], uf[3])]
             for (rv, mag), gv in zip(refs, got):
-                err = abs(complex(gv) - rv) / max(mag, 1e-30)
+                if mag == 0.0:
+                    assert gv == 0, (k, Y)  # every term vanishes on this face
+                    continue
+                err = abs(complex(gv) - rv) / mag
                 worst = max(worst, err)
     print(f"{cfg.name}: worst |generated FP32 - table FP64| / sum|terms| = {worst:.2e}")
     assert worst < 2e-6
@@ -243,33 +289,9 @@ struct PackedTerm { double c; unsigned char e[8]; };
 """
 
 
-def host_harness64(src, h):
-    i0 = src.index('#include "qmc_dev.cuh"') + len('#include "qmc_dev.cuh"')
-    body = src[i0:src.index("struct QdPol")]
-    S = h.dim
-    NP = S * (S + 1) // 2
-    ool = "struct QdGH" in body
-    out = [SHIM64, body]
-    ufr, gh, ufc = [], [], []
-    ta = ", ".join(f"t[{j}]" for j in range(S))
-    za = ", ".join(f"z[{j}].x, z[{j}].y" for j in range(S))
-    for k in range(h.n_sectors):
-        if h.class_begin[0] <= k < h.class_end[0]:
-            ufr.append(f"case {k}: {{ QdR r = qd_ufr_{k}(C, {ta}); U[0] = r.U; U[1] = r.F; return; }}" if ool else
-                       f"case {k}: qd_ufr_{k}(C, t, U[0], U[1]); return;")
-        else:
-            gh.append(f"case {k}: {{ QdGH r = qd_gh_{k}(C, {ta}); for (int j = 0; j < {S}; ++j) g[j] = r.g[j]; "
-                      f"for (int q = 0; q < {NP}; ++q) hh[q] = r.h[q]; return; }}" if ool else
-                      f"case {k}: qd_gh_{k}(C, t, g, hh); return;")
-            ufc.append(f"case {k}: {{ QdC r = qd_ufc_{k}(C, {za}); UF[0] = r.U; UF[1] = r.F; return; }}" if ool else
-                       f"case {k}: qd_ufc_{k}(C, z, UF[0], UF[1]); return;")
-    out.append('extern "C" void h_ufr(int s, const PackedTerm *C, const double *t, double *U) { switch (s) { '
-               + " ".join(ufr) + " } }")
-    out.append('extern "C" void h_gh(int s, const PackedTerm *C, const double *t, double *g, double *hh) { switch (s) { '
-               + " ".join(gh) + " } }")
-    out.append('extern "C" void h_ufc(int s, const PackedTerm *C, const cd *z, cd *UF) { switch (s) { '
-               + " ".join(ufc) + " } }")
-    return "\n".join(out)
+def host_harness64(src, h, secs):
+    body = generated_body(src, "QdPol")
+    return "\n".join([SHIM64, body] + dispatch(h, secs, "qd", "double", "cd", "PackedTerm", "struct QdGH" in body))
 
 
 TERM_D = np.dtype([("c", "<f8"), ("e", "u1", (8,))])
@@ -284,7 +306,7 @@ def test_generated_fp64_functions_evaluate_the_table_polynomials(cfg):
     os.makedirs(WORK, exist_ok=True)
     cpp = os.path.join(WORK, f"gen64_{cfg.name}.cpp")
     so = os.path.join(WORK, f"gen64_{cfg.name}.so")
-    open(cpp, "w").write(host_harness64(src, h))
+    open(cpp, "w").write(host_harness64(src, h, secs))
     subprocess.check_call(["g++", "-O1", "-ffp-contract=off", "-shared", "-fPIC", "-o", so, cpp])
     L = ctypes.CDLL(so)
     S = h.dim
@@ -307,26 +329,31 @@ def test_generated_fp64_functions_evaluate_the_table_polynomials(cfg):
         T_s = np.ascontiguousarray(terms[s.term0: s.term0 + s.n_terms])
         Cp = T_s.ctypes.data_as(ctypes.c_void_p)
         U, F, G, H = blocks(h, s)
-        t = rng.uniform(0.0, 1.0, S)
-        tp = t.ctypes.data_as(dptr)
-        if h.class_begin[0] <= k < h.class_end[0]:
-            outv = np.zeros(2)
-            L.h_ufr(k, Cp, tp, outv.ctypes.data_as(dptr))
-            refs, got = [ref(T_s, *U, t), ref(T_s, *F, t)], list(outv)
-        else:
-            g = np.zeros(S)
-            hh = np.zeros(NP)
-            L.h_gh(k, Cp, tp, g.ctypes.data_as(dptr), hh.ctypes.data_as(dptr))
-            refs = [ref(T_s, lo, hi, t) for lo, hi in G + H]
-            got = list(g) + list(hh)
-            zc = t * (1 - 0.3j * rng.uniform(0, 1, S))
-            zf = np.ascontiguousarray(np.stack([zc.real, zc.imag], -1))
-            uf = np.zeros(4)
-            L.h_ufc(k, Cp, zf.ctypes.data_as(dptr), uf.ctypes.data_as(dptr))
-            refs += [ref(T_s, *U, zc), ref(T_s, *F, zc)]
-            got += [complex(uf[0], uf[1]), complex(uf[2], uf[3])]
-        for (rv, mag), gv in zip(refs, got):
-            worst = max(worst, abs(complex(gv) - rv) / max(mag, 1e-300))
+        for Y in subsets(s.sing_mask):
+            t = rng.uniform(0.0, 1.0, S)
+            t[[j for j in range(S) if (Y >> j) & 1]] = 0.0
+            tp = t.ctypes.data_as(dptr)
+            if h.class_begin[0] <= k < h.class_end[0]:
+                outv = np.zeros(2)
+                L.h_ufr(k, Y, Cp, tp, outv.ctypes.data_as(dptr))
+                refs, got = [ref(T_s, *U, t), ref(T_s, *F, t)], list(outv)
+            else:
+                g = np.zeros(S)
+                hh = np.zeros(NP)
+                L.h_gh(k, Y, Cp, tp, g.ctypes.data_as(dptr), hh.ctypes.data_as(dptr))
+                refs = [ref(T_s, lo, hi, t) for lo, hi in G + H]
+                got = list(g) + list(hh)
+                zc = t * (1 - 0.3j * rng.uniform(0, 1, S))
+                zf = np.ascontiguousarray(np.stack([zc.real, zc.imag], -1))
+                uf = np.zeros(4)
+                L.h_ufc(k, Y, Cp, zf.ctypes.data_as(dptr), uf.ctypes.data_as(dptr))
+                refs += [ref(T_s, *U, zc), ref(T_s, *F, zc)]
+                got += [complex(uf[0], uf[1]), complex(uf[2], uf[3])]
+            for (rv, mag), gv in zip(refs, got):
+                if mag == 0.0:
+                    assert gv == 0, (k, Y)
+                    continue
+                worst = max(worst, abs(complex(gv) - rv) / mag)
     print(f"{cfg.name}: worst |generated FP64 - table| / sum|terms| = {worst:.2e}")
     assert worst < 1e-14
 
