@@ -682,8 +682,10 @@ DEV cf cmulf(cf a, cf b) {
 DEV cf cfma2f(float hi, float lo, cf m, cf a) {
     return cf_(__ffma2_rn(make_float2(hi, hi), f2_(m), __ffma2_rn(make_float2(lo, lo), f2_(m), f2_(a))));
 }
+/* the reciprocal of the squared modulus from the fast approximate division (2 ulp): the FP32 path's error is set by
+   its rounding of products and sums, and an IEEE-rounded reciprocal costs several instructions more */
 DEV cf cinvf(cf a) {
-    const float d = __frcp_rn(fmaf(a.x, a.x, a.y * a.y));
+    const float d = __fdividef(1.f, fmaf(a.x, a.x, a.y * a.y));
     return cf{a.x * d, -a.y * d};
 }
 DEV cf cipowf(cf z, int e) {
@@ -956,7 +958,10 @@ DEV void eval_G_f(const PackedSector &s, const Pol &P, unsigned Y, const float *
         if constexpr (S >= 4) {
             float s[S];
 #pragma unroll
-            for (int j = 0; j < S; ++j) s[j] = sqrtf(tt[j] * ttm[j]);
+            for (int j = 0; j < S; ++j) {
+                const float pj = tt[j] * ttm[j];
+                s[j] = pj > 0.f ? pj * rsqrtf(pj) : 0.f;
+            }
             cf N[S * (S + 1) / 2];
             int p = 0;
 #pragma unroll
@@ -1015,13 +1020,19 @@ DEV void eval_G_f(const PackedSector &s, const Pol &P, unsigned Y, const float *
         X = mkf(0.f, 0.f);
         if (MAXM > 0 && M > 0) {
             cf x = csubf(cscalef(clogf_p(U), (float)ex.eU1), cscalef(clogf_mi0(F), (float)ex.eF1));
+            /* log q_j with q_j = 1 - i d_j: (log(1 + d_j^2) / 2, -atan d_j) */
+            float lr = 0.f;
 #pragma unroll
             for (int j = 0; j < S; ++j) {
                 if (s.B[j] != 0) {
-                    if (s.A[j] != -1) x.x = fmaf((float)s.B[j], Lt[j], x.x);
-                    x = caddf(x, cscalef(clogf_p(q[j]), (float)s.B[j]));
+                    const float Bj = (float)s.B[j];
+                    if (s.A[j] != -1) x.x = fmaf(Bj, Lt[j], x.x);
+                    const float d = -q[j].y;
+                    lr = fmaf(Bj, __logf(fmaf(d, d, 1.f)), lr);
+                    x.y = fmaf(-Bj, atanf(d), x.y);
                 }
             }
+            x.x = fmaf(0.5f, lr, x.x);
             X = x;
         }
     }
@@ -1073,8 +1084,8 @@ DEV void point_integrand_f(const PackedSector &s, const Pol &P, const float *x, 
                 const bool inY = (Y >> j) & 1u;
                 const float Bj = (float)s.B[j];
                 float f[MAXM + 1];
-                f[0] = inY ? 1.f / Bj : 0.f;
-                float c = __frcp_rn(t[j]);
+                f[0] = inY ? __fdividef(1.f, Bj) : 0.f;
+                float c = __fdividef(1.f, t[j]);
 #pragma unroll
                 for (int n = 1; n <= MAXM; ++n) {
                     f[n] = inY ? -c : c;
@@ -1263,6 +1274,470 @@ DEV void eval_f32_body(const JobTable &jt) {
 template <int S, bool DEF, int MAXM>
 __global__ void __launch_bounds__(256) qmc_eval_kernel_f32(const __grid_constant__ JobTable jt) {
     eval_f32_body<S, DEF, MAXM, TabPolF<S>>(jt);
+}
+
+/* ================================================================== FP32 path, two lattice points per thread
+ * The generated evaluators of the mixed pass evaluate two lattice points per thread, one in each lane of GB300's
+ * packed FP32 instructions (__ffma2_rn, __fmul2_rn, __fadd2_rn): every arithmetic step of the per-point code is
+ * issued once for both points, the staged coefficients are read once for both, and the control flow of the
+ * subtraction subsets is shared.  Each lane rounds exactly as the scalar code of the one-point path does, so a
+ * lane's value equals that path's value for its point.  Steps without a packed form run per lane with the scalar
+ * code: the transcendentals, the reciprocals and the elimination of the deformation determinant (which would
+ * need twice the registers in packed form).
+ * Coefficients are staged as (hi, hi, lo, lo): one 128-bit shared load gives both packed operands of a term. */
+DEV float2 bc2(float v) { return make_float2(v, v); }
+DEV float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+DEV float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+DEV float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+DEV float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+DEV float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+DEV float lane(float2 v, int k) { return k ? v.y : v.x; }
+
+/* two complex numbers: lane a = (re.x, im.x), lane b = (re.y, im.y) */
+struct c2 {
+    float2 re, im;
+};
+DEV c2 mkc2(float2 re, float2 im) { return c2{re, im}; }
+DEV c2 zero_c2() { return c2{bc2(0.f), bc2(0.f)}; }
+DEV c2 cadd2(c2 a, c2 b) { return c2{add2(a.re, b.re), add2(a.im, b.im)}; }
+DEV c2 csub2(c2 a, c2 b) { return c2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+DEV c2 cscale2(c2 a, float2 s) { return c2{mul2(a.re, s), mul2(a.im, s)}; }
+/* as cmulf per lane: (fma(a.re, b.re, rn(-a.im b.im)), fma(a.re, b.im, rn(a.im b.re))) */
+DEV c2 cmul2(c2 a, c2 b) { return c2{fma2(a.re, b.re, neg2(mul2(a.im, b.im))), fma2(a.re, b.im, mul2(a.im, b.re))}; }
+/* a + (hi + lo) m for a staged coefficient (hi, hi, lo, lo), as cfma2f per lane */
+DEV c2 cfma2c(const float4 &c, c2 m, c2 a) {
+    const float2 h = make_float2(c.x, c.y), l = make_float2(c.z, c.w);
+    return c2{fma2(h, m.re, fma2(l, m.re, a.re)), fma2(h, m.im, fma2(l, m.im, a.im))};
+}
+/* a + hi m, real (coefficients that only shape the contour deformation) */
+DEV float2 rfma2h(const float4 &c, float2 m, float2 a) { return fma2(make_float2(c.x, c.y), m, a); }
+/* a + (hi + lo) m, real */
+DEV float2 rfma2c(const float4 &c, float2 m, float2 a) {
+    return fma2(make_float2(c.x, c.y), m, fma2(make_float2(c.z, c.w), m, a));
+}
+DEV cf lane_c(c2 v, int k) { return cf{lane(v.re, k), lane(v.im, k)}; }
+DEV c2 join_c(cf a, cf b) { return c2{make_float2(a.x, b.x), make_float2(a.y, b.y)}; }
+DEV c2 cinv2(c2 a) {
+    const float2 d2 = fma2(a.re, a.re, mul2(a.im, a.im));
+    const float2 d = make_float2(__fdividef(1.f, d2.x), __fdividef(1.f, d2.y));
+    return c2{mul2(a.re, d), neg2(mul2(a.im, d))};
+}
+DEV c2 cipow2(c2 z, int e) {
+    c2 r = c2{bc2(1.f), bc2(0.f)};
+    int k = e < 0 ? -e : e;
+    for (int i = 0; i < k; ++i) r = cmul2(r, z);
+    return e < 0 ? cinv2(r) : r;
+}
+DEV float2 ipow2(float2 v, int e) {
+    float2 r = bc2(1.f);
+    int k = e < 0 ? -e : e;
+    for (int i = 0; i < k; ++i) r = mul2(r, v);
+    return e < 0 ? make_float2(__frcp_rn(r.x), __frcp_rn(r.y)) : r;
+}
+
+/* the periodising transform of both points (transform_f per lane) */
+DEV void transform2(int r, float2 x, float2 y, float2 &t, float2 &tm, float2 &w) {
+    const bool la = x.x <= y.x, lb = x.y <= y.y;
+    const float2 u = make_float2(la ? x.x : y.x, lb ? x.y : y.y);
+    float2 p;
+    switch (r) {
+        case 0: p = u; break;
+        case 1: p = mul2(mul2(u, u), fma2(bc2(-2.f), u, bc2(3.f))); break;
+        case 2: p = mul2(mul2(mul2(u, u), u), fma2(u, fma2(bc2(6.f), u, bc2(-15.f)), bc2(10.f))); break;
+        default: {
+            const float2 u2 = mul2(u, u);
+            p = mul2(mul2(u2, u2), fma2(u, fma2(u, fma2(bc2(-20.f), u, bc2(70.f)), bc2(-84.f)), bc2(35.f)));
+        }
+    }
+    const float2 q = sub2(bc2(1.f), p);
+    t = make_float2(la ? p.x : q.x, lb ? p.y : q.y);
+    tm = make_float2(la ? q.x : p.x, lb ? q.y : p.y);
+    const float2 xy = mul2(x, y);
+    switch (r) {
+        case 0: w = bc2(1.f); break;
+        case 1: w = mul2(bc2(6.f), xy); break;
+        case 2: w = mul2(mul2(bc2(30.f), xy), xy); break;
+        default: w = mul2(mul2(mul2(bc2(140.f), xy), xy), xy); break;
+    }
+}
+
+/* G at the points tt of both lanes (eval_G_f per lane): its eps^0 value G0 and the eps-coefficient X of its
+   logarithm.  live: lanes whose point is evaluated (a sign failure is counted only there). */
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void eval_G_f2(const PackedSector &s, const Pol &P, unsigned Y, const float2 *tt, const float2 *ttm,
+                   const float2 *Lt, float lam, int M, const Exps &ex, const bool (&live)[2], c2 &G0, c2 &X,
+                   uint32_t &fails) {
+    const float2 D = bc2(s.Df);
+    if constexpr (!DEF) {
+        float2 U, F;
+        P.UFr(Y, tt, U, F);
+        if (s.kind == 1) F = neg2(F);
+        float2 g = mul2(mul2(D, ipow2(U, ex.eU0)), ipow2(F, -ex.eF0));
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < s.A[j]; ++k) g = mul2(g, tt[j]);
+        G0 = c2{g, bc2(0.f)};
+        X = zero_c2();
+        if (MAXM > 0 && M > 0) {
+            const float2 a = mul2(ipow2(U, ex.eU1), ipow2(F, -ex.eF1));
+            float2 x = make_float2(__logf(a.x), __logf(a.y));
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+                if (s.A[j] != -1 && s.B[j] != 0) x = fma2(bc2((float)s.B[j]), Lt[j], x);
+            X = c2{x, bc2(0.f)};
+        }
+    } else {
+        float2 g[S], h[S * (S + 1) / 2];
+        P.GH(Y, tt, g, h);
+        cf dets[2];
+#pragma unroll 1
+        for (int k = 0; k < 2; ++k) {
+            /* the determinant per lane, as eval_G_f computes it (one lane at a time: registers) */
+            if constexpr (S >= 4) {
+                float sq[S];
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    const float pj = lane(tt[j], k) * lane(ttm[j], k);
+                    sq[j] = pj > 0.f ? pj * rsqrtf(pj) : 0.f;
+                }
+                cf N[S * (S + 1) / 2];
+                int p = 0;
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+#pragma unroll
+                    for (int i = j; i < S; ++i) {
+                        const float tj = lane(tt[j], k), mj = lane(ttm[j], k);
+                        const float b = (i == j) ? fmaf(mj - tj, lane(g[j], k), tj * mj * lane(h[p], k))
+                                                 : sq[j] * sq[i] * lane(h[p], k);
+                        N[p] = mkf(i == j ? 1.f : 0.f, -lam * b);
+                        ++p;
+                    }
+                }
+                dets[k] = det_sym_f<S>(N);
+            } else {
+                float A[S][S];
+                int p = 0;
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+#pragma unroll
+                    for (int i = j; i < S; ++i) {
+                        A[j][i] = lane(tt[j], k) * lane(ttm[j], k) * lane(h[p], k);
+                        if (i != j) A[i][j] = lane(tt[i], k) * lane(ttm[i], k) * lane(h[p], k);
+                        ++p;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < S; ++j)
+                    A[j][j] = fmaf(lane(ttm[j], k) - lane(tt[j], k), lane(g[j], k), A[j][j]);
+                dets[k] = det_deform_f<S>(A, lam);
+            }
+        }
+        const c2 detJ = join_c(dets[0], dets[1]);
+        c2 z[S], q[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const float2 d = mul2(mul2(bc2(lam), ttm[j]), g[j]);
+            z[j] = c2{tt[j], neg2(mul2(tt[j], d))};
+            q[j] = c2{bc2(1.f), neg2(d)};
+        }
+        const bool needU = ex.eU0 != 0 || (MAXM > 0 && M > 0);
+        c2 U, F;
+        P.UFc(Y, z, needU, U, F);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float fr = lane(F.re, k), fi = lane(F.im, k);
+            fails += (live[k] && fi > QMC_F32_SIGN_NOISE * (fabsf(fr) + fabsf(fi))) ? 1u : 0u;
+        }
+        c2 G = cscale2(detJ, D);
+        if (ex.eU0 != 0) G = cmul2(G, cipow2(U, ex.eU0));
+        G = cmul2(G, cipow2(F, -ex.eF0));
+        bool any_mono = false;
+        float2 mono = bc2(1.f);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            for (int k = 0; k < s.A[j]; ++k) {
+                mono = mul2(mono, tt[j]);
+                any_mono = true;
+            }
+        if (any_mono) G = cscale2(G, mono);
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (s.A[j] != 0) G = cmul2(G, cipow2(q[j], s.A[j]));
+        G0 = G;
+        X = zero_c2();
+        if (MAXM > 0 && M > 0) {
+            cf xs[2];
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                cf x = csubf(cscalef(clogf_p(lane_c(U, k)), (float)ex.eU1), cscalef(clogf_mi0(lane_c(F, k)), (float)ex.eF1));
+                float lr = 0.f;
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    if (s.B[j] != 0) {
+                        const float Bj = (float)s.B[j];
+                        if (s.A[j] != -1) x.x = fmaf(Bj, lane(Lt[j], k), x.x);
+                        const float d = -lane(q[j].im, k);
+                        lr = fmaf(Bj, __logf(fmaf(d, d, 1.f)), lr);
+                        x.y = fmaf(-Bj, atanf(d), x.y);
+                    }
+                }
+                x.x = fmaf(0.5f, lr, x.x);
+                xs[k] = x;
+            }
+            X = join_c(xs[0], xs[1]);
+        }
+    }
+}
+
+/* w(x) * (sector integrand) at the points (x, y = 1 - x) of both lanes, as point_integrand_f per lane; live[k]:
+   lane k holds a lattice point (its value is zero otherwise) */
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void point_integrand_f2(const PackedSector &s, const Pol &P, const float2 *x, const float2 *y, int r, float lam,
+                            const Exps &ex, bool (&live)[2], c2 (&out)[MAXM + 1], uint32_t &fails) {
+    float2 t[S], tm[S], w = bc2(1.f);
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        float2 wj;
+        transform2(r, x[j], y[j], t[j], tm[j], wj);
+        w = mul2(w, wj);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        bool bad = !(lane(w, k) > 0.f);
+#pragma unroll
+        for (int j = 0; j < S; ++j) bad |= !(lane(t[j], k) > 0.f) || !(lane(tm[j], k) > 0.f);
+        live[k] = live[k] && !bad;
+    }
+#pragma unroll
+    for (int n = 0; n <= MAXM; ++n) out[n] = zero_c2();
+    if (!live[0] && !live[1]) return;
+    /* a lane without a point evaluates the other lane's point; its value is discarded */
+    if (!live[0] || !live[1]) {
+        const int from = live[0] ? 0 : 1;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            t[j] = bc2(lane(t[j], from));
+            tm[j] = bc2(lane(tm[j], from));
+        }
+        w = bc2(lane(w, from));
+    }
+    const int M = s.M;
+    const unsigned smask = (unsigned)s.sing_mask;
+    float2 Lt[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) Lt[j] = bc2(0.f);
+    if (MAXM > 0 && M > 0) {
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+            if (((smask >> j) & 1u) || s.B[j] != 0) Lt[j] = make_float2(__logf(t[j].x), __logf(t[j].y));
+    }
+    unsigned Y = 0;
+    do {
+        float2 tt[S], ttm[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const bool zj = (Y >> j) & 1u;
+            tt[j] = zj ? bc2(0.f) : t[j];
+            ttm[j] = zj ? bc2(1.f) : tm[j];
+        }
+        c2 G0, X;
+        eval_G_f2<S, DEF, MAXM>(s, P, Y, tt, ttm, Lt, lam, M, ex, live, G0, X, fails);
+        float2 V[MAXM + 1];
+        V[0] = bc2(1.f);
+#pragma unroll
+        for (int n = 1; n <= MAXM; ++n) V[n] = bc2(0.f);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            if ((smask >> j) & 1u) {
+                const bool inY = (Y >> j) & 1u;
+                const float Bj = (float)s.B[j];
+                float2 f[MAXM + 1];
+                f[0] = bc2(inY ? __fdividef(1.f, Bj) : 0.f);
+                float2 c = make_float2(__fdividef(1.f, t[j].x), __fdividef(1.f, t[j].y));
+#pragma unroll
+                for (int n = 1; n <= MAXM; ++n) {
+                    f[n] = inY ? neg2(c) : c;
+                    /* c *= B_j Lt_j / n, per lane as the one-point code */
+                    c = make_float2(c.x * (Bj * Lt[j].x / n), c.y * (Bj * Lt[j].y / n));
+                }
+#pragma unroll
+                for (int n = MAXM; n >= 0; --n) {
+                    float2 acc = bc2(0.f);
+#pragma unroll
+                    for (int k = 0; k <= n; ++k) acc = fma2(V[k], f[n - k], acc);
+                    V[n] = acc;
+                }
+            }
+        }
+        c2 g = G0;
+#pragma unroll
+        for (int n = 0; n <= MAXM; ++n) {
+            if (n <= M) {
+#pragma unroll
+                for (int k = 0; k + n <= MAXM; ++k)
+                    if (n + k <= M) out[n + k] = cadd2(out[n + k], cscale2(g, V[k]));
+                g = cscale2(cmul2(g, X), bc2(1.f / (n + 1)));
+            }
+        }
+        Y = (Y - smask) & smask;
+    } while (Y != 0);
+#pragma unroll
+    for (int n = 0; n <= MAXM; ++n) {
+        out[n] = cscale2(out[n], w);
+        if (!live[0]) out[n] = c2{make_float2(0.f, out[n].re.y), make_float2(0.f, out[n].im.y)};
+        if (!live[1]) out[n] = c2{make_float2(out[n].re.x, 0.f), make_float2(out[n].im.x, 0.f)};
+    }
+}
+
+/* stage a sector for the two-point path: the record, then each term's coefficient as (hi, hi, lo, lo) */
+DEV void stage_sector_f2(const unsigned char *packed, int64_t sectors_off, int64_t termsf_off, int psec,
+                         unsigned char *smem) {
+    const PackedSector *ps = reinterpret_cast<const PackedSector *>(packed + sectors_off) + psec;
+    const int4 *src = reinterpret_cast<const int4 *>(ps);
+    int4 *dst = reinterpret_cast<int4 *>(smem);
+    constexpr int NS = (int)(sizeof(PackedSector) / 16);
+    for (int k = threadIdx.x; k < NS; k += blockDim.x) dst[k] = src[k];
+    const int nt = ps->n_terms;
+    const PackedTermF *tsrc = reinterpret_cast<const PackedTermF *>(packed + termsf_off) + ps->term0;
+    float4 *tdst = reinterpret_cast<float4 *>(dst + NS);
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) {
+        const float hi = tsrc[k].hi, lo = tsrc[k].lo;
+        tdst[k] = make_float4(hi, hi, lo, lo);
+    }
+}
+
+/* ------------------------------------------------------------------ K2x2: persistent FP32 evaluation, two points
+   per thread (generated evaluators).  Work items and their partials are those of eval_f32_body; a thread takes its
+   P points in pairs (p, p + 1) and accumulates lane a before lane b, i.e. in the one-point path's order. */
+template <int S, bool DEF, int MAXM, class Pol>
+DEV void eval_f32x2_body(const JobTable &jt) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_item;
+    __shared__ int s_job;
+    __shared__ double s_red[16][2 * (MAXM + 1)];
+    __shared__ uint32_t s_fail[16];
+    const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
+    const float4 *T = reinterpret_cast<const float4 *>(smem + sizeof(PackedSector));
+    const int lane_id = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int cur = -1, cur_job = -1;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long it = (long long)atomicAdd(jt.counter, 1ull);
+            s_item = it;
+            s_job = it < jt.total_items ? find_job(jt, it) : 0;
+        }
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= jt.total_items) break;
+        const int jb = s_job;
+        const Job &J = jt.jobs[jb];
+        const long long local = item - J.item_begin;
+        const long long per_sector = (long long)J.m * J.chunks;
+        const int ls = (int)(local / per_sector);
+        const long long rem = local - (long long)ls * per_sector;
+        const int shift = (int)(rem / J.chunks);
+        const long long chunk = rem - (long long)shift * J.chunks;
+        const int psec = J.sector_begin + ls;
+        if (J.sector_prec) {
+            const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
+            if (J.sector_prec[gps->orig_index] != 1) {
+                __syncthreads();
+                continue;
+            }
+        }
+        if (psec != cur || jb != cur_job) {
+            stage_sector_f2(J.packed, J.sectors_off, J.termsf_off, psec, smem);
+            __syncthreads();
+            cur = psec;
+            cur_job = jb;
+        }
+        const Exps ex{J.eU0, J.eU1, J.eF0, J.eF1};
+        const Pol pol = Pol::make(T, sec, psec);
+        const uint32_t n = J.n;
+        const float invnf = 1.f / (float)n;
+        const float lam = (float)J.lambda[sec.orig_index];
+        uint32_t rj[S], aj[S], zs[S];
+        float bj[S];
+        const long long i0 = chunk * (long long)blockDim.x * jt.P + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            split_shift(J.shifts[6 * shift + j], n, aj[j], bj[j]);
+            rj[j] = (uint32_t)(((unsigned long long)i0 * J.z[j]) % n);
+            zs[j] = J.zstep[j];
+        }
+        float acc[2 * (MAXM + 1)], cmp[2 * (MAXM + 1)];
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
+        uint32_t fails = 0;
+        for (int p = 0; p < jt.P; p += 2) {
+            bool live[2];
+            float2 x[S], y[S];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const long long i = i0 + (long long)(p + k) * blockDim.x;
+                live[k] = (p + k < jt.P) && i < (long long)n;
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    float xv, yv;
+                    lattice_f32(rj[j], aj[j], bj[j], n, invnf, xv, yv);
+                    if (k == 0) {
+                        x[j].x = xv;
+                        y[j].x = yv;
+                    } else {
+                        x[j].y = xv;
+                        y[j].y = yv;
+                    }
+                    const uint32_t v = rj[j] + zs[j];
+                    rj[j] = v >= n ? v - n : v;
+                }
+            }
+            if (live[0] || live[1]) {
+                c2 val[MAXM + 1];
+                point_integrand_f2<S, DEF, MAXM>(sec, pol, x, y, jt.r, lam, ex, live, val, fails);
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (!live[k]) continue;
+#pragma unroll
+                    for (int m = 0; m <= MAXM; ++m) {
+                        two_sum_acc(acc[2 * m], cmp[2 * m], lane(val[m].re, k));
+                        two_sum_acc(acc[2 * m + 1], cmp[2 * m + 1], lane(val[m].im, k));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2 * (MAXM + 1); ++q) {
+            float s1 = acc[q], c1 = cmp[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float so = __shfl_down_sync(0xffffffffu, s1, off);
+                const float co = __shfl_down_sync(0xffffffffu, c1, off);
+                two_sum_acc(s1, c1, so);
+                c1 += co;
+            }
+            if (lane_id == 0) s_red[warp][q] = (double)s1 + (double)c1;
+        }
+        uint32_t f = fails;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) f += __shfl_down_sync(0xffffffffu, f, off);
+        if (lane_id == 0) s_fail[warp] = f;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int q = threadIdx.x;
+            if (q < J.n_slots * 2) {
+                double s2 = 0.0, c2v = 0.0;
+                if (q < 2 * (MAXM + 1))
+                    for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2v, s_red[w][q]);
+                J.partials[local * J.n_slots * 2 + q] = s2 - c2v;
+            }
+            if (q == 0) {
+                uint32_t tf = 0;
+                for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
+                J.part_fails[local] = tf;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 /* ------------------------------------------------------------------ K3: FP32-versus-FP64 probe per sector */

@@ -121,7 +121,7 @@ def test_every_term_enters_its_polynomial_once(cfg):
     once, and no other term appears, in both precisions."""
     prep = prepared(cfg)
     h, secs, terms = image(prep)
-    for pre, precision, head in (("qg", N.QMC_PREC_MIXED, "const PackedTermF"), ("qd", N.QMC_PREC_FP64, "const PackedTerm")):
+    for pre, precision, head in (("qg", N.QMC_PREC_MIXED, "const float4"), ("qd", N.QMC_PREC_FP64, "const PackedTerm")):
         src = api.gen_source(prep, precision)
         funcs = {}
         for m in re.finditer(rf"\b({pre}_(?:ufr|gh|ufc)_(\d+)_(\d+))\({head}[^{{]*\{{(.*?)\n\}}", src, flags=re.S):
@@ -140,9 +140,10 @@ def check_terms(cfg, h, secs, terms, funcs, pre):
                 groups = {f"{pre}_gh_{k}_{Y}": G + H, f"{pre}_ufc_{k}_{Y}": [U, F]}
             for name, ranges in groups.items():
                 body = funcs[name]
-                # (accumulator, term) of every statement that adds a term; a complex term is one packed FMA (FP32)
-                # or a statement on .x followed by one on .y (FP64)
-                pairs = re.findall(r"a(\d+)(?:\.x)? (?:=|\+=) (?:fmaf?\(|cfma2f\()?C\[(\d+)\]", body)
+                # (accumulator, term) of every statement that adds a term; a complex term is one statement (FP32,
+                # packed over both lanes) or a statement on .x followed by one on .y (FP64)
+                pairs = re.findall(r"a(\d+)(?:\.x|\.re)? (?:=|\+=) (?:fmaf?\(|cfma2c\(|rfma2[ch]\(|add2\(a\d+(?:\.re)?, "
+                                   r"bc2\()?C\[(\d+)\]", body)
                 got = {}
                 for acc, term in pairs:
                     got.setdefault(int(term), set()).add(int(acc))
@@ -157,13 +158,23 @@ SHIM = r"""
 #define __device__
 #define __noinline__ static
 #define __restrict__
-struct cf { float x, y; };
-static inline cf mkf(float x, float y) { return cf{x, y}; }
-static inline cf cmulf(cf a, cf b) { return cf{fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
-static inline cf cfma2f(float hi, float lo, cf m, cf a) {
-    return cf{fmaf(hi, m.x, fmaf(lo, m.x, a.x)), fmaf(hi, m.y, fmaf(lo, m.y, a.y))};
+struct float2 { float x, y; };
+struct float4 { float x, y, z, w; };
+struct c2 { float2 re, im; };
+static inline float2 mk2(float x, float y) { float2 r; r.x = x; r.y = y; return r; }
+static inline float2 bc2(float v) { return mk2(v, v); }
+static inline float2 add2(float2 a, float2 b) { return mk2(a.x + b.x, a.y + b.y); }
+static inline float2 mul2(float2 a, float2 b) { return mk2(a.x * b.x, a.y * b.y); }
+static inline float2 fma2(float2 a, float2 b, float2 c) { return mk2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y)); }
+static inline float2 neg2(float2 a) { return mk2(-a.x, -a.y); }
+static inline c2 mkc2(float2 re, float2 im) { c2 r; r.re = re; r.im = im; return r; }
+static inline c2 zero_c2() { return mkc2(bc2(0.f), bc2(0.f)); }
+static inline c2 cmul2(c2 a, c2 b) { return mkc2(fma2(a.re, b.re, neg2(mul2(a.im, b.im))), fma2(a.re, b.im, mul2(a.im, b.re))); }
+static inline float2 rfma2h(const float4 &c, float2 m, float2 a) { return fma2(mk2(c.x, c.y), m, a); }
+static inline float2 rfma2c(const float4 &c, float2 m, float2 a) { return fma2(mk2(c.x, c.y), m, fma2(mk2(c.z, c.w), m, a)); }
+static inline c2 cfma2c(const float4 &c, c2 m, c2 a) {
+    return mkc2(fma2(mk2(c.x, c.y), m.re, fma2(mk2(c.z, c.w), m.re, a.re)), fma2(mk2(c.x, c.y), m.im, fma2(mk2(c.z, c.w), m.im, a.im)));
 }
-struct PackedTermF { float hi, lo; unsigned char e[8]; };
 """
 
 
@@ -173,7 +184,8 @@ def dispatch(h, secs, pre, R, Cx, term, ool):
     S = h.dim
     NP = S * (S + 1) // 2
     ta = ", ".join(f"t[{j}]" for j in range(S))
-    za = ", ".join(f"z[{j}].x, z[{j}].y" for j in range(S))
+    re_, im_ = ("re", "im") if pre == "qg" else ("x", "y")
+    za = ", ".join(f"z[{j}].{re_}, z[{j}].{im_}" for j in range(S))
     Rr, GH, Cc = ("QgR", "QgGH", "QgC") if pre == "qg" else ("QdR", "QdGH", "QdC")
     ufr, gh, ufc = [], [], []
     for k in range(h.n_sectors):
@@ -205,7 +217,7 @@ def generated_body(src, pol):
 def host_harness(src, h, secs):
     """C++ source: the generated per-sector functions plus extern "C" entry points taking arrays"""
     body = generated_body(src, "QgPol")
-    return "\n".join([SHIM, body] + dispatch(h, secs, "qg", "float", "cf", "PackedTermF", "struct QgGH" in body))
+    return "\n".join([SHIM, body] + dispatch(h, secs, "qg", "float2", "c2", "float4", "struct QgGH" in body))
 
 
 def poly_value(terms, lo, hi, x):
@@ -224,8 +236,9 @@ def poly_value(terms, lo, hi, x):
 
 @pytest.mark.parametrize("cfg", [W.CONFIG0, W.CONFIG1, W.CONFIG2], ids=lambda c: c.name)
 def test_generated_functions_evaluate_the_table_polynomials(cfg):
-    """Each generated FP32 function (per sector and zeroed subset) against the table's terms summed in FP64 at a
-    random point with the subset's coordinates zero."""
+    """Each generated FP32 function (per sector and zeroed subset; two points per call, one per lane) against the
+    table's terms summed in FP64 at random points with the subset's coordinates zero.  The gradient and Hessian
+    terms take the coefficient's FP32 part only, U and F the hi + lo pair: both agree with FP64 to FP32 rounding."""
     prep = prepared(cfg)
     h, secs, terms = image(prep)
     src = api.gen_source(prep)
@@ -242,30 +255,38 @@ def test_generated_functions_evaluate_the_table_polynomials(cfg):
     worst = 0.0
     for k, s in enumerate(secs):
         T_s = np.ascontiguousarray(terms[s.term0: s.term0 + s.n_terms])
-        Cp = T_s.ctypes.data_as(ctypes.c_void_p)
+        # coefficient slots as staged for the two-point path: (hi, hi, lo, lo)
+        C4 = np.ascontiguousarray(np.stack([T_s["hi"], T_s["hi"], T_s["lo"], T_s["lo"]], -1).astype(np.float32))
+        Cp = C4.ctypes.data_as(ctypes.c_void_p)
         U, F, G, H = blocks(h, s)
         for Y in subsets(s.sing_mask):
-            t = rng.uniform(0.0, 1.0, S).astype(np.float32)
-            t[[j for j in range(S) if (Y >> j) & 1]] = 0.0
-            tp = t.ctypes.data_as(fptr)
+            t = rng.uniform(0.0, 1.0, (2, S)).astype(np.float32)   # lane a, lane b
+            t[:, [j for j in range(S) if (Y >> j) & 1]] = 0.0
+            t2 = np.ascontiguousarray(t.T)                          # float2 per variable
+            tp = t2.ctypes.data_as(fptr)
+            refs, got = [], []
             if h.class_begin[0] <= k < h.class_end[0]:
-                outv = np.zeros(2, np.float32)
+                outv = np.zeros((2, 2), np.float32)                 # U, F as float2
                 L.h_ufr(k, Y, Cp, tp, outv.ctypes.data_as(fptr))
-                refs = [poly_value(T_s, *U, t.astype(np.float64)), poly_value(T_s, *F, t.astype(np.float64))]
-                got = list(outv)
+                for ln in range(2):
+                    refs += [poly_value(T_s, *U, t[ln].astype(np.float64)), poly_value(T_s, *F, t[ln].astype(np.float64))]
+                    got += [outv[0, ln], outv[1, ln]]
             else:
-                g = np.zeros(S, np.float32)
-                hh = np.zeros(NP, np.float32)
+                g = np.zeros((S, 2), np.float32)
+                hh = np.zeros((NP, 2), np.float32)
                 L.h_gh(k, Y, Cp, tp, g.ctypes.data_as(fptr), hh.ctypes.data_as(fptr))
-                refs = [poly_value(T_s, lo, hi, t.astype(np.float64)) for lo, hi in G + H]
-                got = list(g) + list(hh)
-                zc = (t * (1 - 0.3j * rng.uniform(0, 1, S))).astype(np.complex64)
-                zf = np.ascontiguousarray(np.stack([zc.real, zc.imag], -1).astype(np.float32))
-                uf = np.zeros(4, np.float32)
+                zc = (t * (1 - 0.3j * rng.uniform(0, 1, (2, S)))).astype(np.complex64)
+                # c2 per variable: (re lane a, re lane b, im lane a, im lane b)
+                zf = np.ascontiguousarray(np.stack([zc.real.T, zc.imag.T], 1).reshape(S, 4).astype(np.float32))
+                uf = np.zeros((2, 4), np.float32)
                 L.h_ufc(k, Y, Cp, zf.ctypes.data_as(fptr), uf.ctypes.data_as(fptr))
-                z64 = zc.astype(np.complex128)
-                refs += [poly_value(T_s, *U, z64), poly_value(T_s, *F, z64)]
-                got += [complex(uf[0], uf[1]), complex(uf[2], uf[3])]
+                for ln in range(2):
+                    tl = t[ln].astype(np.float64)
+                    refs += [poly_value(T_s, lo, hi, tl) for lo, hi in G + H]
+                    got += list(g[:, ln]) + list(hh[:, ln])
+                    z64 = zc[ln].astype(np.complex128)
+                    refs += [poly_value(T_s, *U, z64), poly_value(T_s, *F, z64)]
+                    got += [complex(uf[0, ln], uf[0, 2 + ln]), complex(uf[1, ln], uf[1, 2 + ln])]
             for (rv, mag), gv in zip(refs, got):
                 if mag == 0.0:
                     assert gv == 0, (k, Y)  # every term vanishes on this face
