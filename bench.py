@@ -68,8 +68,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # non-planar family at n = 1048573, 16 shifts), dram__bytes_read.sum + dram__bytes_write.sum from one
 # single-pass ncu capture of a full-size launch; valid while the device code and the generator hash to
 # KERNEL_HASH, null otherwise
-TRAFFIC_BYTES = None
-KERNEL_HASH = ""
+TRAFFIC_BYTES = 2364672 + 78080  # read + write
+KERNEL_HASH = "0f0e2b7425b6fe2a"
 
 
 INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3,
@@ -214,6 +214,11 @@ def max_over_ranks(value, dist, device="cpu"):
     return float(t.item())
 
 
+def phase(name, t0):
+    """Duration of a bench phase, on stderr (stdout carries the one JSON line)."""
+    print(f"bench: {name} took {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+
+
 def korobov_vector(n, a=76):
     """An admissible generating vector (1, a, a^2, ...) mod n for timing the oracle: the cost of an evaluation
     does not depend on which vector the lattice uses."""
@@ -323,9 +328,11 @@ def main_ours(args):
     n64 = max(k for k in lat if k < (1 << (18 if two_loop else 24)))  # lattice of the FP64-alone pass
     evaluator = {"auto": N.QMC_EVAL_AUTO, "table": N.QMC_EVAL_TABLE, "generated": N.QMC_EVAL_GENERATED}[args.evaluator]
     # generated evaluators (FP32 and FP64) compiled before any timing
+    t_ph = time.perf_counter()
     compile_ms = {"fp32": api.gen_compile(prep, precision=N.QMC_PREC_MIXED).compile_ms}
     if evaluator != N.QMC_EVAL_TABLE:
         compile_ms["fp64"] = api.gen_compile(prep, precision=N.QMC_PREC_FP64).compile_ms
+    phase("code generation", t_ph)
     shifts = W.shifts(cfg.seed + rank, N_SHIFTS)
     stream = torch.cuda.Stream(device=dev_name)
     sh = torch.tensor(shifts, device=dev_name)
@@ -339,7 +346,7 @@ def main_ours(args):
         keep = None
         if active is not None:
             keep = (ctypes.c_int32 * ns)(*[int(v) for v in active])
-            p.sector_active = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int32))
+            p.sector_active = ctypes.cast(keep, ctypes.c_void_p)
         return p, keep
 
     # lambda per sector: halved where the sign check of Eq. 14 fails (as qmc_integrate does), checked by the FP64
@@ -423,6 +430,7 @@ def main_ours(args):
             el = max_over_ranks(el, dist, dev_name)
         return el, evs
 
+    t_ph = time.perf_counter()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
@@ -521,6 +529,7 @@ def main_ours(args):
     d2h = len(host_passes) * (sums_h.numel() * 8 + fails_h.numel() * 8)
     ctx.close()
 
+    phase("timed steps, FP64 pass, e2e", t_ph)
     extras = {}
     if not args.no_extras and rank == 0:
         seeds = args.tta_seeds
@@ -528,8 +537,15 @@ def main_ours(args):
         for key, kw in (("mixed_per_sector", dict(precision=N.QMC_PREC_MIXED)),
                         ("fp64_per_sector", dict(precision=N.QMC_PREC_FP64)),
                         ("fp64_per_integral", dict(precision=N.QMC_PREC_FP64, lock_step=1))):
-            tta[key] = time_to_accuracy(api, blob, cfg, local, stream, seeds, **kw)
-        tta["mixed_speedup_p50_vs_fp64_per_integral"] = tta["fp64_per_integral"]["p50_ms"] / tta["mixed_per_sector"]["p50_ms"]
+            t_ph = time.perf_counter()
+            try:
+                tta[key] = time_to_accuracy(api, blob, cfg, local, stream, seeds, **kw)
+            except Exception as exc:  # noqa: BLE001 -- a failure there must not cost the line
+                tta[key] = {"error": f"{type(exc).__name__}: {exc}"}
+            phase(f"time_to_1e-3 {key}", t_ph)
+        if all("p50_ms" in tta[k] for k in ("fp64_per_integral", "mixed_per_sector")):
+            tta["mixed_speedup_p50_vs_fp64_per_integral"] = (tta["fp64_per_integral"]["p50_ms"] /
+                                                             tta["mixed_per_sector"]["p50_ms"])
         extras["time_to_1e-3"] = tta
         guarded = []
         if args.serving_sample > 0:
@@ -539,7 +555,9 @@ def main_ours(args):
                     ("paper_ia_scan", lambda: paper_ia_scan(1000, device=local))]
         for key, fn in guarded:
             try:
+                t_ph = time.perf_counter()
                 extras[key] = fn()
+                phase(key, t_ph)
             except Exception as exc:  # noqa: BLE001 -- a failure there must not cost the line
                 extras[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
@@ -570,7 +588,9 @@ def main_ours(args):
             "clocks": clocks,
         }
         if not args.no_extras:
+            t_ph = time.perf_counter()
             out["cpu_baseline"] = cpu_baseline(cfg)
+            phase("cpu_baseline", t_ph)
         out.update(extras)
         print(json.dumps(out))
     if dist:
