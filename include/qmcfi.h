@@ -85,7 +85,7 @@ typedef struct {
 typedef struct {
     int32_t kind;      /* 0: F > 0 on the cube; 1: F < 0 (real, phase exp(i pi eF(eps)) applied on the host);
                           2: deformed (Eq. 14) */
-    int32_t sigma;     /* number of variables with exponent alpha = -1 (Eqs. 10-12) */
+    int32_t sigma;     /* number of variables with exponent alpha <= -1 (Eqs. 10-12) */
     int32_t n_slots;   /* slots this sector fills */
     int32_t n_terms;   /* polynomial terms staged in shared memory (U, F, dF, d2F) */
     double flops;      /* algorithmic FP work per point */
@@ -139,8 +139,11 @@ int qmc_version(void);
  * that the kernels read (relocatable: offsets only; copy it to device memory as is).
  *   order_min..order_max: Laurent orders of the integral the image must serve (order_max - order_min < 8).
  *   packed: output buffer of packed_capacity bytes, or NULL to query info->packed_bytes only.
- * Errors: QMC_ERR_ARG, QMC_ERR_TABLE, QMC_ERR_UNSUPPORTED (among others: an exponent A_j <= -2, which needs
- * Taylor subtraction beyond Eq. 11 with p = 0), QMC_ERR_KINEMATICS, QMC_ERR_MEMORY (capacity).
+ * Sectors with an exponent A_j = -2 or -3 (Taylor subtraction of Eq. 11 with p = 1, 2) are taken when F~ keeps
+ * one sign on the cube (no deformation) and at most two variables have A_j <= -1: they form a third class that
+ * always runs in FP64 (table evaluator, truncated power series of U~ and F~ in the expanded variables).
+ * Errors: QMC_ERR_ARG, QMC_ERR_TABLE, QMC_ERR_UNSUPPORTED (among others: A_j <= -4, A_j <= -2 in a deformed
+ * sector or beside more than one other singular variable), QMC_ERR_KINEMATICS, QMC_ERR_MEMORY (capacity).
  */
 int qmc_prepare(const void *table, size_t table_bytes, const double *invariants, int32_t n_invariants,
                 int32_t order_min, int32_t order_max, void *packed, size_t packed_capacity, qmc_info *info);

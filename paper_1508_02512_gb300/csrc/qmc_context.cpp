@@ -129,6 +129,7 @@ struct IntegState {
     std::vector<char> active;
     std::vector<int32_t> prec;
     std::vector<double> flops;                  /* per sector (table order) */
+    std::vector<char> fp64_only;                /* per sector: class 2 (alpha <= -2) runs in FP64 always */
     std::vector<std::vector<int32_t>> masks;    /* host masks of the current passes */
     int probe_item = -1;
     std::chrono::steady_clock::time_point t0;
@@ -174,8 +175,12 @@ struct IntegState {
         sums.assign((size_t)ns * m * h->n_slots * 2, 0.0);
         fails.assign((size_t)ns * m, 0);
         flops.assign(ns, 0.0);
+        fp64_only.assign(ns, 0);
         const PackedSector *ps = sectors_of(packed);
-        for (int pi = 0; pi < ns; ++pi) flops[ps[pi].orig_index] = std::max(ps[pi].flops, 1.0);
+        for (int pi = 0; pi < ns; ++pi) {
+            flops[ps[pi].orig_index] = std::max(ps[pi].flops, 1.0);
+            fp64_only[ps[pi].orig_index] = ps[pi].taylor != 0;
+        }
         return QMC_OK;
     }
 
@@ -228,6 +233,7 @@ struct IntegState {
                 const double *v = &pr[((size_t)s * h->n_slots + o) * 4];
                 if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
             }
+            bad |= fp64_only[s] != 0;
             prec[s] = bad ? 0 : 1;
             res.fp64_reruns += bad;
         }

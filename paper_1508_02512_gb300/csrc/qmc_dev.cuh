@@ -538,7 +538,12 @@ DEV int find_job(const JobTable &jt, long long item) {
 }
 
 /* ------------------------------------------------------------------ K1: persistent FP64 evaluation */
-template <int S, bool DEF, int MAXM, class Pol>
+template <int S, int MAXM>
+__device__ __noinline__ void point_integrand_taylor(const PackedSector &s, const PackedTerm *T, const double *x, int r,
+                                                    Exps ex, double *out);
+
+/* TAYLOR: the sectors of class 2 (endpoint exponents alpha <= -2), evaluated by point_integrand_taylor */
+template <int S, bool DEF, int MAXM, class Pol, bool TAYLOR = false>
 DEV void eval_f64_body(const JobTable &jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
@@ -610,7 +615,14 @@ DEV void eval_f64_body(const JobTable &jt) {
 #pragma unroll
                 for (int j = 0; j < S; ++j) x[j] = fma((double)rj[j], invn, delta[j]) - (rj[j] >= Rj[j] ? 1.0 : 0.0);
                 cd val[MAXM + 1];
-                point_integrand<S, DEF, MAXM>(sec, pol, x, jt.r, lam, ex, val, fails);
+                if constexpr (TAYLOR) {
+                    double v[MAXM + 1];
+                    point_integrand_taylor<S, MAXM>(sec, T, x, jt.r, ex, v);
+#pragma unroll
+                    for (int m = 0; m <= MAXM; ++m) val[m] = mk(v[m], 0.0);
+                } else {
+                    point_integrand<S, DEF, MAXM>(sec, pol, x, jt.r, lam, ex, val, fails);
+                }
 #pragma unroll
                 for (int m = 0; m <= MAXM; ++m) {
                     acc[2 * m] += val[m].x;
@@ -656,6 +668,206 @@ DEV void eval_f64_body(const JobTable &jt) {
 template <int S, bool DEF, int MAXM>
 __global__ void __launch_bounds__(256) qmc_eval_kernel(const __grid_constant__ JobTable jt) {
     eval_f64_body<S, DEF, MAXM, TabPol<S>>(jt);
+}
+
+/* ================================================================== endpoint exponents alpha <= -2 (class 2)
+ * Sec. II, Eq. (11) with p > 0: for a variable with t^{a + b eps}, a = -1 - p,
+ *   int_0^1 t^{a+b eps} f(t) dt = int_0^1 t^{a+b eps} [f(t) - sum_{k<=p} f^(k)(0) t^k/k!] dt
+ *                                 + sum_{k<=p} f^(k)(0) / (k! (a + k + 1 + b eps)),
+ * applied to every variable with alpha_j <= -1 of the sector (the operators of different variables commute).
+ * Per point each such variable takes one of three roles: its value (factor t^{a+b eps}), a subtracted Taylor term,
+ * or a pole term.  The Taylor coefficients of f in the variables set to zero (the subset Z) are the coefficients of
+ * truncated power series ("jets"): the jets of U~ and F~ restricted to those variables, raised to their
+ * eps-dependent powers by the power recurrence of a series, P0 |k| R_k = sum_{0<l<=k} (a |l| - |k-l|) P_l R_{k-l}
+ * (from P E R = a R E P with the Euler operator E), and multiplied.  The remainder of a variable with
+ * t_j < QMC_TAYLOR_SMALL_T is taken from its own series (orders p_j < k <= p_j + QMC_TAYLOR_EXTRA), because the
+ * difference loses its digits there.  Undeformed sectors only (F~ of one sign); FP64, table evaluator. */
+#define QMC_TAYLOR_JET (QMC_TAYLOR_Q * QMC_TAYLOR_Q)
+
+/* c = a * b for eps series of length L (truncated) */
+template <int L>
+DEV void ser_mul(const double *a, const double *b, double *c, int n) {
+    for (int i = n - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = 0; k <= i; ++k) s = fma(a[k], b[i - k], s);
+        c[i] = s;
+    }
+}
+
+/* exp(x eps) t^A as a series: t^A x^m / m! */
+template <int L>
+DEV void ser_power_exp(double tA, double x, double *out, int n) {
+    double c = tA;
+    for (int m = 0; m < n; ++m) {
+        out[m] = c;
+        c = c * x / (m + 1);
+    }
+}
+
+/* R = P^{a0 + a1 eps} for a jet P over d0 x d1 orders (row-major, P[0] > 0); R holds L-term series per entry */
+template <int L>
+DEV void jet_power(const double *P, int d0, int d1, int a0, int a1, double *R, int n) {
+    const double P0 = P[0];
+    ser_power_exp<L>(ipow(P0, a0), (double)a1 * qlog(P0), R, n);
+    const double inv0 = 1.0 / P0;
+    for (int k0 = 0; k0 < d0; ++k0)
+        for (int k1 = 0; k1 < d1; ++k1) {
+            const int kk = k0 + k1;
+            if (kk == 0) continue;
+            double acc[L];
+            for (int m = 0; m < n; ++m) acc[m] = 0.0;
+            for (int l0 = 0; l0 <= k0; ++l0)
+                for (int l1 = 0; l1 <= k1; ++l1) {
+                    const int ll = l0 + l1;
+                    if (ll == 0) continue;
+                    const double p = P[l0 * d1 + l1];
+                    if (p == 0.0) continue;
+                    const double *r = R + ((k0 - l0) * d1 + (k1 - l1)) * L;
+                    const double c0 = p * (double)(a0 * ll - (kk - ll)), c1 = p * (double)(a1 * ll);
+                    for (int m = n - 1; m >= 0; --m) acc[m] = fma(c0, r[m], m > 0 ? fma(c1, r[m - 1], acc[m]) : acc[m]);
+                }
+            double *Rk = R + (k0 * d1 + k1) * L;
+            const double s = inv0 / (double)kk;
+            for (int m = 0; m < n; ++m) Rk[m] = acc[m] * s;
+        }
+}
+
+/* w(x) * (sector integrand) at x for a class-2 sector, slots 0..M (slot n = coefficient of eps^(n - sigma)) */
+template <int S, int MAXM>
+__device__ __noinline__ void point_integrand_taylor(const PackedSector &s, const PackedTerm *T, const double *x, int r,
+                                                    Exps ex, double *out) {
+    constexpr int L = MAXM + 1;
+    const int n = s.M + 1;
+    for (int m = 0; m < L; ++m) out[m] = 0.0;
+    double t[S], lt[S], w = 1.0;
+    for (int j = 0; j < S; ++j) {
+        double tm, wj;
+        if (!(x[j] > 0.0)) return; /* the weight vanishes at x = 0 */
+        transform(r, x[j], t[j], tm, wj);
+        w *= wj;
+        lt[j] = qlog(t[j]);
+    }
+    int sv[QMC_TAYLOR_MAX_Z], pv[QMC_TAYLOR_MAX_Z];
+    bool small[QMC_TAYLOR_MAX_Z];
+    int sigma = 0;
+    double base[L];
+    for (int m = 0; m < L; ++m) base[m] = 0.0;
+    base[0] = s.D;
+    for (int j = 0; j < S; ++j) {
+        if (s.A[j] <= -1) {
+            sv[sigma] = j;
+            pv[sigma] = -s.A[j] - 1;
+            small[sigma] = t[j] < QMC_TAYLOR_SMALL_T;
+            ++sigma;
+        } else if (s.A[j] != 0 || s.B[j] != 0) {
+            double f[L];
+            ser_power_exp<L>(ipow(t[j], s.A[j]), (double)s.B[j] * lt[j], f, n);
+            ser_mul<L>(base, f, base, n);
+        }
+    }
+    double tpow[QMC_TAYLOR_MAX_Z][L];
+    for (int i = 0; i < sigma; ++i) {
+        const int j = sv[i];
+        ser_power_exp<L>(ipow(t[j], s.A[j]), (double)s.B[j] * lt[j], tpow[i], n);
+    }
+    const double sgnF = s.kind == 1 ? -1.0 : 1.0; /* F~ < 0 everywhere: |F~| here, the phase on the host */
+    double PU[QMC_TAYLOR_JET], PF[QMC_TAYLOR_JET];
+    double RU[QMC_TAYLOR_JET * L], RF[QMC_TAYLOR_JET * L];
+    for (unsigned zm = 0; zm < (1u << sigma); ++zm) {
+        int zi[QMC_TAYLOR_MAX_Z], q[QMC_TAYLOR_MAX_Z], nz = 0;
+        for (int i = 0; i < sigma; ++i)
+            if ((zm >> i) & 1u) {
+                zi[nz] = i;
+                q[nz] = small[i] ? pv[i] + QMC_TAYLOR_EXTRA : pv[i];
+                ++nz;
+            }
+        /* the values of the variables outside Z: their remainder as a difference, so zero where it is small */
+        double pre[L];
+        for (int m = 0; m < L; ++m) pre[m] = base[m];
+        bool dead = false;
+        for (int i = 0; i < sigma; ++i)
+            if (!((zm >> i) & 1u)) {
+                if (small[i]) dead = true;
+                else ser_mul<L>(pre, tpow[i], pre, n);
+            }
+        if (dead) continue;
+        const int d0 = nz >= 1 ? q[0] + 1 : 1, d1 = nz == 2 ? q[1] + 1 : 1;
+        const int nj = d0 * d1;
+        for (int k = 0; k < nj; ++k) PU[k] = PF[k] = 0.0;
+        for (int a = 0; a < s.nU + s.nF; ++a) {
+            const PackedTerm &tm = T[a];
+            const int k0 = nz >= 1 ? tm.e[sv[zi[0]]] : 0, k1 = nz == 2 ? tm.e[sv[zi[1]]] : 0;
+            if (k0 >= d0 || k1 >= d1) continue;
+            double v = a < s.nU ? tm.c : sgnF * tm.c;
+            for (int j = 0; j < S; ++j) {
+                bool inZ = false;
+                for (int i = 0; i < nz; ++i) inZ |= sv[zi[i]] == j;
+                if (!inZ) v *= ipow(t[j], tm.e[j]);
+            }
+            (a < s.nU ? PU : PF)[k0 * d1 + k1] += v;
+        }
+        jet_power<L>(PU, d0, d1, ex.eU0, ex.eU1, RU, n);
+        jet_power<L>(PF, d0, d1, -ex.eF0, -ex.eF1, RF, n);
+        /* roles: every subset of Z takes the pole role, the rest of Z the subtracted one */
+        for (unsigned tmk = 0; tmk < (1u << nz); ++tmk)
+            for (int k0 = 0; k0 < d0; ++k0)
+                for (int k1 = 0; k1 < d1; ++k1) {
+                    const int kk[2] = {k0, k1};
+                    bool skip = false;
+                    for (int i = 0; i < nz; ++i) {
+                        const int vi = zi[i];
+                        const bool pole = (tmk >> i) & 1u;
+                        if (pole && kk[i] > pv[vi]) skip = true;
+                        /* subtracted: Taylor terms k <= p where the remainder is a difference, series terms
+                           k > p where it comes from its series */
+                        if (!pole && ((kk[i] <= pv[vi]) == small[vi])) skip = true;
+                    }
+                    if (skip) continue;
+                    double g[L];
+                    for (int m = 0; m < L; ++m) g[m] = 0.0;
+                    for (int l0 = 0; l0 <= k0; ++l0)
+                        for (int l1 = 0; l1 <= k1; ++l1) {
+                            double pr[L];
+                            ser_mul<L>(RU + (l0 * d1 + l1) * L, RF + ((k0 - l0) * d1 + (k1 - l1)) * L, pr, n);
+                            for (int m = 0; m < n; ++m) g[m] += pr[m];
+                        }
+                    double term[L];
+                    ser_mul<L>(pre, g, term, n);
+                    int shift = 0;
+                    for (int i = 0; i < nz; ++i) {
+                        const int vi = zi[i], j = sv[vi];
+                        if ((tmk >> i) & 1u) {
+                            const int c = s.A[j] + kk[i] + 1;
+                            if (c == 0) {
+                                for (int m = 0; m < n; ++m) term[m] /= (double)s.B[j];
+                                ++shift;
+                            } else {
+                                double sr[L], f = 1.0 / c;
+                                const double ratio = -(double)s.B[j] / c;
+                                for (int m = 0; m < n; ++m) {
+                                    sr[m] = f;
+                                    f *= ratio;
+                                }
+                                ser_mul<L>(term, sr, term, n);
+                            }
+                        } else {
+                            const double sg = kk[i] <= pv[vi] ? -1.0 : 1.0;
+                            double f[L];
+                            const double tk = sg * ipow(t[j], kk[i]);
+                            for (int m = 0; m < n; ++m) f[m] = tk * tpow[vi][m];
+                            ser_mul<L>(term, f, term, n);
+                        }
+                    }
+                    const int lo = sigma - shift;
+                    for (int m = lo; m < n; ++m) out[m] += term[m - lo];
+                }
+    }
+    for (int m = 0; m < n; ++m) out[m] *= w;
+}
+
+template <int S, int MAXM>
+__global__ void __launch_bounds__(256) qmc_eval_kernel_taylor(const __grid_constant__ JobTable jt) {
+    eval_f64_body<S, false, MAXM, TabPol<S>, true>(jt);
 }
 
 /* ================================================================== FP32 path of the mixed-precision pass
@@ -1824,6 +2036,35 @@ __global__ void __launch_bounds__(128) qmc_probe_kernel(ProbeArgs a) {
 }
 
 /* ------------------------------------------------------------------ per-point values on explicit indices */
+template <int S, int MAXM>
+__global__ void __launch_bounds__(256) qmc_points_kernel_taylor(PointArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    logtab_init();
+    stage_sector(a.packed, a.sectors_off, a.terms_off, a.sector, smem);
+    __syncthreads();
+    const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
+    const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
+    const Exps ex{a.eU0, a.eU1, a.eF0, a.eF1};
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < a.npts;
+         j += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long i = (unsigned long long)a.idx[j];
+        double x[S];
+#pragma unroll
+        for (int d = 0; d < S; ++d) {
+            const uint32_t rj = (uint32_t)((i * a.z[d]) % a.n);
+            const double v = fma((double)rj, a.invn, a.shift[d]);
+            x[d] = v >= 1.0 ? v - 1.0 : v;
+        }
+        double val[MAXM + 1];
+        point_integrand_taylor<S, MAXM>(sec, T, x, a.r, ex, val);
+        for (int n = 0; n < a.n_slots; ++n) {
+            a.out[(j * a.n_slots + n) * 2] = n <= MAXM ? val[n < MAXM + 1 ? n : 0] : 0.0;
+            a.out[(j * a.n_slots + n) * 2 + 1] = 0.0;
+        }
+        a.fails[j] = 0;
+    }
+}
+
 template <int S, bool DEF, int MAXM>
 __global__ void __launch_bounds__(256) qmc_points_kernel(PointArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -60,3 +60,33 @@ static int launch_points_t(const PointArgs &a, cudaStream_t st) {
     k<<<(int)g, block, a.smem_bytes, st>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
+
+/* class 2 (endpoint exponents alpha <= -2): FP64 only */
+template <int S, int MAXM>
+static int launch_eval_taylor_t(const JobTable &t, int grid, int block, cudaStream_t st) {
+    auto k = qmc_eval_kernel_taylor<S, MAXM>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem_bytes) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    k<<<grid, block, t.smem_bytes, st>>>(t);
+    return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+template <int S, int MAXM>
+static int occupancy_taylor_t(int block, int smem, int *out) {
+    auto k = qmc_eval_kernel_taylor<S, MAXM>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return QMC_ERR_CUDA;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, block, smem) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}
+
+template <int S, int MAXM>
+static int launch_points_taylor_t(const PointArgs &a, cudaStream_t st) {
+    auto k = qmc_points_kernel_taylor<S, MAXM>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    const int block = 128;
+    long long g = (a.npts + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 4096) g = 4096;
+    k<<<(int)g, block, a.smem_bytes, st>>>(a);
+    return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+}

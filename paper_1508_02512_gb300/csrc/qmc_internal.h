@@ -22,7 +22,14 @@
 #define QMC_PACK_MAGIC 0x31504d51u /* "QMP1" */
 #define QMC_MAX_EXP 15             /* largest exponent of one variable in one term */
 #define QMC_MAX_SECTOR_TERMS 3072  /* terms staged per sector (48 KiB of shared memory) */
-#define QMC_N_CLASSES 2            /* 0: undeformed sectors, 1: deformed sectors */
+#define QMC_N_CLASSES 3            /* 0: undeformed sectors, 1: deformed sectors, 2: undeformed sectors with an
+                                      endpoint exponent alpha <= -2 (Taylor subtraction of Eq. 11 with p > 0) */
+/* Sectors of class 2: every variable with alpha_j <= -1 is expanded at t_j = 0 to order p_j = -alpha_j - 1 */
+#define QMC_TAYLOR_MAX_P 2         /* alpha_j >= -3 */
+#define QMC_TAYLOR_MAX_Z 2         /* variables with alpha_j <= -1 in such a sector */
+#define QMC_TAYLOR_EXTRA 10        /* Taylor terms of a remainder taken from its own series */
+#define QMC_TAYLOR_SMALL_T 0.02    /* below it a variable's remainder comes from that series */
+#define QMC_TAYLOR_Q (QMC_TAYLOR_MAX_P + QMC_TAYLOR_EXTRA + 1) /* orders per expanded variable */
 
 struct PackedHeader {
     uint32_t magic;
@@ -52,7 +59,7 @@ struct PackedSector {
     int32_t term0;      /* index of the sector's first term in the term array */
     int32_t n_terms;    /* nU + nF + nG + nH */
     int32_t orig_index; /* position of the sector in the table (outputs are indexed by it) */
-    int32_t reserved;
+    int32_t taylor;     /* 1: some alpha_j <= -2 (class 2) */
     int16_t gstart[8];  /* gradient polynomial j: terms [gstart[j], gstart[j+1]) of the G block */
     int16_t hstart[24]; /* Hessian polynomial p (j <= k): terms [hstart[p], hstart[p+1]) of the H block */
     double D;

@@ -42,7 +42,7 @@
 
 namespace {
 
-#define QMC_JIT_GENERATOR_VERSION 7u
+#define QMC_JIT_GENERATOR_VERSION 8u
 #define QMC_GEN_INLINE_TERMS 2048 /* families with more terms get out-of-line sector functions */
 
 const PackedHeader *hdr(const void *p) {
@@ -398,7 +398,7 @@ std::string generate(const PackedHeader *h, const Lang &L) {
                                  : "        " + labels(s, Y) + " " + pre + "_ufc_" + n + "(T, z, U, F); return;\n";
             }
     o += std::string("        default: U = ") + L.zero_c + "; F = " + L.zero_c + ";\n        }\n    }\n};\n\n";
-    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+    for (int c = 0; c < 2; ++c) { /* class 2 (alpha <= -2) runs the ahead-of-time FP64 kernel */
         if (h->class_end[c] <= h->class_begin[c]) continue;
         const char *def = c == 1 ? "true" : "false";
         const int mm = maxm_of(h, c);
@@ -474,7 +474,7 @@ int compile(const std::string &src, Compiled &out) {
 /* ---------------------------------------------------------------- module cache */
 struct Module {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t eval[QMC_N_CLASSES] = {nullptr, nullptr};
+    cudaKernel_t eval[QMC_N_CLASSES] = {};
     bool from_disk = false;
     double compile_ms = 0.0;
     int64_t source_bytes = 0, cubin_bytes = 0;
@@ -574,7 +574,7 @@ int build_module(const PackedHeader *h, int precision, std::unique_ptr<Module> &
     std::unique_ptr<Module> m(new Module());
     if (cudaLibraryLoadData(&m->lib, cc.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) != cudaSuccess)
         return QMC_ERR_CUDA;
-    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+    for (int c = 0; c < 2; ++c) {
         if (h->class_end[c] <= h->class_begin[c]) continue;
         const std::string e = std::string(lang_of(precision).pre) + "_eval_c" + std::to_string(c);
         if (cudaLibraryGetKernel(&m->eval[c], m->lib, e.c_str()) != cudaSuccess) {

@@ -11,47 +11,78 @@
 #define QMC_CAT(a, b) QMC_CAT2(a, b)
 #define QMC_FN(name) QMC_CAT(name, QMC_S)
 
-/* one case per (deformation, series length): key = deform * 10 + maxm, maxm in {0, 2, 4} */
+/* one case per (sector class, series length): key = class * 10 + maxm, maxm in {0, 2, 4}; class 0 undeformed,
+   1 deformed (the template's DEF), 2 undeformed with endpoint exponents alpha <= -2 (FP64 only) */
+#define QMC_TAYLOR_CASES(CALL)                                                                                     \
+    case 20: return CALL(0);                                                                                       \
+    case 22: return CALL(2);                                                                                       \
+    case 24: return CALL(4);
 #define QMC_CASES(CALL)                                                                                            \
     case 0: return CALL(false, 0);                                                                                 \
     case 2: return CALL(false, 2);                                                                                 \
     case 4: return CALL(false, 4);                                                                                 \
     case 10: return CALL(true, 0);                                                                                 \
     case 12: return CALL(true, 2);                                                                                 \
-    case 14: return CALL(true, 4);                                                                                 \
-    default: return QMC_ERR_UNSUPPORTED;
+    case 14: return CALL(true, 4);
 
 int QMC_FN(qmc_launch_eval_d)(int deform, int maxm, int precision, const JobTable &a, int grid, int block,
                               cudaStream_t st) {
 #define F32(D, M) launch_eval_f32_t<QMC_S, D, M>(a, grid, block, st)
 #define F64(D, M) launch_eval_t<QMC_S, D, M>(a, grid, block, st)
+#define TAY(M) launch_eval_taylor_t<QMC_S, M>(a, grid, block, st)
     if (precision == QMC_PREC_MIXED) {
-        switch (deform * 10 + maxm) { QMC_CASES(F32) }
+        switch (deform * 10 + maxm) {
+            QMC_CASES(F32)
+            default: return QMC_ERR_UNSUPPORTED;
+        }
     }
-    switch (deform * 10 + maxm) { QMC_CASES(F64) }
+    switch (deform * 10 + maxm) {
+        QMC_CASES(F64)
+        QMC_TAYLOR_CASES(TAY)
+        default: return QMC_ERR_UNSUPPORTED;
+    }
 #undef F32
 #undef F64
+#undef TAY
 }
 
 int QMC_FN(qmc_occupancy_d)(int deform, int maxm, int precision, int block, int smem, int *out) {
 #define F32(D, M) occupancy_f32_t<QMC_S, D, M>(block, smem, out)
 #define F64(D, M) occupancy_t<QMC_S, D, M>(block, smem, out)
+#define TAY(M) occupancy_taylor_t<QMC_S, M>(block, smem, out)
     if (precision == QMC_PREC_MIXED) {
-        switch (deform * 10 + maxm) { QMC_CASES(F32) }
+        switch (deform * 10 + maxm) {
+            QMC_CASES(F32)
+            default: return QMC_ERR_UNSUPPORTED;
+        }
     }
-    switch (deform * 10 + maxm) { QMC_CASES(F64) }
+    switch (deform * 10 + maxm) {
+        QMC_CASES(F64)
+        QMC_TAYLOR_CASES(TAY)
+        default: return QMC_ERR_UNSUPPORTED;
+    }
 #undef F32
 #undef F64
+#undef TAY
 }
 
 int QMC_FN(qmc_launch_points_d)(int deform, int maxm, const PointArgs &a, cudaStream_t st) {
 #define PTS(D, M) launch_points_t<QMC_S, D, M>(a, st)
-    switch (deform * 10 + maxm) { QMC_CASES(PTS) }
+#define TAY(M) launch_points_taylor_t<QMC_S, M>(a, st)
+    switch (deform * 10 + maxm) {
+        QMC_CASES(PTS)
+        QMC_TAYLOR_CASES(TAY)
+        default: return QMC_ERR_UNSUPPORTED;
+    }
 #undef PTS
+#undef TAY
 }
 
 int QMC_FN(qmc_launch_probe_d)(int deform, int maxm, const ProbeArgs &a, cudaStream_t st) {
 #define PRB(D, M) launch_probe_t<QMC_S, D, M>(a, st)
-    switch (deform * 10 + maxm) { QMC_CASES(PRB) }
+    switch (deform * 10 + maxm) {
+        QMC_CASES(PRB)
+        default: return QMC_ERR_UNSUPPORTED;
+    }
 #undef PRB
 }

@@ -205,8 +205,10 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
         for (const Run &run : pl.runs) {
             const int c = run.cls;
             for (int prec = 0; prec < 2; ++prec) {
-                if (!mixed && prec == 1) continue;
-                if (mixed && prec == 0 && !b.pass.sector_precision) continue;
+                /* class 2 (endpoint exponents alpha <= -2): FP64 whatever the pass's precision */
+                const bool fp64_only = c == 2;
+                if ((!mixed || fp64_only) && prec == 1) continue;
+                if (mixed && !fp64_only && prec == 0 && !b.pass.sector_precision) continue;
                 Job J;
                 std::memset(&J, 0, sizeof(J));
                 J.packed = static_cast<const unsigned char *>(b.packed_dev);
@@ -216,7 +218,7 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
                 J.chunks = pl.chunks;
                 J.shifts = b.shifts_dev;
                 J.lambda = b.lambda_dev;
-                J.sector_prec = mixed ? b.pass.sector_precision : nullptr;
+                J.sector_prec = (mixed && !fp64_only) ? b.pass.sector_precision : nullptr;
                 J.partials = reinterpret_cast<double *>(scr + L.partial_off[i]) + run.item_off * h->n_slots * 2;
                 J.part_fails = reinterpret_cast<uint32_t *>(scr + L.fail_off[i]) + run.item_off;
                 J.n = (uint32_t)b.pass.lattice.n;
@@ -237,7 +239,7 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
                 if (prec == 1 && use_generated(b.pass)) {
                     rc = qmc_gen_kernel(b.packed_host, QMC_PREC_MIXED, c, &gen);
                     if (rc) return rc;
-                } else if (prec == 0 && use_generated64(b.pass, h)) {
+                } else if (prec == 0 && !fp64_only && use_generated64(b.pass, h)) {
                     rc = qmc_gen_kernel(b.packed_host, QMC_PREC_FP64, c, &gen);
                     if (rc) return rc;
                 }
@@ -406,7 +408,7 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
     Plan pl;
     int rc = make_plan(h, pass, pl);
     if (rc) return rc;
-    for (int c = 0; c < QMC_N_CLASSES; ++c) {
+    for (int c = 0; c < 2; ++c) { /* class 2 always runs in FP64: nothing to probe */
         const int ns = h->class_end[c] - h->class_begin[c];
         if (ns <= 0) continue;
         ProbeArgs a;
@@ -576,7 +578,7 @@ int qmc_eval_points(const void *packed_host, const void *packed_dev, int32_t sec
     a.eF0 = h->eF0;
     a.eF1 = h->eF1;
     a.smem_bytes = (int)(sizeof(PackedSector) + (size_t)ps[psec].n_terms * sizeof(PackedTerm));
-    const int cls = ps[psec].kind == 2 ? 1 : 0;
+    const int cls = ps[psec].taylor ? 2 : (ps[psec].kind == 2 ? 1 : 0);
     const int mm = h->class_maxm[cls];
     const int maxm = mm == 0 ? 0 : (mm <= 2 ? 2 : 4);
     return qmc_launch_points(h->dim, cls, maxm, pass->precision, a, stream);

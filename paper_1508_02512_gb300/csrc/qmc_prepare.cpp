@@ -115,8 +115,9 @@ int parse_table(const void *blob, size_t bytes, Table &t) {
         s.D = r.get<double>();
         if (!r.ok || !std::isfinite(s.D)) return QMC_ERR_TABLE;
         for (int j = 0; j < d; ++j) {
-            if (s.A[j] < -1 || s.A[j] > QMC_MAX_EXP) return s.A[j] < -1 ? QMC_ERR_UNSUPPORTED : QMC_ERR_TABLE;
-            if (s.A[j] == -1 && s.B[j] == 0) return QMC_ERR_TABLE; /* unregulated endpoint singularity */
+            if (s.A[j] < -1 - QMC_TAYLOR_MAX_P || s.A[j] > QMC_MAX_EXP)
+                return s.A[j] < 0 ? QMC_ERR_UNSUPPORTED : QMC_ERR_TABLE;
+            if (s.A[j] <= -1 && s.B[j] == 0) return QMC_ERR_TABLE; /* unregulated endpoint singularity */
             if (std::abs(s.B[j]) > 64) return QMC_ERR_TABLE;
         }
         for (int pass = 0; pass < 2; ++pass) {
@@ -260,6 +261,32 @@ double transform_flops(int r) {
 void sector_work(const PackedSector &s, const PTerm *T, int d, int r, int eU0, int eF0, double &flops,
                  double &transc) {
     const int M = s.M;
+    if (s.taylor) {
+        /* class 2 (Eq. 11 with p > 0), counted where no remainder comes from its series: per subset Z of the
+           singular variables, the jets of U~ and F~ (J = prod (p_j + 1) orders), two power recurrences, the jet
+           product per role and the role factors; eps series of L = M + 1 terms */
+        const int L = M + 1;
+        int pv[QMC_MAX_DIM], ns = 0;
+        for (int j = 0; j < d; ++j)
+            if (s.A[j] <= -1) pv[ns++] = -s.A[j] - 1;
+        double f = d * transform_flops(r);
+        for (int zm = 0; zm < (1 << ns); ++zm) {
+            double J = 1.0;
+            int nz = 0;
+            for (int i = 0; i < ns; ++i)
+                if ((zm >> i) & 1) {
+                    J *= pv[i] + 1;
+                    ++nz;
+                }
+            f += (s.nU + s.nF) * (d - nz + 1.0);
+            f += 2.0 * (J * (J + 1.0) / 2.0) * 4.0 * L;
+            f += (double)(1 << nz) * J * (J * L * L + (2.0 + nz) * L * L);
+            f += (ns - nz) * (double)L * L;
+        }
+        flops = f + 4.0 * L;
+        transc = d + 2.0 * (1 << ns);
+        return;
+    }
     double per_subset = 0.0, trans_subset = 0.0;
     auto real_poly = [&](int off, int n) {
         double f = 0.0;
@@ -389,14 +416,19 @@ int pack_table(const Table &t, const double *inv, int n_inv, int order_min, int 
         ps.Df = (float)s.D;
         ps.orig_index = si;
         int sigma = 0, mask = 0;
+        bool taylor = false;
         for (int j = 0; j < d; ++j) {
             ps.A[j] = s.A[j];
             ps.B[j] = s.B[j];
-            if (s.A[j] == -1) {
+            if (s.A[j] <= -1) {
                 ++sigma;
                 mask |= 1 << j;
             }
+            taylor |= s.A[j] <= -2;
         }
+        /* alpha <= -2 (Eq. 11 with p > 0): undeformed sectors with at most QMC_TAYLOR_MAX_Z singular variables */
+        if (taylor && (kind == 2 || sigma > QMC_TAYLOR_MAX_Z)) return QMC_ERR_UNSUPPORTED;
+        ps.taylor = taylor ? 1 : 0;
         ps.sigma = sigma;
         ps.sing_mask = mask;
         ps.M = kmax + sigma;
@@ -450,7 +482,7 @@ int pack_table(const Table &t, const double *inv, int n_inv, int order_min, int 
         ps.n_terms = (int)w.terms.size();
         if (ps.n_terms > QMC_MAX_SECTOR_TERMS || ps.nG > 32767 || ps.nH > 32767) return QMC_ERR_UNSUPPORTED;
         max_terms = std::max(max_terms, ps.n_terms);
-        w.cls = kind == 2 ? 1 : 0;
+        w.cls = taylor ? 2 : (kind == 2 ? 1 : 0);
         double fl, tr;
         sector_work(ps, w.terms.data(), d, r_for_count, t.eU0, t.eF0, fl, tr);
         ps.flops = fl;

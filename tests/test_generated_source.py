@@ -37,8 +37,8 @@ class PackedHeader(ctypes.Structure):
                 ("eU0", ctypes.c_int32), ("eU1", ctypes.c_int32), ("eF0", ctypes.c_int32), ("eF1", ctypes.c_int32),
                 ("order_min", ctypes.c_int32), ("order_max", ctypes.c_int32), ("kmax", ctypes.c_int32),
                 ("n_slots", ctypes.c_int32), ("pre_low", ctypes.c_int32), ("n_pre", ctypes.c_int32),
-                ("pre", ctypes.c_double * (N.QMC_MAX_ORDERS + 4)), ("class_begin", ctypes.c_int32 * 2),
-                ("class_end", ctypes.c_int32 * 2), ("class_maxm", ctypes.c_int32 * 2), ("max_terms", ctypes.c_int32),
+                ("pre", ctypes.c_double * (N.QMC_MAX_ORDERS + 4)), ("class_begin", ctypes.c_int32 * 3),
+                ("class_end", ctypes.c_int32 * 3), ("class_maxm", ctypes.c_int32 * 3), ("max_terms", ctypes.c_int32),
                 ("n_terms_total", ctypes.c_int32), ("sectors_off", ctypes.c_int64), ("terms_off", ctypes.c_int64),
                 ("total_bytes", ctypes.c_int64), ("flops_per_eval", ctypes.c_double),
                 ("transc_per_eval", ctypes.c_double), ("n_deformed", ctypes.c_int32), ("n_negative", ctypes.c_int32),
@@ -50,7 +50,7 @@ class PackedSector(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("sigma", ctypes.c_int32), ("sing_mask", ctypes.c_int32),
                 ("M", ctypes.c_int32), ("A", ctypes.c_int32 * 8), ("B", ctypes.c_int32 * 8), ("nU", ctypes.c_int32),
                 ("nF", ctypes.c_int32), ("nG", ctypes.c_int32), ("nH", ctypes.c_int32), ("term0", ctypes.c_int32),
-                ("n_terms", ctypes.c_int32), ("orig_index", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_terms", ctypes.c_int32), ("orig_index", ctypes.c_int32), ("taylor", ctypes.c_int32),
                 ("gstart", ctypes.c_int16 * 8), ("hstart", ctypes.c_int16 * 24), ("D", ctypes.c_double),
                 ("flops", ctypes.c_double), ("transc", ctypes.c_double), ("Df", ctypes.c_float),
                 ("pad", ctypes.c_float)]

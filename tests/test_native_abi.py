@@ -100,10 +100,10 @@ def test_table_compiler_rejects_alpha_minus_two():
             T.compile_integral(dotted, ("pp1", "pp2", "pp3", "pp4"), strategy=strategy)
 
 
-def test_squared_propagator_tables_match_the_oracle_and_prepare_refuses_them():
+def test_squared_propagator_tables_match_the_oracle_and_prepare_takes_them():
     """With allow_higher_poles the table compiler writes the alpha = -2 sectors of the squared-propagator box,
-    sector for sector equal to the oracle's (which integrates them with oracle.taylor); qmc_prepare refuses
-    them until the kernels take Taylor subtraction beyond p = 0."""
+    sector for sector equal to the oracle's (which integrates them with oracle.taylor); qmc_prepare takes them
+    (undeformed: Taylor subtraction of Eq. 11 with p > 0 in the class-2 kernel) and counts them as such."""
     import dataclasses
     topo = W.box(False)
     dotted = dataclasses.replace(topo, props=(dataclasses.replace(topo.props[0], nu=2),) + topo.props[1:])
@@ -114,7 +114,14 @@ def test_squared_propagator_tables_match_the_oracle_and_prepare_refuses_them():
         ref = OS.decompose(dotted, zero, strategy, allow_higher_poles=True)
         assert canon_product(leaves, meta) == OS.canonical(ref)
         assert min(int(s.A.min()) for s in leaves) == -2
-        assert _prep_status(blob, W.kinematics(dotted, s=-3.0, t=-2.0)) == N.QMC_ERR_UNSUPPORTED
+        prep = api.prepare(blob, W.kinematics(dotted, s=-3.0, t=-2.0), -2, 0)
+        # class-2 sectors are sorted last; their sigma counts every variable with alpha <= -1
+        higher = [k for k, s in enumerate(leaves) if int(s.A.min()) <= -2]
+        for k in higher:
+            assert prep.sector(k).sigma == int((leaves[k].A <= -1).sum())
+        assert 0 < len(higher) < len(leaves)
+        # the physical region (deformed sectors) stays refused for alpha <= -2
+        assert _prep_status(blob, W.kinematics(dotted, s=3.0, t=-2.0)) == N.QMC_ERR_UNSUPPORTED
 
 
 def test_symanzik_matches_oracle_for_all_topologies():
@@ -262,8 +269,12 @@ def test_prepare_rejects_malformed_tables():
     assert _prep_status(blob, kin, 0, 9) == N.QMC_ERR_ARG                          # too many orders
     meta, leaves = T.read_table(blob)
     bad = [T.SectorRecord(s.A.copy(), s.B.copy(), s.U, s.F, s.D) for s in leaves]
-    bad[0].A[0] = -2                                                               # alpha <= -2
+    bad[0].A[0], bad[0].B[0] = -2, -1                                      # alpha <= -2 in a deformed sector
     assert _prep_status(T.write_table(bad, meta), kin) == N.QMC_ERR_UNSUPPORTED
+    bad[0].A[0] = -4                                                               # beyond alpha = -3
+    assert _prep_status(T.write_table(bad, meta), kin) == N.QMC_ERR_UNSUPPORTED
+    bad[0].B[0] = 0                                                                # alpha <= -2 unregulated
+    assert _prep_status(T.write_table(bad, meta), kin) in (N.QMC_ERR_UNSUPPORTED, N.QMC_ERR_TABLE)
     bad[0].A[0] = -1
     bad[0].B[0] = 0                                                                # unregulated pole
     assert _prep_status(T.write_table(bad, meta), kin) == N.QMC_ERR_TABLE
