@@ -337,8 +337,14 @@ typedef struct {
     double max_seconds;      /* 0 = no limit */
     int32_t block, points_per_thread; /* launch shape (0 = default) */
     int64_t probe_samples;   /* QMC_PREC_MIXED: points per sector of the FP32/FP64 probe (0 = 4096) */
-    double fp32_budget;      /* QMC_PREC_MIXED: a sector runs in FP64 when its probe's sum|v32-v64| exceeds
-                                fp32_budget * rel_tol * sum|v64| in any order (0 = 0.1) */
+    double fp32_budget;      /* QMC_PREC_MIXED (0 = 0.1): the FP32 error budget is fp32_budget * rel_tol of the
+                                integral.  Per eps order, the probe's mean |v32 - v64| per point of the sectors kept
+                                in FP32 may add up to that fraction of the current estimate of the order (summed
+                                over sectors, before the Gamma prefactor); sectors take the budget in order of their
+                                share of it and the rest run in FP64.  Before any estimate exists (the probe precedes
+                                the first FP32 pass), a sector runs in FP64 when its sum|v32-v64| exceeds
+                                fp32_budget * rel_tol * sum|v64| in any order; after the first evaluation the
+                                decision is taken again on the same probe with the estimates. */
     int32_t evaluator;       /* QMC_EVAL_* of the FP32 evaluation (passes and probe) */
     int32_t lock_step;       /* 0 (default): each sector has its own lattice size, and after each step only the
                                 sectors that carry most of the remaining error per unit of cost move up the ladder
@@ -364,6 +370,7 @@ typedef struct {
     int64_t rounds;                   /* batched rounds run by the scheduler */
     int64_t batched_passes;           /* passes run, summed over rounds */
     int64_t device_bytes;             /* device memory held by the context */
+    int64_t shed;                     /* requests turned away before running: their deadline could not be met */
 } qmc_serving_stats;
 
 /* Context: owns a CUDA stream binding, the device copies of loaded integrals and its scratch.
@@ -403,8 +410,14 @@ int qmc_integrate(qmc_ctx *ctx, int32_t integral_id, const qmc_options *opt, qmc
  * contributes the pass at its current lattice size to shared launches (qmc_eval_batch); requests that arrive
  * meanwhile join at the next round.  A request's result is the same, bit for bit, as qmc_integrate with the same
  * options would give alone.  opt->max_seconds counts from submission: a request whose limit passes while it
- * is still queued finishes with QMC_ERR_TIMEOUT without running.  The paper has no serving loop; this is the
- * library's deployment layer. */
+ * is still queued finishes with QMC_ERR_TIMEOUT without running, and so does one that cannot finish in time by
+ * the loop's estimate (counted in qmc_serving_stats.shed).  The estimate: each round's measured time is charged
+ * to its requests by their share of its evaluations; a completed request's charge, averaged per integral, is the
+ * cost of the next one; the work ahead of a queued request is the remaining cost of the running ones (requests
+ * running together share every round, so one ends no earlier than their summed cost); all taken with a margin of
+ * 1.25.  A queued request also waits while admitting it would, by the same estimate, end a running request past
+ * its limit.  The paper
+ * has no serving loop; this is the library's deployment layer. */
 int qmc_submit(qmc_ctx *ctx, int32_t integral_id, const double *invariants, int32_t n_invariants, int32_t order_min,
                int32_t order_max, const qmc_options *opt, int64_t *request_id);
 

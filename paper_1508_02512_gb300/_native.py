@@ -85,7 +85,7 @@ class qmc_result(ctypes.Structure):
 class qmc_serving_stats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("queued", c_int64), ("active", c_int64),
                 ("peak_active", c_int64), ("rounds", c_int64), ("batched_passes", c_int64),
-                ("device_bytes", c_int64)]
+                ("device_bytes", c_int64), ("shed", c_int64)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/qmcfi.h

@@ -16,6 +16,7 @@
 #include <condition_variable>
 #include <deque>
 #include <functional>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -26,6 +27,12 @@
 
 #include "lattice_table.h"
 #include "qmc_host_internal.h"
+
+/* the serving loop's admission takes its load estimates times this factor before comparing them with limits */
+#define QMC_SHED_MARGIN 1.25
+/* cost of an FP64 evaluation per algorithmic flop relative to FP32, for charging a shared round's time to its
+   requests (the two generated kernels' measured rates on six-dimensional sectors differ by ~30x) */
+#define QMC_FP64_WEIGHT 30.0
 
 namespace {
 
@@ -132,6 +139,10 @@ struct IntegState {
     std::vector<char> fp64_only;                /* per sector: class 2 (alpha <= -2) runs in FP64 always */
     std::vector<std::vector<int32_t>> masks;    /* host masks of the current passes */
     int probe_item = -1;
+    std::vector<double> Tr, Ti;                 /* order_totals(): per order, summed over sectors */
+    std::vector<double> probe_pr;               /* the last probe's sums, and its points per sector */
+    int64_t probe_n = 0;
+    bool prec_provisional = false;
     std::chrono::steady_clock::time_point t0;
 
     int init(const unsigned char *packed_host, const qmc_options &o, std::chrono::steady_clock::time_point start,
@@ -176,6 +187,10 @@ struct IntegState {
         fails.assign((size_t)ns * m, 0);
         flops.assign(ns, 0.0);
         fp64_only.assign(ns, 0);
+        Tr.clear();
+        Ti.clear();
+        probe_pr.clear();
+        prec_provisional = false;
         const PackedSector *ps = sectors_of(packed);
         for (int pi = 0; pi < ns; ++pi) {
             flops[ps[pi].orig_index] = std::max(ps[pi].flops, 1.0);
@@ -224,20 +239,110 @@ struct IntegState {
         for (size_t k = 0; k < out.size(); ++k) out[k].sector_active = masks[k].empty() ? nullptr : masks[k].data();
     }
 
-    void set_precision(const std::vector<double> &pr, qmc_result &res) {
+    /* Per eps order k of the sector sums (slot - sigma, offset by the largest sigma): the current estimate T_k
+       summed over sectors, before the Gamma prefactor.  Called where every sector's sums belong to its rung. */
+    void order_totals() {
+        const int sl = h->n_slots;
+        const PackedSector *ps = sectors_of(packed);
+        std::vector<int> sig(ns, 0);
+        for (int pi = 0; pi < ns; ++pi) sig[ps[pi].orig_index] = ps[pi].sigma;
+        int maxsig = 0;
+        for (int s = 0; s < ns; ++s) maxsig = std::max(maxsig, sig[s]);
+        Tr.assign(sl + maxsig, 0.0);
+        Ti.assign(sl + maxsig, 0.0);
+        for (int s = 0; s < ns; ++s) {
+            const double inv = 1.0 / ((double)m * (double)ladder[rung[s]].n);
+            for (int o = 0; o < sl; ++o) {
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k < m; ++k) {
+                    re += sums[(((size_t)s * m + k) * sl + o) * 2];
+                    im += sums[(((size_t)s * m + k) * sl + o) * 2 + 1];
+                }
+                Tr[o - sig[s] + maxsig] += re * inv;
+                Ti[o - sig[s] + maxsig] += im * inv;
+            }
+        }
+    }
+
+    /* Precision of each sector from the FP32/FP64 probe (sums over n_samp points per sector and slot of |v64|,
+       |v32 - v64|, v32 - v64).  The FP32 error budget is budget = fp32_budget * rel_tol of the integral: per eps
+       order k, the mean |v32 - v64| per point of the sectors kept in FP32 (a bound on their bias in that order)
+       may add up to budget * |T_k| (order_totals), with the floor 1e-6 max_k |T_k| of the convergence test.
+       Sectors are kept in FP32 in order of their largest share of that budget until it is spent; the rest run in
+       FP64.  Without totals yet (before the first evaluation) each sector is held to budget * sum |v64| of its
+       own (per slot), and the decision is provisional: revisit_precision takes it again on the same probe once
+       totals exist.  Non-finite FP32 values and class-2 sectors always take FP64. */
+    void set_precision(const std::vector<double> &pr, int64_t n_samp, qmc_result &res) {
         const double budget = (opt.fp32_budget > 0 ? opt.fp32_budget : 0.1) * opt.rel_tol;
+        const int sl = h->n_slots;
+        const PackedSector *ps = sectors_of(packed);
+        std::vector<int> sig(ns, 0);
+        for (int pi = 0; pi < ns; ++pi) sig[ps[pi].orig_index] = ps[pi].sigma;
+        int maxsig = 0;
+        for (int s = 0; s < ns; ++s) maxsig = std::max(maxsig, sig[s]);
+        const int K = sl + maxsig;
+        if ((int)Tr.size() != K) {
+            Tr.assign(K, 0.0);
+            Ti.assign(K, 0.0);
+        }
+        std::vector<double> lim(K, 0.0);
+        double tmax = 0.0;
+        for (int k = 0; k < K; ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
+        for (int k = 0; k < K; ++k) lim[k] = budget * std::max(std::hypot(Tr[k], Ti[k]), 1e-6 * tmax);
+        const double per = 1.0 / (double)std::max<int64_t>(n_samp, 1);
+        std::vector<char> bad(ns, 0);
+        std::vector<double> share(ns, 0.0);
+        for (int s = 0; s < ns; ++s) {
+            bad[s] = fp64_only[s] != 0;
+            for (int o = 0; o < sl; ++o) {
+                const double *v = &pr[((size_t)s * sl + o) * 4];
+                if (!std::isfinite(v[1])) bad[s] = 1;
+                if (tmax <= 0.0) {
+                    if (v[1] > budget * v[0]) bad[s] = 1;
+                } else {
+                    const double l = lim[o - sig[s] + maxsig];
+                    share[s] = std::max(share[s], l > 0.0 ? v[1] * per / l : (v[1] > 0.0 ? 1e300 : 0.0));
+                }
+            }
+        }
+        if (tmax > 0.0) {
+            std::vector<int> order;
+            for (int s = 0; s < ns; ++s)
+                if (!bad[s]) order.push_back(s);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return share[a] < share[b]; });
+            std::vector<double> used(K, 0.0);
+            for (int s : order) {
+                bool fits = true;
+                for (int o = 0; o < sl && fits; ++o) {
+                    const int k = o - sig[s] + maxsig;
+                    fits = used[k] + pr[((size_t)s * sl + o) * 4 + 1] * per <= lim[k];
+                }
+                if (!fits) {
+                    bad[s] = 1;
+                    continue;
+                }
+                for (int o = 0; o < sl; ++o) used[o - sig[s] + maxsig] += pr[((size_t)s * sl + o) * 4 + 1] * per;
+            }
+        }
         res.fp64_reruns = 0;
         for (int s = 0; s < ns; ++s) {
-            bool bad = false;
-            for (int o = 0; o < h->n_slots; ++o) {
-                const double *v = &pr[((size_t)s * h->n_slots + o) * 4];
-                if (v[1] > budget * v[0] || !std::isfinite(v[1])) bad = true;
-            }
-            bad |= fp64_only[s] != 0;
-            prec[s] = bad ? 0 : 1;
-            res.fp64_reruns += bad;
+            prec[s] = bad[s] ? 0 : 1;
+            res.fp64_reruns += bad[s];
         }
         probe_due = false;
+        prec_provisional = tmax <= 0.0;
+        if (&pr != &probe_pr) probe_pr = pr;
+        probe_n = n_samp;
+    }
+
+    /* true when the precision was taken again (the caller copies prec to the device before the next pass) */
+    bool revisit_precision(qmc_result &res) {
+        if (!prec_provisional || probe_pr.empty()) return false;
+        double tmax = 0.0;
+        for (size_t k = 0; k < Tr.size(); ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
+        if (tmax <= 0.0) return false;
+        set_precision(probe_pr, probe_n, res);
+        return true;
     }
 
     void count(const std::vector<qmc_pass> &ps, qmc_result &res) const {
@@ -278,6 +383,7 @@ struct IntegState {
             nvec[s] = ladder[rung[s]].n;
             nmax = std::max(nmax, nvec[s]);
         }
+        if (mixed) order_totals();
         std::vector<double> Q((size_t)m * nord * 2), mean(nord * 2), err(nord * 2);
         qmc_combine_sectors(packed, m, nvec.data(), sums.data(), Q.data(), mean.data(), err.data());
         res.n_final = nmax;
@@ -479,10 +585,13 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
                                                  cudaMemcpyDeviceToHost, c->stream));
             if (!rc) rc = cuda_status(cudaStreamSynchronize(c->stream));
             if (!rc) {
-                st.set_precision(pr, *res);
+                st.set_precision(pr, std::min<int64_t>(st.probe_samples(), passes[st.probe_item].lattice.n), *res);
                 rc = cuda_status(cudaMemcpyAsync(c->prec.p, st.prec.data(), ns * sizeof(int32_t),
                                                  cudaMemcpyHostToDevice, c->stream));
             }
+        } else if (!rc && st.revisit_precision(*res)) {
+            rc = cuda_status(cudaMemcpyAsync(c->prec.p, st.prec.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                             c->stream));
         }
         if (rc) return res->status = rc;
         items.assign(passes.size(), qmc_batch_item());
@@ -587,6 +696,7 @@ struct Request {
     std::vector<qmc_pass> passes;  /* passes of the current round */
     qmc_result res;
     std::chrono::steady_clock::time_point t_submit, t_admit;
+    double sec_used = 0.0;         /* loop seconds charged to it so far: its share of each round's time */
     bool cancelled = false;
     int state = REQ_QUEUED;
 };
@@ -606,6 +716,9 @@ struct Serving {
     std::map<int64_t, std::shared_ptr<Request>> all;
     int64_t next_id = 1;
     qmc_serving_stats stats;
+    /* load estimate for shedding: per integral id, a moving average of the loop seconds its completed requests
+       were charged */
+    std::map<int32_t, double> sec_per_request;
 };
 
 namespace {
@@ -623,6 +736,18 @@ void finish(Serving *S, qmc_ctx *c, Request &r, int status) {
     std::lock_guard<std::mutex> g(S->mu);
     r.state = REQ_DONE;
     S->stats.completed += 1;
+    if (status == QMC_OK && r.sec_used > 0.0) {
+        auto it = S->sec_per_request.find(r.integral_id);
+        if (it == S->sec_per_request.end()) S->sec_per_request[r.integral_id] = r.sec_used;
+        else it->second = 0.7 * it->second + 0.3 * r.sec_used;
+    }
+}
+
+/* seconds of device work a queued request still needs by the loop's estimate (0 when it has no history) */
+double est_seconds(const Serving *S, int32_t integral_id, double used) {
+    auto it = S->sec_per_request.find(integral_id);
+    if (it == S->sec_per_request.end()) return 0.0;
+    return std::max(0.0, it->second - used);
 }
 
 /* host preparation and device buffers of a newly admitted request (called with the context mutex held) */
@@ -675,7 +800,7 @@ int probe(Serving *S, Request &r) {
                                          S->stream));
     if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
     if (rc) return rc;
-    r.st.set_precision(pr, r.res);
+    r.st.set_precision(pr, std::min<int64_t>(r.st.probe_samples(), r.passes[r.st.probe_item].lattice.n), r.res);
     return cuda_status(cudaMemcpyAsync(r.dprec.p, r.st.prec.data(), r.st.ns * sizeof(int32_t), cudaMemcpyHostToDevice,
                                        S->stream));
 }
@@ -683,6 +808,7 @@ int probe(Serving *S, Request &r) {
 void serve_loop(qmc_ctx *c) {
     Serving *S = c->serving;
     cudaSetDevice(c->device);
+    std::chrono::steady_clock::time_point t_iter;
     for (;;) {
         std::vector<std::shared_ptr<Request>> fresh, cancelled, expired;
         /* lock order: the context mutex is never taken while the serving mutex is held */
@@ -697,6 +823,7 @@ void serve_loop(qmc_ctx *c) {
             if (S->compiling.empty()) S->cv.wait(lk, ready);
             else S->cv.wait_for(lk, std::chrono::milliseconds(2), ready);
             if (S->stop) return;
+            t_iter = std::chrono::steady_clock::now();
             /* cancelled requests leave at the round boundary (finished below, outside this lock) */
             for (auto it = S->active.begin(); it != S->active.end();) {
                 if ((*it)->cancelled) {
@@ -707,7 +834,28 @@ void serve_loop(qmc_ctx *c) {
                 }
             }
             /* admission: requests are taken in arrival order while the budget keeps room for their tables and
-               sums plus a first-pass share of scratch; at least one request always runs */
+               sums plus a first-pass share of scratch; at least one request always runs.  With load estimates
+               (est_seconds), a round advances every active request together, so an admitted request ends no
+               earlier than the work of all requests running beside it: a request with a time limit is shed when
+               its own work on top of the work ahead (the active, compiling and just admitted requests'
+               remaining) would end past its limit, and the queue waits while admitting its head would end the
+               work ahead past the tightest limit among those running.  Both compare with a margin of
+               QMC_SHED_MARGIN on the estimates. */
+            const auto now = std::chrono::steady_clock::now();
+            auto left = [&](const Request &q) {
+                return q.opt.max_seconds > 0
+                           ? q.opt.max_seconds - std::chrono::duration<double>(now - q.t_submit).count()
+                           : std::numeric_limits<double>::infinity();
+            };
+            double ahead = 0.0, tight = std::numeric_limits<double>::infinity();
+            for (const auto &a : S->active) {
+                ahead += est_seconds(S, a->integral_id, a->sec_used);
+                tight = std::min(tight, left(*a));
+            }
+            for (const auto &a : S->compiling) {
+                ahead += est_seconds(S, a->integral_id, 0.0);
+                tight = std::min(tight, left(*a));
+            }
             while (!S->queue.empty()) {
                 auto r = S->queue.front();
                 if (r->cancelled) {
@@ -717,21 +865,33 @@ void serve_loop(qmc_ctx *c) {
                     S->stats.completed += 1;
                     continue;
                 }
-                if (r->opt.max_seconds > 0 &&
-                    std::chrono::duration<double>(std::chrono::steady_clock::now() - r->t_submit).count() >
-                        r->opt.max_seconds) {
+                const double mine = left(*r);
+                if (mine < 0.0) {
                     /* its deadline passed in the queue: it leaves without work (finished below, outside this
                        lock), which keeps an overloaded loop's device time for requests that can still finish */
                     S->queue.pop_front();
-                    r->t_admit = std::chrono::steady_clock::now();
+                    r->t_admit = now;
                     expired.push_back(r);
                     continue;
                 }
+                const double own = est_seconds(S, r->integral_id, 0.0);
+                const double end = QMC_SHED_MARGIN * (ahead + own);
+                if (own > 0.0 && end > mine) {
+                    S->queue.pop_front();
+                    r->t_admit = now;
+                    expired.push_back(r);
+                    S->stats.shed += 1;
+                    continue;
+                }
+                const bool running = !S->active.empty() || !fresh.empty();
+                if (running && own > 0.0 && end > tight) break;
                 const size_t est = 2 * r->table.size() + ((size_t)8 << 20);
-                if (!S->active.empty() && in_use + est > c->budget) break;
+                if (running && in_use + est > c->budget) break;
                 S->queue.pop_front();
                 fresh.push_back(r);
                 in_use += est;
+                ahead += own;
+                tight = std::min(tight, mine);
                 if (S->active.size() + fresh.size() >= QMC_MAX_JOBS / 4) break;
             }
         }
@@ -799,6 +959,9 @@ void serve_loop(qmc_ctx *c) {
             rc = cuda_status(cudaMemcpyAsync(r->dlambda.p, r->st.lam.data(), r->st.lam.size() * sizeof(double),
                                              cudaMemcpyHostToDevice, S->stream));
             if (!rc && r->st.probe_item >= 0) rc = probe(S, *r);
+            else if (!rc && r->st.revisit_precision(r->res))
+                rc = cuda_status(cudaMemcpyAsync(r->dprec.p, r->st.prec.data(), r->st.ns * sizeof(int32_t),
+                                                 cudaMemcpyHostToDevice, S->stream));
             if (rc) break;
         }
         std::vector<qmc_batch_item> items;
@@ -841,6 +1004,27 @@ void serve_loop(qmc_ctx *c) {
                                                  cudaMemcpyDeviceToHost, S->stream));
         }
         if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
+        /* the round's time (the whole iteration: admission, preparation, probes, the batch, the copies back) is
+           charged to its requests in proportion to their evaluations' algorithmic flop, FP64 evaluations
+           weighted by QMC_FP64_WEIGHT */
+        const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_iter).count();
+        std::vector<double> wv(batch.size(), 0.0);
+        double round_work = 0.0;
+        for (size_t i = 0; i < batch.size() && !rc; ++i) {
+            Request &r = *batch[i];
+            const PackedSector *ps = sectors_of(r.packed.data());
+            std::vector<double> fl(r.st.ns, 0.0);
+            for (int pi = 0; pi < r.st.ns; ++pi) fl[ps[pi].orig_index] = ps[pi].flops;
+            for (const qmc_pass &p : r.passes)
+                for (int s = 0; s < r.st.ns; ++s)
+                    if (!p.sector_active || p.sector_active[s]) {
+                        const bool f32 = p.precision == QMC_PREC_MIXED && r.st.prec[s] != 0;
+                        wv[i] += fl[s] * (double)r.st.m * (double)p.lattice.n * (f32 ? 1.0 : QMC_FP64_WEIGHT);
+                    }
+            round_work += wv[i];
+        }
+        if (!rc && round_work > 0.0)
+            for (size_t i = 0; i < batch.size(); ++i) batch[i]->sec_used += sec * wv[i] / round_work;
         {
             std::lock_guard<std::mutex> g2(S->mu);
             S->stats.rounds += 1;

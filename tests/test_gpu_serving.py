@@ -177,3 +177,33 @@ def test_serving_admission_by_memory():
     # the budget admits only a few requests at once (each reserves room for its first pass), so some waited
     assert peak_bytes <= budget and 1 <= st.peak_active < len(ids)
     ctx.close()
+
+
+def test_overload_sheds_requests_that_cannot_meet_their_deadline():
+    """A burst of two-loop requests far above the loop's capacity, each with a time limit of a few single-request
+    times: once the loop has the cost (charged loop seconds) of completed requests for that integral, it turns
+    away, before they run, the requests whose limit the work ahead of them would pass (status QMC_ERR_TIMEOUT with
+    no evaluation, counted in qmc_serving_stats.shed), while the admitted ones still converge."""
+    cfg = W.CONFIG2
+    ctx = api.Context(0, 8 << 30)
+    iid = ctx.load_sectors(table(cfg))
+    kw = dict(rel_tol=1e-3, n_shifts=16, lam=0.5, precision=N.QMC_PREC_MIXED)
+    first = ctx.wait(ctx.submit(iid, point(cfg), -2, 0, seed=1, **kw))  # compiles, and gives the work history
+    assert first.status == 0
+    again = ctx.wait(ctx.submit(iid, point(cfg), -2, 0, seed=2, **kw))
+    assert again.status == 0
+    limit = max(6.0 * again.seconds, 1.0)
+    rids = [ctx.submit(iid, point(cfg, s=6.0 + 0.05 * k), -2, 0, seed=100 + k, max_seconds=limit, **kw)
+            for k in range(40)]
+    res = [ctx.wait(r, timeout=600.0) for r in rids]
+    st = ctx.serving_stats()
+    ctx.close()
+    shed = [r for r in res if r.status == N.QMC_ERR_TIMEOUT and r.evals == 0]
+    ok = [r for r in res if r.status == 0]
+    print(f"limit {limit:.2f} s: {len(ok)} converged, {st.shed} shed, {len(shed)} left without running, "
+          f"{len(res) - len(ok) - len(shed)} ran out of time; shed after "
+          f"{max((r.seconds for r in shed), default=0):.2f} s at most")
+    assert st.shed > 0 and len(shed) >= st.shed
+    assert len(ok) > 0
+    # turned away early, not when their limit passed
+    assert min(r.seconds for r in shed) < limit
