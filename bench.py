@@ -287,9 +287,10 @@ def main_reference(args):
 
 
 def probe_flags(L, N, prep, di, p_mixed, sh, lam, budget):
-    """Per-sector precision of a mixed pass, decided as qmc_integrate decides it: the FP32/FP64 probe
-    (qmc_probe_precision, 4096 strided points of the first shift) sends a sector to FP64 when, in any slot, the
-    summed |v32 - v64| exceeds budget * sum |v64|.  Returns (fp32 mask, probe ratios), table order."""
+    """Per-sector precision of the timed mixed pass from the FP32/FP64 probe (qmc_probe_precision, 4096 strided
+    points of the first shift): a sector goes to FP64 when, in any slot, the summed |v32 - v64| exceeds
+    budget * sum |v64| of its own -- the library's rule before it has estimates of the integral, stricter than the
+    whole-integral budget it applies afterwards.  Returns (fp32 mask, probe ratios), table order."""
     import ctypes
     import torch
     ns, slots = prep.info.n_sectors, prep.info.n_slots

@@ -103,8 +103,10 @@ typedef struct {
     int32_t grid;              /* blocks of the persistent kernel: 0 = one wave on the device */
     int32_t evaluator;         /* QMC_EVAL_* of the FP32 evaluation */
     int32_t reserved;
-    const int32_t *sector_precision; /* QMC_PREC_MIXED only: device array, one entry per sector (table order),
-                                        1 = evaluate in FP32, anything else = FP64; NULL = every sector FP32 */
+    const int32_t *sector_precision; /* QMC_PREC_MIXED only: device array, one entry per sector (table order):
+                                        1 = evaluate in FP32; 2 + L (0 <= L < QMC_ISLAND_LEVELS) = FP32 except
+                                        at the sector's island points of level L, which run in FP64 (see
+                                        qmc_probe_islands); anything else = FP64.  NULL = every sector FP32 */
     const int32_t *sector_active;    /* HOST array, one entry per sector (table order): nonzero = evaluate this
                                         sector; NULL = every sector.  The pass writes sums/fails of the evaluated
                                         sectors only and leaves the others' entries as they were, so passes of
@@ -204,6 +206,25 @@ int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const q
  */
 int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
                         const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream);
+
+/*
+ * FP64 islands.  The subtraction of Eq. 11 cancels near the faces t_j = 0 of a sector's singular variables (the
+ * remark after Eq. 12): that is where FP32 loses the digits a sector's error budget needs.  A mixed pass can keep
+ * such a sector in FP32 and evaluate only its island points in FP64.  A lattice point is an island at level L
+ * when prod_{j singular} (k_j + 1) / n < 10^-(L+1), k_j = floor(n x_j) the integer part of its shifted lattice
+ * coordinate; the product is taken in FP32, each factor and product correctly rounded, floored at 1e-30 after
+ * each factor.  Its island bin is the number of levels it is an island at (0 .. QMC_ISLAND_LEVELS).
+ *
+ * qmc_probe_islands -- qmc_probe_precision's sample and output, and in addition, per sector and island bin,
+ * the sample points in the bin and per slot the sum of |v32 - v64| over them:
+ *   bins_dev[(s * QMC_ISLAND_BINS + b) * (1 + n_slots) + 0]        = points of sector s in bin b
+ *   bins_dev[(s * QMC_ISLAND_BINS + b) * (1 + n_slots) + 1 + slot] = sum over them of |v32 - v64| in that slot
+ * With islands at level L the FP32 points are those of bins 0..L.  bins_dev must not be NULL (QMC_ERR_ARG).
+ */
+#define QMC_ISLAND_LEVELS 6
+#define QMC_ISLAND_BINS (QMC_ISLAND_LEVELS + 1)
+int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
+                      const double *lambda_dev, int64_t n_sample, double *out_dev, double *bins_dev, void *stream);
 
 /*
  * Generated evaluators (the paper evaluates a fixed, hand-written integrand per sector; this is the
@@ -363,6 +384,8 @@ typedef struct {
     double kernel_ms;                 /* device time of the evaluation kernels, all passes */
     int32_t passes, lambda_halvings, fp64_reruns, sign_failures;
     double queued_seconds;            /* serving: time between qmc_submit and admission */
+    int32_t island_sectors;           /* mixed: sectors in FP32 with FP64 islands (fp64_reruns: sectors in FP64) */
+    int32_t reserved;
 } qmc_result;
 
 typedef struct {

@@ -30,6 +30,8 @@ QMC_ERR_CODEGEN = -13
 QMC_MAX_DIM = 6
 QMC_MAX_SLOTS = 5
 QMC_MAX_ORDERS = 8
+QMC_ISLAND_LEVELS = 6
+QMC_ISLAND_BINS = QMC_ISLAND_LEVELS + 1
 QMC_PREC_FP64 = 0
 QMC_PREC_MIXED = 1
 QMC_EVAL_AUTO = 0
@@ -79,7 +81,8 @@ class qmc_result(ctypes.Structure):
                 ("value", (c_double * 2) * QMC_MAX_ORDERS), ("error", (c_double * 2) * QMC_MAX_ORDERS),
                 ("n_final", c_int64), ("evals", c_int64), ("seconds", c_double), ("kernel_ms", c_double),
                 ("passes", c_int32), ("lambda_halvings", c_int32), ("fp64_reruns", c_int32),
-                ("sign_failures", c_int32), ("queued_seconds", c_double)]
+                ("sign_failures", c_int32), ("queued_seconds", c_double), ("island_sectors", c_int32),
+                ("reserved", c_int32)]
 
 
 class qmc_serving_stats(ctypes.Structure):
@@ -117,6 +120,8 @@ PROTOTYPES = {
                                     c_void_p]),
     "qmc_probe_precision": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_int64, c_void_p,
                                     c_void_p]),
+    "qmc_probe_islands": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_int64, c_void_p,
+                                  c_void_p, c_void_p]),
     "qmc_eval_sums_noalloc": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
     "qmc_autotune_scratch_bytes": (c_size_t, [c_void_p, POINTER(qmc_pass)]),

@@ -30,9 +30,10 @@
 
 /* the serving loop's admission takes its load estimates times this factor before comparing them with limits */
 #define QMC_SHED_MARGIN 1.25
-/* cost of an FP64 evaluation per algorithmic flop relative to FP32, for charging a shared round's time to its
-   requests (the two generated kernels' measured rates on six-dimensional sectors differ by ~30x) */
-#define QMC_FP64_WEIGHT 30.0
+/* cost of an FP64 evaluation per algorithmic flop relative to FP32 (the two generated kernels' measured rates
+   on six-dimensional sectors differ by ~30x): for charging a shared round's time to its requests, and for the
+   choice of each sector's precision */
+#define QMC_FP64_COST 30.0
 
 namespace {
 
@@ -264,14 +265,18 @@ struct IntegState {
         }
     }
 
-    /* Precision of each sector from the FP32/FP64 probe (sums over n_samp points per sector and slot of |v64|,
-       |v32 - v64|, v32 - v64).  The FP32 error budget is budget = fp32_budget * rel_tol of the integral: per eps
-       order k, the mean |v32 - v64| per point of the sectors kept in FP32 (a bound on their bias in that order)
-       may add up to budget * |T_k| (order_totals), with the floor 1e-6 max_k |T_k| of the convergence test.
-       Sectors are kept in FP32 in order of their largest share of that budget until it is spent; the rest run in
-       FP64.  Without totals yet (before the first evaluation) each sector is held to budget * sum |v64| of its
-       own (per slot), and the decision is provisional: revisit_precision takes it again on the same probe once
-       totals exist.  Non-finite FP32 values and class-2 sectors always take FP64. */
+    /* Precision of each sector from the FP32/FP64 probe with island bins (qmc_probe_islands: pr holds the probe's
+       n_sectors x n_slots x 4 sums, then n_sectors x QMC_ISLAND_BINS x (1 + n_slots) bins, over n_samp points per
+       sector).  Options per sector: FP32 (code 1), FP32 with FP64 islands at level L (code 2 + L: the FP32 error
+       of bins 0..L remains, the points of the other bins cost FP64), FP64 (code 0).  An option's error per slot
+       is its mean |v32 - v64| per point; its cost is the sector's algorithmic flop per point, FP64 evaluations
+       counted QMC_FP64_COST times.  The FP32 error budget is budget = fp32_budget * rel_tol of the integral: per
+       eps order k, the errors of all sectors' options may add up to budget * |T_k| (order_totals), with the floor
+       1e-6 max_k |T_k| of the convergence test.  Each sector takes the option of least cost + mu * sum_k err_k /
+       lim_k, with the smallest mu (bisection) that keeps every order within its limit.  Without totals yet (before
+       the first evaluation) each sector takes its cheapest option whose error is within budget * mean |v64| of
+       its own in every slot, and the decision is provisional: revisit_precision takes it again on the same probe
+       once totals exist.  An option with a non-finite FP32 error is never taken; class-2 sectors take FP64. */
     void set_precision(const std::vector<double> &pr, int64_t n_samp, qmc_result &res) {
         const double budget = (opt.fp32_budget > 0 ? opt.fp32_budget : 0.1) * opt.rel_tol;
         const int sl = h->n_slots;
@@ -290,44 +295,106 @@ struct IntegState {
         for (int k = 0; k < K; ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
         for (int k = 0; k < K; ++k) lim[k] = budget * std::max(std::hypot(Tr[k], Ti[k]), 1e-6 * tmax);
         const double per = 1.0 / (double)std::max<int64_t>(n_samp, 1);
-        std::vector<char> bad(ns, 0);
-        std::vector<double> share(ns, 0.0);
+        const double *bins = pr.data() + (size_t)ns * sl * 4;
+        const int per_bin = 1 + sl;
+        /* options: 0 = FP32, 1 + L = islands at level L, NOPT - 1 = FP64 */
+        const int NOPT = QMC_ISLAND_LEVELS + 2;
+        std::vector<double> cost((size_t)ns * NOPT), err((size_t)ns * NOPT * sl, 0.0), own((size_t)ns * sl);
+        std::vector<char> ok((size_t)ns * NOPT, 1);
         for (int s = 0; s < ns; ++s) {
-            bad[s] = fp64_only[s] != 0;
-            for (int o = 0; o < sl; ++o) {
-                const double *v = &pr[((size_t)s * sl + o) * 4];
-                if (!std::isfinite(v[1])) bad[s] = 1;
-                if (tmax <= 0.0) {
-                    if (v[1] > budget * v[0]) bad[s] = 1;
-                } else {
-                    const double l = lim[o - sig[s] + maxsig];
-                    share[s] = std::max(share[s], l > 0.0 ? v[1] * per / l : (v[1] > 0.0 ? 1e300 : 0.0));
+            const double *bs = bins + (size_t)s * QMC_ISLAND_BINS * per_bin;
+            for (int o = 0; o < sl; ++o) own[(size_t)s * sl + o] = pr[((size_t)s * sl + o) * 4] * per;
+            for (int q = 0; q < NOPT; ++q) {
+                const int top = q == NOPT - 1 ? -1 : (q == 0 ? QMC_ISLAND_BINS - 1 : q - 1); /* FP32 bins 0..top */
+                double island = 0.0;
+                for (int b = top + 1; b < QMC_ISLAND_BINS; ++b) island += bs[b * per_bin] * per;
+                cost[(size_t)s * NOPT + q] = flops[s] * (q == NOPT - 1 ? QMC_FP64_COST : 1.0 + QMC_FP64_COST * island);
+                for (int o = 0; o < sl; ++o) {
+                    double e = 0.0;
+                    for (int b = 0; b <= top; ++b) e += bs[b * per_bin + 1 + o] * per;
+                    err[((size_t)s * NOPT + q) * sl + o] = e;
+                    if (!std::isfinite(e)) ok[(size_t)s * NOPT + q] = 0;
                 }
             }
+            if (fp64_only[s])
+                for (int q = 0; q < NOPT - 1; ++q) ok[(size_t)s * NOPT + q] = 0;
         }
-        if (tmax > 0.0) {
-            std::vector<int> order;
-            for (int s = 0; s < ns; ++s)
-                if (!bad[s]) order.push_back(s);
-            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return share[a] < share[b]; });
-            std::vector<double> used(K, 0.0);
-            for (int s : order) {
-                bool fits = true;
-                for (int o = 0; o < sl && fits; ++o) {
-                    const int k = o - sig[s] + maxsig;
-                    fits = used[k] + pr[((size_t)s * sl + o) * 4 + 1] * per <= lim[k];
+        std::vector<int> pick(ns, NOPT - 1);
+        if (tmax <= 0.0) {
+            for (int s = 0; s < ns; ++s) {
+                double best = std::numeric_limits<double>::infinity();
+                for (int q = 0; q < NOPT; ++q) {
+                    if (!ok[(size_t)s * NOPT + q]) continue;
+                    bool fits = true;
+                    for (int o = 0; o < sl && fits; ++o)
+                        fits = err[((size_t)s * NOPT + q) * sl + o] <= budget * own[(size_t)s * sl + o];
+                    if (fits && cost[(size_t)s * NOPT + q] < best) {
+                        best = cost[(size_t)s * NOPT + q];
+                        pick[s] = q;
+                    }
                 }
-                if (!fits) {
-                    bad[s] = 1;
-                    continue;
+            }
+        } else {
+            auto choose = [&](double mu, std::vector<int> &out) {
+                std::vector<double> used(K, 0.0);
+                for (int s = 0; s < ns; ++s) {
+                    double best = std::numeric_limits<double>::infinity();
+                    int bq = NOPT - 1;
+                    for (int q = 0; q < NOPT; ++q) {
+                        if (!ok[(size_t)s * NOPT + q]) continue;
+                        double pen = 0.0;
+                        for (int o = 0; o < sl; ++o) {
+                            const double e = err[((size_t)s * NOPT + q) * sl + o], l = lim[o - sig[s] + maxsig];
+                            pen += l > 0.0 ? e / l : (e > 0.0 ? std::numeric_limits<double>::infinity() : 0.0);
+                        }
+                        const double v = cost[(size_t)s * NOPT + q] + mu * pen;
+                        if (v < best) {
+                            best = v;
+                            bq = q;
+                        }
+                    }
+                    out[s] = bq;
+                    for (int o = 0; o < sl; ++o) used[o - sig[s] + maxsig] += err[((size_t)s * NOPT + bq) * sl + o];
                 }
-                for (int o = 0; o < sl; ++o) used[o - sig[s] + maxsig] += pr[((size_t)s * sl + o) * 4 + 1] * per;
+                for (int k = 0; k < K; ++k)
+                    if (used[k] > lim[k]) return false;
+                return true;
+            };
+            std::vector<int> cand(ns);
+            if (!choose(0.0, pick)) {
+                /* the smallest feasible mu, bracketed by doubling and then bisected in log space */
+                double lo = 0.0, hi = 1.0;
+                double total = 0.0;
+                for (int s = 0; s < ns; ++s) total += flops[s];
+                hi = std::max(total, 1.0) * 1e-12;
+                int guard = 0;
+                while (!choose(hi, cand) && guard++ < 400) {
+                    lo = hi;
+                    hi *= 2.0;
+                }
+                if (guard > 400) {
+                    for (int s = 0; s < ns; ++s) pick[s] = NOPT - 1;
+                } else {
+                    pick = cand;
+                    for (int it = 0; it < 48 && (lo <= 0.0 || hi / lo > 1.0 + 1e-3); ++it) {
+                        const double mid = lo > 0.0 ? std::sqrt(lo * hi) : hi * 0.5;
+                        if (choose(mid, cand)) {
+                            hi = mid;
+                            pick = cand;
+                        } else {
+                            lo = mid;
+                        }
+                    }
+                }
             }
         }
         res.fp64_reruns = 0;
+        res.island_sectors = 0;
         for (int s = 0; s < ns; ++s) {
-            prec[s] = bad[s] ? 0 : 1;
-            res.fp64_reruns += bad[s];
+            const int q = pick[s];
+            prec[s] = q == NOPT - 1 ? 0 : (q == 0 ? 1 : 2 + (q - 1));
+            res.fp64_reruns += q == NOPT - 1;
+            res.island_sectors += q > 0 && q < NOPT - 1;
         }
         probe_due = false;
         prec_provisional = tmax <= 0.0;
@@ -565,7 +632,8 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
     if (!rc) rc = dev_reserve(c, c->sums, st.sums.size() * sizeof(double));
     if (!rc) rc = dev_reserve(c, c->fails, st.fails.size() * sizeof(int64_t));
     if (!rc && st.mixed) rc = dev_reserve(c, c->prec, ns * sizeof(int32_t));
-    if (!rc && st.mixed) rc = dev_reserve(c, c->probe, (size_t)ns * h->n_slots * 4 * sizeof(double));
+    const size_t probe_words = (size_t)ns * h->n_slots * 4, bin_words = (size_t)ns * QMC_ISLAND_BINS * (1 + h->n_slots);
+    if (!rc && st.mixed) rc = dev_reserve(c, c->probe, (probe_words + bin_words) * sizeof(double));
     if (rc) return res->status = rc;
     float kernel_ms_total = 0.f;
     std::vector<qmc_pass> passes;
@@ -577,9 +645,10 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
                                          c->stream));
         if (!rc && st.probe_item >= 0) {
             /* FP32 budget of Sec. II's cancellation-prone sectors: the probe decides which sectors stay in FP32 */
-            std::vector<double> pr((size_t)ns * h->n_slots * 4);
-            rc = qmc_probe_precision(st.packed, I.dpacked.p, &passes[st.probe_item], (const double *)c->shifts.p,
-                                     (const double *)c->lambda.p, st.probe_samples(), (double *)c->probe.p, c->stream);
+            std::vector<double> pr(probe_words + bin_words);
+            rc = qmc_probe_islands(st.packed, I.dpacked.p, &passes[st.probe_item], (const double *)c->shifts.p,
+                                   (const double *)c->lambda.p, st.probe_samples(), (double *)c->probe.p,
+                                   (double *)c->probe.p + probe_words, c->stream);
             if (!rc)
                 rc = cuda_status(cudaMemcpyAsync(pr.data(), c->probe.p, pr.size() * sizeof(double),
                                                  cudaMemcpyDeviceToHost, c->stream));
@@ -771,7 +840,9 @@ int admit(Serving *S, qmc_ctx *c, Request &r) {
     if (!rc) rc = dev_reserve(c, r.dsums, r.st.sums.size() * sizeof(double));
     if (!rc) rc = dev_reserve(c, r.dfails, r.st.fails.size() * sizeof(int64_t));
     if (!rc) rc = dev_reserve(c, r.dprec, ns * sizeof(int32_t));
-    if (!rc) rc = dev_reserve(c, r.dprobe, (size_t)ns * h->n_slots * 4 * sizeof(double));
+    if (!rc)
+        rc = dev_reserve(c, r.dprobe,
+                         ((size_t)ns * h->n_slots * 4 + (size_t)ns * QMC_ISLAND_BINS * (1 + h->n_slots)) * sizeof(double));
     if (rc) return rc;
     rc = cuda_status(cudaMemcpyAsync(r.dpacked.p, r.packed.data(), r.packed.size(), cudaMemcpyHostToDevice, S->stream));
     if (!rc)
@@ -792,9 +863,11 @@ int gen_ready(const Request &r) {
    must already be on the device */
 int probe(Serving *S, Request &r) {
     const PackedHeader *h = r.st.h;
-    std::vector<double> pr((size_t)h->n_sectors * h->n_slots * 4);
-    int rc = qmc_probe_precision(r.packed.data(), r.dpacked.p, &r.passes[r.st.probe_item], (const double *)r.dshifts.p,
-                                 (const double *)r.dlambda.p, r.st.probe_samples(), (double *)r.dprobe.p, S->stream);
+    const size_t probe_words = (size_t)h->n_sectors * h->n_slots * 4;
+    std::vector<double> pr(probe_words + (size_t)h->n_sectors * QMC_ISLAND_BINS * (1 + h->n_slots));
+    int rc = qmc_probe_islands(r.packed.data(), r.dpacked.p, &r.passes[r.st.probe_item], (const double *)r.dshifts.p,
+                               (const double *)r.dlambda.p, r.st.probe_samples(), (double *)r.dprobe.p,
+                               (double *)r.dprobe.p + probe_words, S->stream);
     if (!rc)
         rc = cuda_status(cudaMemcpyAsync(pr.data(), r.dprobe.p, pr.size() * sizeof(double), cudaMemcpyDeviceToHost,
                                          S->stream));
@@ -1006,7 +1079,7 @@ void serve_loop(qmc_ctx *c) {
         if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
         /* the round's time (the whole iteration: admission, preparation, probes, the batch, the copies back) is
            charged to its requests in proportion to their evaluations' algorithmic flop, FP64 evaluations
-           weighted by QMC_FP64_WEIGHT */
+           weighted by QMC_FP64_COST */
         const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_iter).count();
         std::vector<double> wv(batch.size(), 0.0);
         double round_work = 0.0;
@@ -1019,7 +1092,7 @@ void serve_loop(qmc_ctx *c) {
                 for (int s = 0; s < r.st.ns; ++s)
                     if (!p.sector_active || p.sector_active[s]) {
                         const bool f32 = p.precision == QMC_PREC_MIXED && r.st.prec[s] != 0;
-                        wv[i] += fl[s] * (double)r.st.m * (double)p.lattice.n * (f32 ? 1.0 : QMC_FP64_WEIGHT);
+                        wv[i] += fl[s] * (double)r.st.m * (double)p.lattice.n * (f32 ? 1.0 : QMC_FP64_COST);
                     }
             round_work += wv[i];
         }

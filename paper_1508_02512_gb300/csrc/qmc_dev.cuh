@@ -518,6 +518,52 @@ DEV uint32_t wrap_threshold(double delta, uint32_t n, double invn) {
     return R;
 }
 
+/* ------------------------------------------------------------------ FP64 islands of a mixed pass
+ * The subtraction of Eq. 11 cancels near the faces t_j = 0 of the singular variables (the remark after Eq. 12),
+ * and that is where FP32 loses the digits a sector's error budget needs.  A mixed pass may evaluate a sector in
+ * FP32 except at its island points, which the FP64 kernel evaluates: at level L, the points whose product over
+ * the singular variables of (k_j + 1) / n is below 10^-(L+1), k_j = floor(n x_j) the integer part of the shifted
+ * lattice coordinate (x_j = (k_j + b_j) / n, 0 <= b_j < 1).  The FP32 kernels, the FP64 kernel and the probe take
+ * this decision with the functions below alone -- integer steps and correctly rounded FP32 operations -- so
+ * every kernel sees the same islands. */
+DEV uint32_t shift_floor(double delta, uint32_t n) {
+    const double fl = floor(__dmul_rn(delta, (double)n));
+    return fl >= (double)n ? n - 1u : (uint32_t)fl;
+}
+
+DEV uint32_t shifted_index(uint32_t r, uint32_t a, uint32_t n) {
+    const uint32_t k = r + a;
+    return k >= n ? k - n : k;
+}
+
+DEV float island_rn(uint32_t n) { return __frcp_rn(__uint2float_rn(n)); }
+
+/* prod over the singular variables (mask) of (k_j + 1) / n, floored at 1e-30 after each factor (no subnormals) */
+template <int S>
+DEV float island_key(const uint32_t (&k)[S], unsigned mask, float rn) {
+    float c = 1.f;
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+        if ((mask >> j) & 1u) c = fmaxf(__fmul_rn(c, __fmul_rn(__uint2float_rn(k[j] + 1u), rn)), 1e-30f);
+    return c;
+}
+
+/* the threshold of level L: 10^-(L+1) rounded to FP32 */
+DEV float island_xi(int L) {
+    return L == 0 ? 1e-1f : L == 1 ? 1e-2f : L == 2 ? 1e-3f : L == 3 ? 1e-4f : L == 4 ? 1e-5f : 1e-6f;
+}
+
+/* the number of levels a point with this key is an island at */
+DEV int island_bin(float key) {
+    int b = 0;
+#pragma unroll
+    for (int L = 0; L < QMC_ISLAND_LEVELS; ++L) b += key < island_xi(L) ? 1 : 0;
+    return b;
+}
+
+/* island level of a sector precision code of a mixed pass (2 + L), or -1 */
+DEV int island_level(int code) { return code >= 2 && code < 2 + QMC_ISLAND_LEVELS ? code - 2 : -1; }
+
 DEV void kahan_add(double &s, double &c, double v) {
     const double y = v - c;
     const double t = s + y;
@@ -550,9 +596,12 @@ DEV void eval_f64_body(const JobTable &jt) {
     __shared__ int s_job;
     __shared__ double s_red[16][2 * (MAXM + 1)];
     __shared__ uint32_t s_fail[16];
+    /* per warp: lattice residues r_j of the points gathered for evaluation (at most 63 wait between batches) */
+    __shared__ uint32_t s_queue[8][64 * S];
     const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
     const PackedTerm *T = reinterpret_cast<const PackedTerm *>(smem + sizeof(PackedSector));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint32_t *queue = s_queue[warp & 7];
     int cur = -1, cur_job = -1;
     logtab_init(); /* made visible by the __syncthreads() after the first item fetch */
     for (;;) {
@@ -573,13 +622,17 @@ DEV void eval_f64_body(const JobTable &jt) {
         const int shift = (int)(rem / J.chunks);
         const long long chunk = rem - (long long)shift * J.chunks;
         const int psec = J.sector_begin + ls;
+        int level = -1; /* island level: this kernel evaluates only the sector's island points */
         if (J.sector_prec) {
-            /* mixed pass: items of sectors evaluated in FP32 belong to the other kernel */
+            /* mixed pass: items of sectors evaluated in FP32 belong to the other kernel; of sectors with FP64
+               islands, this kernel takes the islands and writes the item's partial first (it launches first) */
             const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
-            if (J.sector_prec[gps->orig_index] == 1) {
+            const int code = J.sector_prec[gps->orig_index];
+            if (code == 1) {
                 __syncthreads();
                 continue;
             }
+            level = island_level(code);
         }
         if (psec != cur || jb != cur_job) {
             stage_sector(J.packed, J.sectors_off, J.terms_off, psec, smem);
@@ -593,7 +646,7 @@ DEV void eval_f64_body(const JobTable &jt) {
         const double invn = J.invn;
         const double lam = J.lambda[sec.orig_index];
         double delta[S];
-        uint32_t rj[S], Rj[S], zs[S];
+        uint32_t rj[S], Rj[S], zs[S], aj[S];
         const long long i0 = chunk * (long long)blockDim.x * jt.P + threadIdx.x;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
@@ -601,19 +654,53 @@ DEV void eval_f64_body(const JobTable &jt) {
             rj[j] = (uint32_t)(((unsigned long long)i0 * J.z[j]) % n);
             Rj[j] = wrap_threshold(delta[j], n, invn);
             zs[j] = J.zstep[j];
+            aj[j] = shift_floor(delta[j], n);
         }
-        /* a thread sums its P points plainly; the block combines threads by a shuffle tree, warps and items
+        const float rn = island_rn(n), xi = island_xi(level < 0 ? 0 : level);
+        const unsigned smask = (unsigned)sec.sing_mask;
+        /* a thread sums its points plainly; the block combines threads by a shuffle tree, warps and items
            with compensated (Kahan) sums */
         double acc[2 * (MAXM + 1)];
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = 0.0;
         uint32_t fails = 0;
-        for (int p = 0; p < jt.P; ++p) {
-            const long long i = i0 + (long long)p * blockDim.x;
-            if (i < (long long)n) {
+        /* The warp gathers its points (every point, or the islands) into its queue 32 lanes at a time and
+           evaluates them in batches of 32, so island points keep whole warps busy.  With every point taken,
+           lane l evaluates its own points in order, as a plain loop would. */
+        int qn = 0, p = 0;
+        for (;;) {
+            while (qn < 32 && p < jt.P) {
+                const long long i = i0 + (long long)p * blockDim.x;
+                bool take = i < (long long)n;
+                if (take && level >= 0) {
+                    uint32_t k[S];
+#pragma unroll
+                    for (int j = 0; j < S; ++j) k[j] = shifted_index(rj[j], aj[j], n);
+                    take = island_key<S>(k, smask, rn) < xi;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (take) {
+                    const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+#pragma unroll
+                    for (int j = 0; j < S; ++j) queue[pos * S + j] = rj[j];
+                }
+                qn += __popc(bal);
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    const uint32_t v = rj[j] + zs[j];
+                    rj[j] = v >= n ? v - n : v;
+                }
+                ++p;
+            }
+            if (qn == 0) break;
+            __syncwarp();
+            if (lane < qn) {
                 double x[S];
 #pragma unroll
-                for (int j = 0; j < S; ++j) x[j] = fma((double)rj[j], invn, delta[j]) - (rj[j] >= Rj[j] ? 1.0 : 0.0);
+                for (int j = 0; j < S; ++j) {
+                    const uint32_t r = queue[lane * S + j];
+                    x[j] = fma((double)r, invn, delta[j]) - (r >= Rj[j] ? 1.0 : 0.0);
+                }
                 cd val[MAXM + 1];
                 if constexpr (TAYLOR) {
                     double v[MAXM + 1];
@@ -629,11 +716,14 @@ DEV void eval_f64_body(const JobTable &jt) {
                     acc[2 * m + 1] += val[m].y;
                 }
             }
+            __syncwarp();
+            const int rest = qn > 32 ? qn - 32 : 0;
+            if (lane < rest) {
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-                const uint32_t v = rj[j] + zs[j];
-                rj[j] = v >= n ? v - n : v;
+                for (int j = 0; j < S; ++j) queue[lane * S + j] = queue[(32 + lane) * S + j];
             }
+            __syncwarp();
+            qn = rest;
         }
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) {
@@ -1330,18 +1420,14 @@ DEV void point_integrand_f(const PackedSector &s, const Pol &P, const float *x, 
 
 /* x = ((r + a) mod n + b)/n and 1 - x = ((n - 1 - (r + a) mod n) + (1 - b))/n, with delta * n = a + b */
 DEV void lattice_f32(uint32_t r, uint32_t a, float b, uint32_t n, float invnf, float &x, float &y) {
-    uint32_t k = r + a;
-    k = k >= n ? k - n : k;
+    const uint32_t k = shifted_index(r, a, n);
     x = ((float)k + b) * invnf;
     y = ((float)(n - 1u - k) + (1.f - b)) * invnf;
 }
 
 DEV void split_shift(double delta, uint32_t n, uint32_t &a, float &b) {
-    const double dn = delta * (double)n;
-    double fl = floor(dn);
-    if (fl >= (double)n) fl = (double)(n - 1u);
-    a = (uint32_t)fl;
-    b = (float)(dn - fl);
+    a = shift_floor(delta, n);
+    b = (float)(__dmul_rn(delta, (double)n) - (double)a);
 }
 
 /* TwoSum: s + v = (s') + err exactly; the error goes into the compensation term */
@@ -1395,10 +1481,13 @@ DEV void eval_f32_body(const JobTable &jt) {
         const int shift = (int)(rem / J.chunks);
         const long long chunk = rem - (long long)shift * J.chunks;
         const int psec = J.sector_begin + ls;
+        int level = -1; /* island level: the FP64 kernel has evaluated the island points and written the partial */
         if (J.sector_prec) {
             /* mixed pass: items of sectors evaluated in FP64 belong to the other kernel */
             const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
-            if (J.sector_prec[gps->orig_index] != 1) {
+            const int code = J.sector_prec[gps->orig_index];
+            level = island_level(code);
+            if (code != 1 && level < 0) {
                 __syncthreads();
                 continue;
             }
@@ -1427,9 +1516,17 @@ DEV void eval_f32_body(const JobTable &jt) {
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
         uint32_t fails = 0;
+        const float rn = island_rn(n), xi = island_xi(level < 0 ? 0 : level);
         for (int p = 0; p < jt.P; ++p) {
             const long long i = i0 + (long long)p * blockDim.x;
-            if (i < (long long)n) {
+            bool take = i < (long long)n;
+            if (take && level >= 0) {
+                uint32_t k[S];
+#pragma unroll
+                for (int j = 0; j < S; ++j) k[j] = shifted_index(rj[j], aj[j], n);
+                take = !(island_key<S>(k, (unsigned)sec.sing_mask, rn) < xi);
+            }
+            if (take) {
                 float x[S], y[S];
 #pragma unroll
                 for (int j = 0; j < S; ++j) lattice_f32(rj[j], aj[j], bj[j], n, invnf, x[j], y[j]);
@@ -1471,12 +1568,13 @@ DEV void eval_f32_body(const JobTable &jt) {
                 double s2 = 0.0, c2 = 0.0;
                 if (q < 2 * (MAXM + 1))
                     for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2, s_red[w][q]);
-                J.partials[local * J.n_slots * 2 + q] = s2 - c2;
+                double *dst = &J.partials[local * J.n_slots * 2 + q];
+                *dst = level >= 0 ? *dst + (s2 - c2) : s2 - c2;
             }
             if (q == 0) {
                 uint32_t tf = 0;
                 for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
-                J.part_fails[local] = tf;
+                J.part_fails[local] = level >= 0 ? J.part_fails[local] + tf : tf;
             }
         }
         __syncthreads();
@@ -1602,31 +1700,44 @@ DEV void eval_G_f2(const PackedSector &s, const Pol &P, unsigned Y, const float2
         float2 g[S], h[S * (S + 1) / 2];
         P.GH(Y, tt, g, h);
         cf dets[2];
-#pragma unroll 1
-        for (int k = 0; k < 2; ++k) {
-            /* the determinant per lane, as eval_G_f computes it (one lane at a time: registers) */
-            if constexpr (S >= 4) {
-                float sq[S];
+        if constexpr (S >= 4) {
+            /* the matrix entries of both lanes in packed form (rounded as eval_G_f rounds them), then the
+               elimination per lane with the lane fixed at compile time (no per-element lane selects) */
+            float2 sq[S];
 #pragma unroll
-                for (int j = 0; j < S; ++j) {
-                    const float pj = lane(tt[j], k) * lane(ttm[j], k);
-                    sq[j] = pj > 0.f ? pj * rsqrtf(pj) : 0.f;
+            for (int j = 0; j < S; ++j) {
+                const float2 pj = mul2(tt[j], ttm[j]);
+                sq[j] = make_float2(pj.x > 0.f ? pj.x * rsqrtf(pj.x) : 0.f, pj.y > 0.f ? pj.y * rsqrtf(pj.y) : 0.f);
+            }
+            float2 bm[S * (S + 1) / 2];
+            int p = 0;
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+#pragma unroll
+                for (int i = j; i < S; ++i) {
+                    bm[p] = (i == j) ? fma2(sub2(ttm[j], tt[j]), g[j], mul2(mul2(tt[j], ttm[j]), h[p]))
+                                     : mul2(mul2(sq[j], sq[i]), h[p]);
+                    ++p;
                 }
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
                 cf N[S * (S + 1) / 2];
-                int p = 0;
+                int q = 0;
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
 #pragma unroll
                     for (int i = j; i < S; ++i) {
-                        const float tj = lane(tt[j], k), mj = lane(ttm[j], k);
-                        const float b = (i == j) ? fmaf(mj - tj, lane(g[j], k), tj * mj * lane(h[p], k))
-                                                 : sq[j] * sq[i] * lane(h[p], k);
-                        N[p] = mkf(i == j ? 1.f : 0.f, -lam * b);
-                        ++p;
+                        N[q] = mkf(i == j ? 1.f : 0.f, -lam * (k ? bm[q].y : bm[q].x));
+                        ++q;
                     }
                 }
                 dets[k] = det_sym_f<S>(N);
-            } else {
+            }
+        } else {
+#pragma unroll 1
+            for (int k = 0; k < 2; ++k) {
+                /* the determinant per lane, as eval_G_f computes it (one lane at a time: registers) */
                 float A[S][S];
                 int p = 0;
 #pragma unroll
@@ -1850,9 +1961,12 @@ DEV void eval_f32x2_body(const JobTable &jt) {
         const int shift = (int)(rem / J.chunks);
         const long long chunk = rem - (long long)shift * J.chunks;
         const int psec = J.sector_begin + ls;
+        int level = -1; /* island level: the FP64 kernel has evaluated the island points and written the partial */
         if (J.sector_prec) {
             const PackedSector *gps = reinterpret_cast<const PackedSector *>(J.packed + J.sectors_off) + psec;
-            if (J.sector_prec[gps->orig_index] != 1) {
+            const int code = J.sector_prec[gps->orig_index];
+            level = island_level(code);
+            if (code != 1 && level < 0) {
                 __syncthreads();
                 continue;
             }
@@ -1881,6 +1995,7 @@ DEV void eval_f32x2_body(const JobTable &jt) {
 #pragma unroll
         for (int q = 0; q < 2 * (MAXM + 1); ++q) acc[q] = cmp[q] = 0.f;
         uint32_t fails = 0;
+        const float rn = island_rn(n), xi = island_xi(level < 0 ? 0 : level);
         for (int p = 0; p < jt.P; p += 2) {
             bool live[2];
             float2 x[S], y[S];
@@ -1888,6 +2003,12 @@ DEV void eval_f32x2_body(const JobTable &jt) {
             for (int k = 0; k < 2; ++k) {
                 const long long i = i0 + (long long)(p + k) * blockDim.x;
                 live[k] = (p + k < jt.P) && i < (long long)n;
+                if (live[k] && level >= 0) {
+                    uint32_t kk[S];
+#pragma unroll
+                    for (int j = 0; j < S; ++j) kk[j] = shifted_index(rj[j], aj[j], n);
+                    live[k] = !(island_key<S>(kk, (unsigned)sec.sing_mask, rn) < xi);
+                }
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
                     float xv, yv;
@@ -1940,12 +2061,13 @@ DEV void eval_f32x2_body(const JobTable &jt) {
                 double s2 = 0.0, c2v = 0.0;
                 if (q < 2 * (MAXM + 1))
                     for (int w = 0; w < nwarps; ++w) kahan_add(s2, c2v, s_red[w][q]);
-                J.partials[local * J.n_slots * 2 + q] = s2 - c2v;
+                double *dst = &J.partials[local * J.n_slots * 2 + q];
+                *dst = level >= 0 ? *dst + (s2 - c2v) : s2 - c2v;
             }
             if (q == 0) {
                 uint32_t tf = 0;
                 for (int w = 0; w < nwarps; ++w) tf += s_fail[w];
-                J.part_fails[local] = tf;
+                J.part_fails[local] = level >= 0 ? J.part_fails[local] + tf : tf;
             }
         }
         __syncthreads();
@@ -1981,6 +2103,12 @@ DEV void probe_body(const ProbeArgs &a) {
     double acc[4 * (MAXM + 1)];
 #pragma unroll
     for (int q = 0; q < 4 * (MAXM + 1); ++q) acc[q] = 0.0;
+    /* island bins (when a.bins is set): per bin, the points and per slot sum |v32 - v64| */
+    constexpr int NB = QMC_ISLAND_BINS * (MAXM + 2);
+    double bacc[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) bacc[q] = 0.0;
+    const float rn = island_rn(a.n);
     uint32_t Rj[S], aj[S];
     float bj[S];
 #pragma unroll
@@ -1993,12 +2121,15 @@ DEV void probe_body(const ProbeArgs &a) {
         const unsigned long long i = (unsigned long long)k * stride;
         double x[S];
         float xf[S], yf[S];
+        uint32_t kk[S];
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             const uint32_t r = (uint32_t)((i * a.z[j]) % a.n);
             x[j] = fma((double)r, a.invn, a.shift[j]) - (r >= Rj[j] ? 1.0 : 0.0);
             lattice_f32(r, aj[j], bj[j], a.n, invnf, xf[j], yf[j]);
+            kk[j] = shifted_index(r, aj[j], a.n);
         }
+        const int bin = island_bin(island_key<S>(kk, (unsigned)sec.sing_mask, rn));
         cd v64[MAXM + 1];
         cf v32[MAXM + 1];
         point_integrand<S, DEF, MAXM>(sec, TabPol<S>{T, &sec}, x, a.r, lam, ex, v64, f64);
@@ -2010,6 +2141,14 @@ DEV void probe_body(const ProbeArgs &a) {
             acc[4 * n + 1] += hypot(dr, di);
             acc[4 * n + 2] += dr;
             acc[4 * n + 3] += di;
+        }
+#pragma unroll
+        for (int b = 0; b < QMC_ISLAND_BINS; ++b) {
+            if (b != bin) continue;
+            bacc[b * (MAXM + 2)] += 1.0;
+#pragma unroll
+            for (int n = 0; n <= MAXM; ++n)
+                bacc[b * (MAXM + 2) + 1 + n] += hypot((double)v32[n].x - v64[n].x, (double)v32[n].y - v64[n].y);
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -2027,6 +2166,26 @@ DEV void probe_body(const ProbeArgs &a) {
         if (q < 4 * (MAXM + 1))
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w][q];
         a.out[(size_t)sec.orig_index * a.n_slots * 4 + q] = v;
+    }
+    if (a.bins) {
+        __shared__ double s_bin[4][NB];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            double v = bacc[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0) s_bin[warp][q] = v;
+        }
+        __syncthreads();
+        const int per = 1 + a.n_slots;
+        for (int q = threadIdx.x; q < QMC_ISLAND_BINS * per; q += blockDim.x) {
+            const int b = q / per, e = q - b * per; /* e = 0: points; 1 + slot: errors */
+            double v = 0.0;
+            if (e < MAXM + 2)
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_bin[w][b * (MAXM + 2) + e];
+            a.bins[(size_t)sec.orig_index * QMC_ISLAND_BINS * per + q] = v;
+        }
     }
 }
 

@@ -151,6 +151,8 @@ struct ProbeArgs {
     const double *lambda;         /* per sector, table order */
     int64_t n_sample;             /* sample points per sector */
     double *out;                  /* n_sectors(table order) x n_slots x 4: sum|v64|, sum|v32-v64|, sum(v32-v64) re, im */
+    double *bins;                 /* null, or n_sectors(table order) x QMC_ISLAND_BINS x (1 + n_slots): per island
+                                     bin, the points in it and per slot sum|v32-v64| over them */
     int32_t eU0, eU1, eF0, eF1;
     int32_t smem_bytes;
 };

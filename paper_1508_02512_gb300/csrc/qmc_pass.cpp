@@ -251,6 +251,10 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
             }
         }
     }
+    /* Launch order: the map orders keys by (dim, class, series length) and then precision, so the FP64 launch
+       of a mixed pass's items precedes their FP32 launch.  Sectors with FP64 islands rely on it: the FP64 kernel
+       writes an item's island partial, the FP32 kernel then adds the rest to it. */
+    static_assert(QMC_PREC_FP64 < QMC_PREC_MIXED, "FP64 launches must sort before FP32 launches");
     int counter = 0;
     std::unique_ptr<JobTable> jt(new JobTable());
     for (auto &kv : groups) {
@@ -401,8 +405,10 @@ int qmc_eval_partials(const void *packed_host, const void *packed_dev, const qmc
     }
 }
 
-int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
-                        const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream) {
+namespace {
+
+int probe(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
+          const double *lambda_dev, int64_t n_sample, double *out_dev, double *bins_dev, void *stream) {
     const PackedHeader *h = header_of(packed_host);
     if (!h || !packed_dev || !pass || !shift_dev || !lambda_dev || !out_dev || n_sample < 1) return QMC_ERR_ARG;
     Plan pl;
@@ -428,6 +434,7 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
         a.lambda = lambda_dev;
         a.n_sample = n_sample;
         a.out = out_dev;
+        a.bins = bins_dev;
         a.eU0 = h->eU0;
         a.eU1 = h->eU1;
         a.eF0 = h->eF0;
@@ -437,6 +444,19 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
         if (rc) return rc;
     }
     return QMC_OK;
+}
+
+}  // namespace
+
+int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
+                        const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream) {
+    return probe(packed_host, packed_dev, pass, shift_dev, lambda_dev, n_sample, out_dev, nullptr, stream);
+}
+
+int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
+                      const double *lambda_dev, int64_t n_sample, double *out_dev, double *bins_dev, void *stream) {
+    if (!bins_dev) return QMC_ERR_ARG;
+    return probe(packed_host, packed_dev, pass, shift_dev, lambda_dev, n_sample, out_dev, bins_dev, stream);
 }
 
 int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const void *scratch_dev,
