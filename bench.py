@@ -8,8 +8,9 @@ decomposition, every one contour-deformed with lambda = 0.5, halved per sector w
 fails).  A step is one pass of the whole hot path over it: every sector x 16 random shifts x every point of the
 rank-1 lattice of size n = 1048573 (largest prime below 2^20), Korobov transform r = 3 -- 8.05e8 integrand
 evaluations, reduced per (sector, shift) -- in mixed precision as the library runs it: the FP32/FP64 probe
-(qmc_probe_precision, 4096 points per sector) keeps a sector in FP32 unless its FP32 error exceeds 1e-4 of its
-magnitude, and the sectors it flags run in FP64 in the same step.
+with island bins (qmc_probe_islands, 4096 points per sector) and qmc_choose_precision keep a sector in FP32 (with
+FP64 islands near its singular faces where that is cheaper) unless its FP32 error exceeds 1e-4 of its magnitude,
+and the sectors it flags run in FP64 in the same step.
 
 Output: one JSON line (rank 0).
   value      evaluations/s of the mixed step, with the table, shifts and lambda already resident on the device
@@ -286,22 +287,27 @@ def main_reference(args):
         dist.destroy_process_group()
 
 
-def probe_flags(L, N, prep, di, p_mixed, sh, lam, budget):
-    """Per-sector precision of the timed mixed pass from the FP32/FP64 probe (qmc_probe_precision, 4096 strided
-    points of the first shift): a sector goes to FP64 when, in any slot, the summed |v32 - v64| exceeds
-    budget * sum |v64| of its own -- the library's rule before it has estimates of the integral, stricter than the
-    whole-integral budget it applies afterwards.  Returns (fp32 mask, probe ratios), table order."""
+def probe_codes(L, N, prep, di, p_mixed, sh, lam, rel_tol, fp32_budget):
+    """Per-sector precision codes of the timed mixed pass, as the library chooses them before it has an estimate
+    of the integral: the FP32/FP64 probe with island bins (qmc_probe_islands, 4096 strided points of the first
+    shift) and qmc_choose_precision without sums (each sector held to fp32_budget * rel_tol of its own
+    magnitude).  Returns (codes: 1 FP32, 2 + L FP32 with FP64 islands, 0 FP64; the probe's largest ratio
+    sum|v32 - v64| / sum|v64| per sector), table order."""
     import ctypes
     import torch
     ns, slots = prep.info.n_sectors, prep.info.n_slots
     out = torch.zeros((ns, slots, 4), dtype=torch.float64, device=sh.device)
-    N.check(L.qmc_probe_precision(prep.packed, di.dpacked.data_ptr(), ctypes.byref(p_mixed), sh.data_ptr(),
-                                  lam.data_ptr(), 4096, out.data_ptr(), None), "qmc_probe_precision")
+    bins = torch.zeros((ns, N.QMC_ISLAND_BINS, 1 + slots), dtype=torch.float64, device=sh.device)
+    N.check(L.qmc_probe_islands(prep.packed, di.dpacked.data_ptr(), ctypes.byref(p_mixed), sh.data_ptr(),
+                                lam.data_ptr(), 4096, out.data_ptr(), bins.data_ptr(), None), "qmc_probe_islands")
     torch.cuda.synchronize()
-    pr = out.cpu().numpy()
+    pr = np.ascontiguousarray(out.cpu().numpy())
+    bn = np.ascontiguousarray(bins.cpu().numpy())
+    codes = np.zeros(ns, dtype=np.int32)
+    N.check(L.qmc_choose_precision(prep.packed, 0, None, None, pr.ctypes.data, bn.ctypes.data, 4096, rel_tol,
+                                   fp32_budget, codes.ctypes.data, None), "qmc_choose_precision")
     ratio = pr[:, :, 1] / np.maximum(pr[:, :, 0], 1e-300)
-    bad = np.any(pr[:, :, 1] > budget * pr[:, :, 0], axis=1) | ~np.all(np.isfinite(pr[:, :, 1]), axis=1)
-    return (~bad).astype(np.int32), ratio.max(axis=1)
+    return codes, ratio.max(axis=1)
 
 
 def start_compiles(preps):
@@ -402,10 +408,16 @@ def main_ours(args):
 
     # precision of each sector in the mixed step: the probe's decision at this lattice size
     p_probe, _k = mkpass(n, N.QMC_PREC_MIXED)
-    keep32, probe_ratio = probe_flags(L, N, prep, di, p_probe, sh, lam, FP32_BUDGET * REL_TOL)
+    codes, probe_ratio = probe_codes(L, N, prep, di, p_probe, sh, lam, REL_TOL, FP32_BUDGET)
+    keep32 = (codes != 0).astype(np.int32)
     keep64 = 1 - keep32
     n32, n64s = int(keep32.sum()), int(keep64.sum())
+    n_isl = int((codes >= 2).sum())
     p32, k32 = mkpass(n, N.QMC_PREC_MIXED, keep32) if n32 else (None, None)
+    codes_dev = None
+    if p32 is not None and n_isl:  # sectors with FP64 islands: the pass's FP64 kernel takes their island points
+        codes_dev = torch.tensor(codes, device=dev_name)
+        p32.sector_precision = codes_dev.data_ptr()
     p64m, k64 = mkpass(n, N.QMC_PREC_FP64, keep64) if n64s else (None, None)
     scr = {}
 
@@ -486,6 +498,7 @@ def main_ours(args):
     # reduction launch per pass
     cls = np.array([1 if prep.sector(s).kind == 2 else 0 for s in range(ns)])
     launches_mixed = sum(len(set(cls[np.asarray(mask) > 0])) + 1 for mask in (keep32, keep64) if np.any(mask))
+    launches_mixed += len(set(cls[codes >= 2]))  # the FP64 kernel of the FP32 pass, for island points
 
     # the FP64 pass alone (all sectors) on the smaller lattice, and the mixed pass on the same points
     p64, _ = mkpass(n64, N.QMC_PREC_FP64)
@@ -601,6 +614,7 @@ def main_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {**workload_config(cfg, n, ns, lam_desc), "fp32_sectors": n32, "fp64_sectors": n64s,
+                       "fp64_island_sectors": n_isl,
                        "fp32_budget": f"{FP32_BUDGET} x rel_tol {REL_TOL}"},
             "e2e": {"value": world * evals_step * args.steps / te, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

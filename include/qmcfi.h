@@ -227,6 +227,31 @@ int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc
                       const double *lambda_dev, int64_t n_sample, double *out_dev, double *bins_dev, void *stream);
 
 /*
+ * qmc_choose_precision -- per-sector precision codes for a mixed pass (qmc_pass.sector_precision), as qmc_integrate
+ * and the serving loop choose them.  Host-only: all arrays are host memory.
+ *   probe, bins: qmc_probe_islands' outputs (copied to the host), n_sample points per sector.
+ *   sums, n_sector, n_shifts: the current sums (qmc_eval_sums layout) and each sector's lattice size (table
+ *     order), for the estimate T_k of each eps order summed over sectors before the Gamma prefactor; sums = NULL
+ *     when no estimate exists yet.
+ *   codes: out, one per sector: 1 = FP32, 2 + L = FP32 with FP64 islands at level L, 0 = FP64.
+ *   counts: out (may be NULL): [0] sectors in FP64, [1] sectors with islands.
+ * Options per sector: FP32 (the FP32 error of every bin), islands at level L (the error of bins 0..L; the points
+ * of the other bins cost FP64) and FP64 (no error); error = mean |v32 - v64| per point per slot, cost = the
+ * sector's flop per point with FP64 evaluations counted 30 times.  The FP32 error budget is
+ * (fp32_budget > 0 ? fp32_budget : 0.1) * rel_tol: per order k the sectors' errors may add up to budget * |T_k|
+ * (floor 1e-6 max_k |T_k|).  Every sector starts at its cheapest option; while an order is over its limit, the
+ * change of one sector's option with the largest reduction of the excess per extra cost is taken; what no single
+ * change can fix goes to FP64.  Without an estimate, each sector takes its cheapest option within budget times
+ * its own mean |v64| in every slot.  An option with a non-finite FP32 error is never taken; sectors with endpoint
+ * exponents alpha <= -2 always take FP64.
+ * Errors: QMC_ERR_ARG for a NULL required pointer, n_sample < 1, negative rel_tol/fp32_budget, or sums without
+ * n_sector / n_shifts >= 1 / positive sizes.
+ */
+int qmc_choose_precision(const void *packed_host, int32_t n_shifts, const int64_t *n_sector, const double *sums,
+                         const double *probe, const double *bins, int64_t n_sample, double rel_tol,
+                         double fp32_budget, int32_t *codes, int32_t *counts);
+
+/*
  * Generated evaluators (the paper evaluates a fixed, hand-written integrand per sector; this is the
  * library's way of getting the same straight-line arithmetic for any table).  A family = the sector tables
  * with identical exponent structure (same topology and kinematic class, any kinematic point).

@@ -122,6 +122,8 @@ PROTOTYPES = {
                                     c_void_p]),
     "qmc_probe_islands": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_int64, c_void_p,
                                   c_void_p, c_void_p]),
+    "qmc_choose_precision": (c_int, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_double,
+                                     c_double, c_void_p, c_void_p]),
     "qmc_eval_sums_noalloc": (c_int, [c_void_p, c_void_p, POINTER(qmc_pass), c_void_p, c_void_p, c_void_p, c_void_p,
                                       c_void_p]),
     "qmc_autotune_scratch_bytes": (c_size_t, [c_void_p, POINTER(qmc_pass)]),

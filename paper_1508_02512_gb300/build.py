@@ -21,7 +21,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libqmcfi.so")
 ROOT = os.path.dirname(HERE)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["qmc_kernels.cu", "qmc_prepare.cpp", "qmc_pass.cpp", "qmc_context.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"]
+SOURCES = ["qmc_kernels.cu", "qmc_prepare.cpp", "qmc_pass.cpp", "qmc_context.cpp", "qmc_precision.cpp", "qmc_noalloc.cu", "qmc_jit.cpp"]
 # the ahead-of-time kernels, one translation unit per sector dimension (built in parallel)
 DIM_SOURCE = "qmc_kern_dim.cu"
 DIMS = range(1, 7)

@@ -30,10 +30,6 @@
 
 /* the serving loop's admission takes its load estimates times this factor before comparing them with limits */
 #define QMC_SHED_MARGIN 1.25
-/* cost of an FP64 evaluation per algorithmic flop relative to FP32 (the two generated kernels' measured rates
-   on six-dimensional sectors differ by ~30x): for charging a shared round's time to its requests, and for the
-   choice of each sector's precision */
-#define QMC_FP64_COST 30.0
 
 namespace {
 
@@ -240,164 +236,24 @@ struct IntegState {
         for (size_t k = 0; k < out.size(); ++k) out[k].sector_active = masks[k].empty() ? nullptr : masks[k].data();
     }
 
-    /* Per eps order k of the sector sums (slot - sigma, offset by the largest sigma): the current estimate T_k
-       summed over sectors, before the Gamma prefactor.  Called where every sector's sums belong to its rung. */
+    /* the current estimate of each eps order, summed over sectors (qmci::order_totals); called where every
+       sector's sums belong to its rung */
     void order_totals() {
-        const int sl = h->n_slots;
-        const PackedSector *ps = sectors_of(packed);
-        std::vector<int> sig(ns, 0);
-        for (int pi = 0; pi < ns; ++pi) sig[ps[pi].orig_index] = ps[pi].sigma;
-        int maxsig = 0;
-        for (int s = 0; s < ns; ++s) maxsig = std::max(maxsig, sig[s]);
-        Tr.assign(sl + maxsig, 0.0);
-        Ti.assign(sl + maxsig, 0.0);
-        for (int s = 0; s < ns; ++s) {
-            const double inv = 1.0 / ((double)m * (double)ladder[rung[s]].n);
-            for (int o = 0; o < sl; ++o) {
-                double re = 0.0, im = 0.0;
-                for (int k = 0; k < m; ++k) {
-                    re += sums[(((size_t)s * m + k) * sl + o) * 2];
-                    im += sums[(((size_t)s * m + k) * sl + o) * 2 + 1];
-                }
-                Tr[o - sig[s] + maxsig] += re * inv;
-                Ti[o - sig[s] + maxsig] += im * inv;
-            }
-        }
+        std::vector<int64_t> nv(ns);
+        for (int s = 0; s < ns; ++s) nv[s] = ladder[rung[s]].n;
+        qmci::order_totals(packed, m, nv.data(), sums.data(), Tr, Ti);
     }
 
-    /* Precision of each sector from the FP32/FP64 probe with island bins (qmc_probe_islands: pr holds the probe's
+    /* Precision of each sector (qmc_choose_precision's rule) from the probe with island bins: pr holds the probe's
        n_sectors x n_slots x 4 sums, then n_sectors x QMC_ISLAND_BINS x (1 + n_slots) bins, over n_samp points per
-       sector).  Options per sector: FP32 (code 1), FP32 with FP64 islands at level L (code 2 + L: the FP32 error
-       of bins 0..L remains, the points of the other bins cost FP64), FP64 (code 0).  An option's error per slot
-       is its mean |v32 - v64| per point; its cost is the sector's algorithmic flop per point, FP64 evaluations
-       counted QMC_FP64_COST times.  The FP32 error budget is budget = fp32_budget * rel_tol of the integral: per
-       eps order k, the errors of all sectors' options may add up to budget * |T_k| (order_totals), with the floor
-       1e-6 max_k |T_k| of the convergence test.  Each sector takes the option of least cost + mu * sum_k err_k /
-       lim_k, with the smallest mu (bisection) that keeps every order within its limit.  Without totals yet (before
-       the first evaluation) each sector takes its cheapest option whose error is within budget * mean |v64| of
-       its own in every slot, and the decision is provisional: revisit_precision takes it again on the same probe
-       once totals exist.  An option with a non-finite FP32 error is never taken; class-2 sectors take FP64. */
+       sector.  Before the first evaluation (no totals) the decision is provisional: revisit_precision takes it
+       again on the same probe once totals exist. */
     void set_precision(const std::vector<double> &pr, int64_t n_samp, qmc_result &res) {
         const double budget = (opt.fp32_budget > 0 ? opt.fp32_budget : 0.1) * opt.rel_tol;
-        const int sl = h->n_slots;
-        const PackedSector *ps = sectors_of(packed);
-        std::vector<int> sig(ns, 0);
-        for (int pi = 0; pi < ns; ++pi) sig[ps[pi].orig_index] = ps[pi].sigma;
-        int maxsig = 0;
-        for (int s = 0; s < ns; ++s) maxsig = std::max(maxsig, sig[s]);
-        const int K = sl + maxsig;
-        if ((int)Tr.size() != K) {
-            Tr.assign(K, 0.0);
-            Ti.assign(K, 0.0);
-        }
-        std::vector<double> lim(K, 0.0);
-        double tmax = 0.0;
-        for (int k = 0; k < K; ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
-        for (int k = 0; k < K; ++k) lim[k] = budget * std::max(std::hypot(Tr[k], Ti[k]), 1e-6 * tmax);
-        const double per = 1.0 / (double)std::max<int64_t>(n_samp, 1);
-        const double *bins = pr.data() + (size_t)ns * sl * 4;
-        const int per_bin = 1 + sl;
-        /* options: 0 = FP32, 1 + L = islands at level L, NOPT - 1 = FP64 */
-        const int NOPT = QMC_ISLAND_LEVELS + 2;
-        std::vector<double> cost((size_t)ns * NOPT), err((size_t)ns * NOPT * sl, 0.0), own((size_t)ns * sl);
-        std::vector<char> ok((size_t)ns * NOPT, 1);
-        for (int s = 0; s < ns; ++s) {
-            const double *bs = bins + (size_t)s * QMC_ISLAND_BINS * per_bin;
-            for (int o = 0; o < sl; ++o) own[(size_t)s * sl + o] = pr[((size_t)s * sl + o) * 4] * per;
-            for (int q = 0; q < NOPT; ++q) {
-                const int top = q == NOPT - 1 ? -1 : (q == 0 ? QMC_ISLAND_BINS - 1 : q - 1); /* FP32 bins 0..top */
-                double island = 0.0;
-                for (int b = top + 1; b < QMC_ISLAND_BINS; ++b) island += bs[b * per_bin] * per;
-                cost[(size_t)s * NOPT + q] = flops[s] * (q == NOPT - 1 ? QMC_FP64_COST : 1.0 + QMC_FP64_COST * island);
-                for (int o = 0; o < sl; ++o) {
-                    double e = 0.0;
-                    for (int b = 0; b <= top; ++b) e += bs[b * per_bin + 1 + o] * per;
-                    err[((size_t)s * NOPT + q) * sl + o] = e;
-                    if (!std::isfinite(e)) ok[(size_t)s * NOPT + q] = 0;
-                }
-            }
-            if (fp64_only[s])
-                for (int q = 0; q < NOPT - 1; ++q) ok[(size_t)s * NOPT + q] = 0;
-        }
-        std::vector<int> pick(ns, NOPT - 1);
-        if (tmax <= 0.0) {
-            for (int s = 0; s < ns; ++s) {
-                double best = std::numeric_limits<double>::infinity();
-                for (int q = 0; q < NOPT; ++q) {
-                    if (!ok[(size_t)s * NOPT + q]) continue;
-                    bool fits = true;
-                    for (int o = 0; o < sl && fits; ++o)
-                        fits = err[((size_t)s * NOPT + q) * sl + o] <= budget * own[(size_t)s * sl + o];
-                    if (fits && cost[(size_t)s * NOPT + q] < best) {
-                        best = cost[(size_t)s * NOPT + q];
-                        pick[s] = q;
-                    }
-                }
-            }
-        } else {
-            auto choose = [&](double mu, std::vector<int> &out) {
-                std::vector<double> used(K, 0.0);
-                for (int s = 0; s < ns; ++s) {
-                    double best = std::numeric_limits<double>::infinity();
-                    int bq = NOPT - 1;
-                    for (int q = 0; q < NOPT; ++q) {
-                        if (!ok[(size_t)s * NOPT + q]) continue;
-                        double pen = 0.0;
-                        for (int o = 0; o < sl; ++o) {
-                            const double e = err[((size_t)s * NOPT + q) * sl + o], l = lim[o - sig[s] + maxsig];
-                            pen += l > 0.0 ? e / l : (e > 0.0 ? std::numeric_limits<double>::infinity() : 0.0);
-                        }
-                        const double v = cost[(size_t)s * NOPT + q] + mu * pen;
-                        if (v < best) {
-                            best = v;
-                            bq = q;
-                        }
-                    }
-                    out[s] = bq;
-                    for (int o = 0; o < sl; ++o) used[o - sig[s] + maxsig] += err[((size_t)s * NOPT + bq) * sl + o];
-                }
-                for (int k = 0; k < K; ++k)
-                    if (used[k] > lim[k]) return false;
-                return true;
-            };
-            std::vector<int> cand(ns);
-            if (!choose(0.0, pick)) {
-                /* the smallest feasible mu, bracketed by doubling and then bisected in log space */
-                double lo = 0.0, hi = 1.0;
-                double total = 0.0;
-                for (int s = 0; s < ns; ++s) total += flops[s];
-                hi = std::max(total, 1.0) * 1e-12;
-                int guard = 0;
-                while (!choose(hi, cand) && guard++ < 400) {
-                    lo = hi;
-                    hi *= 2.0;
-                }
-                if (guard > 400) {
-                    for (int s = 0; s < ns; ++s) pick[s] = NOPT - 1;
-                } else {
-                    pick = cand;
-                    for (int it = 0; it < 48 && (lo <= 0.0 || hi / lo > 1.0 + 1e-3); ++it) {
-                        const double mid = lo > 0.0 ? std::sqrt(lo * hi) : hi * 0.5;
-                        if (choose(mid, cand)) {
-                            hi = mid;
-                            pick = cand;
-                        } else {
-                            lo = mid;
-                        }
-                    }
-                }
-            }
-        }
-        res.fp64_reruns = 0;
-        res.island_sectors = 0;
-        for (int s = 0; s < ns; ++s) {
-            const int q = pick[s];
-            prec[s] = q == NOPT - 1 ? 0 : (q == 0 ? 1 : 2 + (q - 1));
-            res.fp64_reruns += q == NOPT - 1;
-            res.island_sectors += q > 0 && q < NOPT - 1;
-        }
+        const bool totals = qmci::choose_precision(packed, pr.data(), pr.data() + (size_t)ns * h->n_slots * 4, n_samp,
+                                                   Tr, Ti, budget, prec.data(), &res.fp64_reruns, &res.island_sectors);
         probe_due = false;
-        prec_provisional = tmax <= 0.0;
+        prec_provisional = !totals;
         if (&pr != &probe_pr) probe_pr = pr;
         probe_n = n_samp;
     }
