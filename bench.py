@@ -69,8 +69,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 # non-planar family at n = 1048573, 16 shifts), dram__bytes_read.sum + dram__bytes_write.sum from one
 # single-pass ncu capture of a full-size launch; valid while the device code and the generator hash to
 # KERNEL_HASH, null otherwise
-TRAFFIC_BYTES = 2364672 + 78080  # read + write
-KERNEL_HASH = "0f0e2b7425b6fe2a"
+TRAFFIC_BYTES = 2243072 + 44544  # read + write
+KERNEL_HASH = "c075159337f022b8"
 
 
 INTEGRALS = {"massive_box": W.CONFIG1, "planar_dbox": W.CONFIG2, "nonplanar_dbox": W.CONFIG3,
@@ -297,7 +297,7 @@ def probe_codes(L, N, prep, di, p_mixed, sh, lam, rel_tol, fp32_budget):
     import torch
     ns, slots = prep.info.n_sectors, prep.info.n_slots
     out = torch.zeros((ns, slots, 4), dtype=torch.float64, device=sh.device)
-    bins = torch.zeros((ns, N.QMC_ISLAND_BINS, 1 + slots), dtype=torch.float64, device=sh.device)
+    bins = torch.zeros((ns, N.QMC_ISLAND_BINS, N.island_bin_words(slots)), dtype=torch.float64, device=sh.device)
     N.check(L.qmc_probe_islands(prep.packed, di.dpacked.data_ptr(), ctypes.byref(p_mixed), sh.data_ptr(),
                                 lam.data_ptr(), 4096, out.data_ptr(), bins.data_ptr(), None), "qmc_probe_islands")
     torch.cuda.synchronize()
@@ -793,7 +793,7 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0, lock
     ctx.set_kinematics(iid, cfg.kin, cfg.order_min, cfg.order_max)
     kw = dict(rel_tol=1e-3, n_shifts=N_SHIFTS, lam=LAMBDA, precision=precision, lock_step=lock_step, max_seconds=120)
     ctx.integrate(iid, seed=999, **kw)  # warm-up (kernels, generated evaluator)
-    ts, ns, ev, ok, kms, rr, worst = [], [], [], 0, [], [], 0.0
+    ts, ns, ev, ok, kms, rr, isl, worst = [], [], [], 0, [], [], [], 0.0
     for s in range(seeds):
         t0 = time.perf_counter()
         r = ctx.integrate(iid, seed=1000 + s, **kw)
@@ -802,6 +802,7 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0, lock
         ev.append(r.evals)
         kms.append(r.kernel_ms)
         rr.append(r.fp64_reruns)
+        isl.append(r.island_sectors)
         ok += r.status == 0
         val, err = api.result_arrays(r)
         vmax = float(np.max(np.abs(val)))
@@ -811,6 +812,7 @@ def time_to_accuracy(api, blob, cfg, device, stream, seeds=32, precision=0, lock
     return {"p50_ms": statistics.median(ts), "p99_ms": pct(ts, 0.99), "seeds": seeds, "converged": ok,
             "median_final_n": int(statistics.median(ns)), "median_evals": int(statistics.median(ev)),
             "median_kernel_ms": statistics.median(kms), "median_fp64_sectors": statistics.median(rr),
+            "median_island_sectors": statistics.median(isl),
             "worst_rel_err": worst, "precision": "f64" if precision == 0 else "f32+f64",
             "lattices": "one ladder for all sectors" if lock_step else "per sector"}
 

@@ -216,13 +216,16 @@ int qmc_probe_precision(const void *packed_host, const void *packed_dev, const q
  * each factor.  Its island bin is the number of levels it is an island at (0 .. QMC_ISLAND_LEVELS).
  *
  * qmc_probe_islands -- qmc_probe_precision's sample and output, and in addition, per sector and island bin,
- * the sample points in the bin and per slot the sum of |v32 - v64| over them:
- *   bins_dev[(s * QMC_ISLAND_BINS + b) * (1 + n_slots) + 0]        = points of sector s in bin b
- *   bins_dev[(s * QMC_ISLAND_BINS + b) * (1 + n_slots) + 1 + slot] = sum over them of |v32 - v64| in that slot
+ * the sample points in the bin and per slot sums over them of e = v32 - v64:
+ *   bins_dev[(s * QMC_ISLAND_BINS + b) * (1 + 4 n_slots) + 0]                    = points of sector s in bin b
+ *   bins_dev[(s * QMC_ISLAND_BINS + b) * (1 + 4 n_slots) + 1 + 4 slot + {0..3}] = sum |e|, sum e (re, im),
+ *                                                                                 sum |e|^2 in that slot
  * With islands at level L the FP32 points are those of bins 0..L.  bins_dev must not be NULL (QMC_ERR_ARG).
+ * Each sector's sample is spread over a cluster of blocks and reduced in a fixed order (deterministic).
  */
 #define QMC_ISLAND_LEVELS 6
 #define QMC_ISLAND_BINS (QMC_ISLAND_LEVELS + 1)
+#define QMC_ISLAND_BIN_WORDS(n_slots) (1 + 4 * (n_slots)) /* doubles per (sector, bin) of bins_dev */
 int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
                       const double *lambda_dev, int64_t n_sample, double *out_dev, double *bins_dev, void *stream);
 
@@ -236,8 +239,10 @@ int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc
  *   codes: out, one per sector: 1 = FP32, 2 + L = FP32 with FP64 islands at level L, 0 = FP64.
  *   counts: out (may be NULL): [0] sectors in FP64, [1] sectors with islands.
  * Options per sector: FP32 (the FP32 error of every bin), islands at level L (the error of bins 0..L; the points
- * of the other bins cost FP64) and FP64 (no error); error = mean |v32 - v64| per point per slot, cost = the
- * sector's flop per point with FP64 evaluations counted 30 times.  The FP32 error budget is
+ * of the other bins cost FP64) and FP64 (no error).  Error per slot: a bound on the bias the option's FP32 points
+ * add to the sector's mean, min(sum |e|, |sum e| + 3 sqrt(sum |e|^2)) / n_sample over its bins (the sample mean
+ * of e with three standard errors, capped by the mean of |e|); cost = the sector's flop per point with FP64
+ * evaluations counted 30 times.  The FP32 error budget is
  * (fp32_budget > 0 ? fp32_budget : 0.1) * rel_tol: per order k the sectors' errors may add up to budget * |T_k|
  * (floor 1e-6 max_k |T_k|).  Every sector starts at its cheapest option; while an order is over its limit, the
  * change of one sector's option with the largest reduction of the excess per extra cost is taken; what no single

@@ -32,6 +32,11 @@ QMC_MAX_SLOTS = 5
 QMC_MAX_ORDERS = 8
 QMC_ISLAND_LEVELS = 6
 QMC_ISLAND_BINS = QMC_ISLAND_LEVELS + 1
+
+
+def island_bin_words(n_slots: int) -> int:
+    """doubles per (sector, island bin) of qmc_probe_islands' bins: points, then 4 sums per slot"""
+    return 1 + 4 * n_slots
 QMC_PREC_FP64 = 0
 QMC_PREC_MIXED = 1
 QMC_EVAL_AUTO = 0

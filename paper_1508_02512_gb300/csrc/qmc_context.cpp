@@ -245,9 +245,9 @@ struct IntegState {
     }
 
     /* Precision of each sector (qmc_choose_precision's rule) from the probe with island bins: pr holds the probe's
-       n_sectors x n_slots x 4 sums, then n_sectors x QMC_ISLAND_BINS x (1 + n_slots) bins, over n_samp points per
-       sector.  Before the first evaluation (no totals) the decision is provisional: revisit_precision takes it
-       again on the same probe once totals exist. */
+       n_sectors x n_slots x 4 sums, then n_sectors x QMC_ISLAND_BINS x QMC_ISLAND_BIN_WORDS(n_slots) bins, over
+       n_samp points per sector.  Before the first evaluation (no totals) the decision is provisional:
+       revisit_precision takes it again on the same probe once totals exist. */
     void set_precision(const std::vector<double> &pr, int64_t n_samp, qmc_result &res) {
         const double budget = (opt.fp32_budget > 0 ? opt.fp32_budget : 0.1) * opt.rel_tol;
         const bool totals = qmci::choose_precision(packed, pr.data(), pr.data() + (size_t)ns * h->n_slots * 4, n_samp,
@@ -488,7 +488,8 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
     if (!rc) rc = dev_reserve(c, c->sums, st.sums.size() * sizeof(double));
     if (!rc) rc = dev_reserve(c, c->fails, st.fails.size() * sizeof(int64_t));
     if (!rc && st.mixed) rc = dev_reserve(c, c->prec, ns * sizeof(int32_t));
-    const size_t probe_words = (size_t)ns * h->n_slots * 4, bin_words = (size_t)ns * QMC_ISLAND_BINS * (1 + h->n_slots);
+    const size_t probe_words = (size_t)ns * h->n_slots * 4;
+    const size_t bin_words = (size_t)ns * QMC_ISLAND_BINS * QMC_ISLAND_BIN_WORDS(h->n_slots);
     if (!rc && st.mixed) rc = dev_reserve(c, c->probe, (probe_words + bin_words) * sizeof(double));
     if (rc) return res->status = rc;
     float kernel_ms_total = 0.f;
@@ -698,7 +699,8 @@ int admit(Serving *S, qmc_ctx *c, Request &r) {
     if (!rc) rc = dev_reserve(c, r.dprec, ns * sizeof(int32_t));
     if (!rc)
         rc = dev_reserve(c, r.dprobe,
-                         ((size_t)ns * h->n_slots * 4 + (size_t)ns * QMC_ISLAND_BINS * (1 + h->n_slots)) * sizeof(double));
+                         ((size_t)ns * h->n_slots * 4 + (size_t)ns * QMC_ISLAND_BINS * QMC_ISLAND_BIN_WORDS(h->n_slots))
+                             * sizeof(double));
     if (rc) return rc;
     rc = cuda_status(cudaMemcpyAsync(r.dpacked.p, r.packed.data(), r.packed.size(), cudaMemcpyHostToDevice, S->stream));
     if (!rc)
@@ -720,7 +722,7 @@ int gen_ready(const Request &r) {
 int probe(Serving *S, Request &r) {
     const PackedHeader *h = r.st.h;
     const size_t probe_words = (size_t)h->n_sectors * h->n_slots * 4;
-    std::vector<double> pr(probe_words + (size_t)h->n_sectors * QMC_ISLAND_BINS * (1 + h->n_slots));
+    std::vector<double> pr(probe_words + (size_t)h->n_sectors * QMC_ISLAND_BINS * QMC_ISLAND_BIN_WORDS(h->n_slots));
     int rc = qmc_probe_islands(r.packed.data(), r.dpacked.p, &r.passes[r.st.probe_item], (const double *)r.dshifts.p,
                                (const double *)r.dlambda.p, r.st.probe_samples(), (double *)r.dprobe.p,
                                (double *)r.dprobe.p + probe_words, S->stream);

@@ -2074,12 +2074,46 @@ DEV void eval_f32x2_body(const JobTable &jt) {
     }
 }
 
-/* ------------------------------------------------------------------ K3: FP32-versus-FP64 probe per sector */
+/* ------------------------------------------------------------------ K3: FP32-versus-FP64 probe per sector
+ * One thread-block cluster per sector (cluster size = the launch's cluster dimension, 1 when clusters cannot be
+ * had): block r of the cluster takes the sample points k = r * blockDim + thread (+ blockDim * cluster size), each
+ * block reduces its threads in fixed order into shared memory, and block 0 adds the blocks' totals in rank order
+ * through distributed shared memory -- deterministic, and no scratch in global memory. */
+DEV unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+DEV unsigned cluster_blocks() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+/* every thread of every block of the cluster; orders the cluster's shared-memory writes before later reads */
+DEV void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+/* a double in the shared memory of block `rank` of this cluster, at the address of `p` in this block */
+DEV double ld_cluster(const double *p, unsigned rank) {
+    const unsigned local = (unsigned)__cvta_generic_to_shared(p);
+    unsigned remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(rank));
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(remote) : "memory");
+    return v;
+}
+
 template <int S, bool DEF, int MAXM, class Pol>
 DEV void probe_body(const ProbeArgs &a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_red[4][4 * (MAXM + 1)];
-    const int psec = a.sector_begin + blockIdx.x;
+    /* per bin: points, then per slot sum |e|, sum e re, sum e im, sum |e|^2 (e = v32 - v64) */
+    constexpr int NBIN = 1 + 4 * (MAXM + 1);
+    constexpr int NB = QMC_ISLAND_BINS * NBIN;
+    constexpr int NA = 4 * (MAXM + 1);
+    __shared__ double s_red[4][NA + NB];
+    __shared__ double s_tot[NA + NB];
+    const unsigned crank = cluster_rank(), csize = cluster_blocks();
+    const int psec = a.sector_begin + (int)(blockIdx.x / csize);
     logtab_init();
     /* FP64 record + terms, then the FP32 terms */
     stage_sector(a.packed, a.sectors_off, a.terms_off, psec, smem);
@@ -2100,11 +2134,9 @@ DEV void probe_body(const ProbeArgs &a) {
     const double lam = a.lambda[sec.orig_index];
     const float invnf = 1.f / (float)a.n;
     const unsigned long long stride = a.n_sample >= (int64_t)a.n ? 1ull : (unsigned long long)(a.n / a.n_sample);
-    double acc[4 * (MAXM + 1)];
+    double acc[NA];
 #pragma unroll
-    for (int q = 0; q < 4 * (MAXM + 1); ++q) acc[q] = 0.0;
-    /* island bins (when a.bins is set): per bin, the points and per slot sum |v32 - v64| */
-    constexpr int NB = QMC_ISLAND_BINS * (MAXM + 2);
+    for (int q = 0; q < NA; ++q) acc[q] = 0.0;
     double bacc[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) bacc[q] = 0.0;
@@ -2117,7 +2149,9 @@ DEV void probe_body(const ProbeArgs &a) {
         split_shift(a.shift[j], a.n, aj[j], bj[j]);
     }
     uint32_t f64 = 0, f32 = 0;
-    for (long long k = threadIdx.x; k < a.n_sample && (unsigned long long)k * stride < a.n; k += blockDim.x) {
+    const long long step = (long long)blockDim.x * csize;
+    for (long long k = (long long)crank * blockDim.x + threadIdx.x;
+         k < a.n_sample && (unsigned long long)k * stride < a.n; k += step) {
         const unsigned long long i = (unsigned long long)k * stride;
         double x[S];
         float xf[S], yf[S];
@@ -2135,58 +2169,65 @@ DEV void probe_body(const ProbeArgs &a) {
         point_integrand<S, DEF, MAXM>(sec, TabPol<S>{T, &sec}, x, a.r, lam, ex, v64, f64);
         point_integrand_f<S, DEF, MAXM>(sec, pol, xf, yf, a.r, (float)lam, ex, v32, f32);
 #pragma unroll
-        for (int n = 0; n <= MAXM; ++n) {
-            const double dr = (double)v32[n].x - v64[n].x, di = (double)v32[n].y - v64[n].y;
-            acc[4 * n] += hypot(v64[n].x, v64[n].y);
-            acc[4 * n + 1] += hypot(dr, di);
-            acc[4 * n + 2] += dr;
-            acc[4 * n + 3] += di;
-        }
-#pragma unroll
         for (int b = 0; b < QMC_ISLAND_BINS; ++b) {
             if (b != bin) continue;
-            bacc[b * (MAXM + 2)] += 1.0;
+            bacc[b * NBIN] += 1.0;
+        }
 #pragma unroll
-            for (int n = 0; n <= MAXM; ++n)
-                bacc[b * (MAXM + 2) + 1 + n] += hypot((double)v32[n].x - v64[n].x, (double)v32[n].y - v64[n].y);
+        for (int n = 0; n <= MAXM; ++n) {
+            const double dr = (double)v32[n].x - v64[n].x, di = (double)v32[n].y - v64[n].y;
+            const double m = hypot(dr, di);
+            acc[4 * n] += hypot(v64[n].x, v64[n].y);
+            acc[4 * n + 1] += m;
+            acc[4 * n + 2] += dr;
+            acc[4 * n + 3] += di;
+#pragma unroll
+            for (int b = 0; b < QMC_ISLAND_BINS; ++b) {
+                if (b != bin) continue;
+                double *e = &bacc[b * NBIN + 1 + 4 * n];
+                e[0] += m;
+                e[1] += dr;
+                e[2] += di;
+                e[3] = fma(m, m, e[3]);
+            }
         }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    /* threads -> warps (shuffle tree) -> block (warps in order) -> cluster (blocks in rank order) */
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (int)(blockDim.x >> 5);
 #pragma unroll
-    for (int q = 0; q < 4 * (MAXM + 1); ++q) {
-        double v = acc[q];
+    for (int q = 0; q < NA + NB; ++q) {
+        double v = q < NA ? acc[q] : bacc[q - NA];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
         if (lane == 0) s_red[warp][q] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 4 * a.n_slots) {
-        const int q = threadIdx.x;
+    for (int q = threadIdx.x; q < NA + NB; q += blockDim.x) {
         double v = 0.0;
-        if (q < 4 * (MAXM + 1))
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_red[w][q];
-        a.out[(size_t)sec.orig_index * a.n_slots * 4 + q] = v;
+        for (int w = 0; w < nwarps; ++w) v += s_red[w][q];
+        s_tot[q] = v;
     }
-    if (a.bins) {
-        __shared__ double s_bin[4][NB];
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            double v = bacc[q];
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0) s_bin[warp][q] = v;
-        }
-        __syncthreads();
-        const int per = 1 + a.n_slots;
-        for (int q = threadIdx.x; q < QMC_ISLAND_BINS * per; q += blockDim.x) {
-            const int b = q / per, e = q - b * per; /* e = 0: points; 1 + slot: errors */
+    cluster_sync_all();
+    if (crank == 0) {
+        for (int q = threadIdx.x; q < 4 * a.n_slots; q += blockDim.x) {
             double v = 0.0;
-            if (e < MAXM + 2)
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += s_bin[w][b * (MAXM + 2) + e];
-            a.bins[(size_t)sec.orig_index * QMC_ISLAND_BINS * per + q] = v;
+            if (q < NA)
+                for (unsigned r = 0; r < csize; ++r) v += ld_cluster(&s_tot[q], r);
+            a.out[(size_t)sec.orig_index * a.n_slots * 4 + q] = v;
+        }
+        if (a.bins) {
+            const int per = QMC_ISLAND_BIN_WORDS(a.n_slots);
+            for (int q = threadIdx.x; q < QMC_ISLAND_BINS * per; q += blockDim.x) {
+                const int b = q / per, e = q - b * per; /* e = 0: points; 1 + 4 slot + {0,1,2,3}: errors */
+                double v = 0.0;
+                if (e < NBIN)
+                    for (unsigned r = 0; r < csize; ++r) v += ld_cluster(&s_tot[NA + b * NBIN + e], r);
+                a.bins[(size_t)sec.orig_index * QMC_ISLAND_BINS * per + q] = v;
+            }
         }
     }
+    /* the other blocks keep their shared memory until block 0 has read it */
+    cluster_sync_all();
 }
 
 template <int S, bool DEF, int MAXM>

@@ -44,8 +44,30 @@ static int launch_probe_t(const ProbeArgs &a, cudaStream_t st) {
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem_bytes) != cudaSuccess)
         return QMC_ERR_CUDA;
     if (a.n_sect < 1) return QMC_OK;
-    k<<<a.n_sect, 128, a.smem_bytes, st>>>(a);
-    return cudaPeekAtLastError() == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
+    /* one cluster of QMC_PROBE_CLUSTER blocks per sector where the device can place such clusters with this
+       shared memory; otherwise one block per sector (the kernel reads its cluster shape) */
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = QMC_PROBE_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)a.n_sect * QMC_PROBE_CLUSTER);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = (size_t)a.smem_bytes;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        clusters = 0;
+    }
+    if (clusters < 1) {
+        cfg.gridDim = dim3((unsigned)a.n_sect);
+        cfg.numAttrs = 0;
+    }
+    return cudaLaunchKernelEx(&cfg, k, a) == cudaSuccess ? QMC_OK : QMC_ERR_CUDA;
 }
 
 template <int S, bool DEF, int MAXM>

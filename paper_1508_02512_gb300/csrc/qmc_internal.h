@@ -138,6 +138,9 @@ struct FinTable {
 static_assert(sizeof(JobTable) < 32000, "job table must fit the kernel parameter limit");
 static_assert(sizeof(FinTable) < 32000, "finalize table must fit the kernel parameter limit");
 
+/* blocks per sector of the precision probe (a thread-block cluster; portable size) */
+#define QMC_PROBE_CLUSTER 8
+
 /* Precision probe: a strided sample of each sector's lattice points for one shift, in FP32 and FP64. */
 struct ProbeArgs {
     const unsigned char *packed;
@@ -151,8 +154,9 @@ struct ProbeArgs {
     const double *lambda;         /* per sector, table order */
     int64_t n_sample;             /* sample points per sector */
     double *out;                  /* n_sectors(table order) x n_slots x 4: sum|v64|, sum|v32-v64|, sum(v32-v64) re, im */
-    double *bins;                 /* null, or n_sectors(table order) x QMC_ISLAND_BINS x (1 + n_slots): per island
-                                     bin, the points in it and per slot sum|v32-v64| over them */
+    double *bins;                 /* null, or n_sectors(table order) x QMC_ISLAND_BINS x (1 + 4 n_slots): per island
+                                     bin, the points in it and per slot, over them, sum |e|, sum e (re, im) and
+                                     sum |e|^2, e = v32 - v64 */
     int32_t eU0, eU1, eF0, eF1;
     int32_t smem_bytes;
 };

@@ -66,7 +66,7 @@ bool choose_precision(const void *packed_host, const double *probe, const double
         for (int k = 0; k < K; ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
     for (int k = 0; k < K && tmax > 0.0; ++k) lim[k] = budget * std::max(std::hypot(Tr[k], Ti[k]), 1e-6 * tmax);
     const double per = 1.0 / (double)std::max<int64_t>(n_sample, 1);
-    const int per_bin = 1 + sl;
+    const int per_bin = QMC_ISLAND_BIN_WORDS(sl);
     /* options: 0 = FP32, 1 + L = islands at level L, NOPT - 1 = FP64 */
     const int NOPT = QMC_ISLAND_LEVELS + 2;
     std::vector<double> cost((size_t)ns * NOPT), err((size_t)ns * NOPT * sl, 0.0), own((size_t)ns * sl);
@@ -80,10 +80,18 @@ bool choose_precision(const void *packed_host, const double *probe, const double
             for (int b = top + 1; b < QMC_ISLAND_BINS; ++b) island += bs[b * per_bin] * per;
             cost[(size_t)s * NOPT + q] = flops[s] * (q == NOPT - 1 ? QMC_FP64_COST : 1.0 + QMC_FP64_COST * island);
             for (int o = 0; o < sl; ++o) {
-                double e = 0.0;
-                for (int b = 0; b <= top; ++b) e += bs[b * per_bin + 1 + o] * per;
+                /* the bias of the FP32 points' mean: |mean e| + 3 rms(e) / sqrt(n), capped by mean |e| */
+                double sa = 0.0, sr = 0.0, si = 0.0, sq = 0.0;
+                for (int b = 0; b <= top; ++b) {
+                    const double *v = &bs[b * per_bin + 1 + 4 * o];
+                    sa += v[0];
+                    sr += v[1];
+                    si += v[2];
+                    sq += v[3];
+                }
+                const double e = std::min(sa, std::hypot(sr, si) + 3.0 * std::sqrt(sq)) * per;
                 err[((size_t)s * NOPT + q) * sl + o] = e;
-                if (!std::isfinite(e)) ok[(size_t)s * NOPT + q] = 0;
+                if (!std::isfinite(e) || !std::isfinite(sa)) ok[(size_t)s * NOPT + q] = 0;
             }
         }
         if (fp64_only[s])

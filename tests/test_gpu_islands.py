@@ -84,7 +84,7 @@ def test_probe_bins_count_the_islands_of_the_sample():
     lams = [0.0] * ns
     p = api.make_pass(n, z, len(shifts), 3, precision=N.QMC_PREC_MIXED)
     out = torch.zeros((ns, sl, 4), dtype=torch.float64, device="cuda")
-    bins = torch.full((ns, R.BINS, 1 + sl), -1.0, dtype=torch.float64, device="cuda")
+    bins = torch.full((ns, R.BINS, 1 + 4 * sl), -1.0, dtype=torch.float64, device="cuda")
     sh = torch.tensor(np.asarray(shifts, dtype=np.float64), device="cuda")
     lam = torch.tensor(lams, dtype=torch.float64, device="cuda")
     n_sample = 4096
@@ -103,9 +103,12 @@ def test_probe_bins_count_the_islands_of_the_sample():
         k = R.shifted_indices(idx, n, z[: sec.dim], shifts[0][: sec.dim])
         want = np.bincount(R.bins(R.keys(k, mask, n)), minlength=R.BINS)
         assert np.array_equal(bn[s, :, 0], want.astype(np.float64)), (s, bn[s, :, 0], want)
-        tot = bn[s, :, 1:].sum(axis=0)
-        assert np.allclose(tot, pr[s, :, 1], rtol=1e-12, atol=0.0)
-        e = bn[s, :, 1:].sum(axis=1)
+        per = bn[s, :, 1:].reshape(R.BINS, sl, 4)  # sum |e|, sum e re, sum e im, sum |e|^2 per bin and slot
+        assert np.allclose(per[:, :, 0].sum(axis=0), pr[s, :, 1], rtol=1e-12, atol=0.0)
+        assert np.allclose(per[:, :, 1].sum(axis=0), pr[s, :, 2], rtol=1e-12, atol=1e-300)
+        assert np.allclose(per[:, :, 2].sum(axis=0), pr[s, :, 3], rtol=1e-12, atol=1e-300)
+        assert np.all(per[:, :, 3] >= per[:, :, 0] ** 2 / np.maximum(bn[s, :, 0:1], 1))  # Cauchy-Schwarz
+        e = per[:, :, 0].sum(axis=1)
         frac_err[s] = np.cumsum(e) / max(e.sum(), 1e-300)
     heavy = [s for s, sec in enumerate(prob.sectors) if bin(R.sing_mask(sec)).count("1") == 4]
     print(f"{len(heavy)} four-pole sectors: median share of the FP32 error left outside the islands, levels "

@@ -2,6 +2,7 @@
 and FP64 for a mixed pass, from synthetic probe outputs.  The rule as the header states it is restated here (option
 errors from the island bins, costs with FP64 counted 30 times, the per-order limits budget * |T_k| from the sums),
 and the library's choice must
+* bound each option's error by the FP32 points' bias with three standard errors, capped by their mean |e|;
 * meet every order's limit (on random instances, including ones where options tie in some slots -- the case where
   a rounding of used - e0 + e1 once made every change look worse and sent all sectors to FP64);
 * cost no more than 1.5x the brute-force optimum over the sectors that carry error;
@@ -54,7 +55,8 @@ def option_of(code):
 
 
 def restated(prep, bins, n_sample):
-    """per sector and option: error per slot and cost, as the header defines them"""
+    """per sector and option: error per slot (min(sum |e|, |sum e| + 3 sqrt(sum |e|^2)) / n over the option's FP32
+    bins) and cost, as the header defines them"""
     ns, sl = prep.info.n_sectors, prep.info.n_slots
     err = np.zeros((ns, NOPT, sl))
     cost = np.zeros((ns, NOPT))
@@ -62,7 +64,8 @@ def restated(prep, bins, n_sample):
         fl = max(prep.sector(s).flops, 1.0)
         for q in range(NOPT):
             top = -1 if q == NOPT - 1 else (BINS - 1 if q == 0 else q - 1)
-            err[s, q] = bins[s, : top + 1, 1:].sum(axis=0) / n_sample
+            v = bins[s, : top + 1, 1:].reshape(top + 1, sl, 4).sum(axis=0)
+            err[s, q] = np.minimum(v[:, 0], np.hypot(v[:, 1], v[:, 2]) + 3.0 * np.sqrt(v[:, 3])) / n_sample
             island = bins[s, top + 1:, 0].sum() / n_sample
             cost[s, q] = fl * (FP64_COST if q == NOPT - 1 else 1.0 + FP64_COST * island)
     return err, cost
@@ -91,7 +94,7 @@ def instance(prep, rng, active, n_sample=4096, m=4, n=1021):
     """errors only in the active sectors, decreasing away from the faces (higher bins carry more)"""
     ns, sl = prep.info.n_sectors, prep.info.n_slots
     counts = rng.multinomial(n_sample, np.array([0.55, 0.25, 0.1, 0.05, 0.03, 0.015, 0.005]), size=ns)
-    bins = np.zeros((ns, BINS, 1 + sl))
+    bins = np.zeros((ns, BINS, 1 + 4 * sl))
     bins[:, :, 0] = counts
     for s in active:
         scale = 10.0 ** rng.uniform(-7, -4)
@@ -99,10 +102,15 @@ def instance(prep, rng, active, n_sample=4096, m=4, n=1021):
             prof = 10.0 ** (rng.uniform(0.0, 1.5) * np.arange(BINS)) * rng.uniform(0.2, 1.0, BINS)
             if rng.uniform() < 0.3:  # ties: this slot's error lies in bin 0 only, the same for every FP32 option
                 prof[1:] = 0.0
-            bins[s, :, 1 + o] = scale * prof / prof.sum() * n_sample
+            absum = scale * prof / prof.sum() * n_sample
+            bias = rng.uniform(-1.0, 1.0, (BINS, 2)) * absum[:, None] * rng.uniform(0.0, 1.0)
+            bins[s, :, 1 + 4 * o] = absum
+            bins[s, :, 2 + 4 * o] = bias[:, 0]
+            bins[s, :, 3 + 4 * o] = bias[:, 1]
+            bins[s, :, 4 + 4 * o] = absum ** 2 / np.maximum(counts[s], 1) * rng.uniform(1.0, 30.0, BINS)
     probe = np.zeros((ns, sl, 4))
     probe[:, :, 0] = n_sample * 1.0
-    probe[:, :, 1] = bins[:, :, 1:].sum(axis=1)
+    probe[:, :, 1] = bins[:, :, 1::4].sum(axis=1)
     sums = rng.normal(0.0, 1.0, (ns, m, sl, 2)) * n
     return probe, bins, sums, np.full(ns, n, dtype=np.int64), m
 
@@ -162,7 +170,7 @@ def test_non_finite_errors_and_class2_sectors_go_to_safe_options(box):
     rng = np.random.default_rng(5)
     probe, bins, sums, nsec, m = instance(prep, rng, [0, 1])
     bins[0, 4, 1] = np.inf   # an FP32 overflow at points of bin 4: only islands at levels 0..3 or FP64 avoid it
-    bins[1, 0, 2] = np.nan   # a NaN away from the faces: only FP64 avoids it
+    bins[1, 0, 1 + 4 * 2] = np.nan   # a NaN away from the faces: only FP64 avoids it
     rc, codes, _ = call(prep, probe, bins, 4096, 1e-3, 10.0, sums, nsec, m)
     assert rc == 0
     assert codes[0] in (0, 2, 3, 4, 5) and codes[1] == 0
@@ -173,7 +181,7 @@ def test_non_finite_errors_and_class2_sectors_go_to_safe_options(box):
     p2 = api.prepare(blob, W.kinematics(topo, pp1=-2.0), -2, 2)
     n2, s2 = p2.info.n_sectors, p2.info.n_slots
     pr2 = np.ones((n2, s2, 4))
-    b2 = np.zeros((n2, BINS, 1 + s2))
+    b2 = np.zeros((n2, BINS, 1 + 4 * s2))
     b2[:, 0, 0] = 4096
     rc, codes, counts = call(p2, pr2, b2, 4096, 1e-3, 0.1)
     prob = OI.make_problem(topo, dict(pp1=-2.0), -2, 2,
@@ -186,7 +194,7 @@ def test_argument_errors(box):
     prep = box
     ns, sl = prep.info.n_sectors, prep.info.n_slots
     probe = np.zeros((ns, sl, 4))
-    bins = np.zeros((ns, BINS, 1 + sl))
+    bins = np.zeros((ns, BINS, 1 + 4 * sl))
     codes = np.zeros(ns, dtype=np.int32)
     L = N.lib()
     assert L.qmc_choose_precision(None, 0, None, None, probe.ctypes.data, bins.ctypes.data, 1, 1e-3, 0.1,
