@@ -238,16 +238,18 @@ int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc
  *     when no estimate exists yet.
  *   codes: out, one per sector: 1 = FP32, 2 + L = FP32 with FP64 islands at level L, 0 = FP64.
  *   counts: out (may be NULL): [0] sectors in FP64, [1] sectors with islands.
- * Options per sector: FP32 (the FP32 error of every bin), islands at level L (the error of bins 0..L; the points
- * of the other bins cost FP64) and FP64 (no error).  Error per slot: a bound on the bias the option's FP32 points
- * add to the sector's mean, min(sum |e|, |sum e| + 3 sqrt(sum |e|^2)) / n_sample over its bins (the sample mean
- * of e with three standard errors, capped by the mean of |e|); cost = the sector's flop per point with FP64
- * evaluations counted 30 times.  The FP32 error budget is
- * (fp32_budget > 0 ? fp32_budget : 0.1) * rel_tol: per order k the sectors' errors may add up to budget * |T_k|
- * (floor 1e-6 max_k |T_k|).  Every sector starts at its cheapest option; while an order is over its limit, the
- * change of one sector's option with the largest reduction of the excess per extra cost is taken; what no single
- * change can fix goes to FP64.  Without an estimate, each sector takes its cheapest option within budget times
- * its own mean |v64| in every slot.  An option with a non-finite FP32 error is never taken; sectors with endpoint
+ * Options per sector: FP32 (every bin in FP32), islands at level L (bins 0..L in FP32; the points of the other
+ * bins cost FP64) and FP64.  Per option and slot the FP32 bins give mean |e|, |mean e| and sum |e|^2 / n^2
+ * (e = v32 - v64, n = n_sample); cost = the sector's flop per point with FP64 evaluations counted 30 times.  The
+ * FP32 error budget is (fp32_budget > 0 ? fp32_budget : 0.1) * rel_tol.  Per order k the chosen options'
+ * statistics add up over the sectors whose slot falls in that order, and the order's FP32 bias bound
+ * min(sum mean |e|, sum |mean e| + 3 sqrt(sum |e|^2 / n^2)) -- each sector's signed mean (no cancellation
+ * between sectors) with three standard errors, capped by the mean |e| -- may not exceed budget * |T_k|
+ * (floor 1e-6 max_k |T_k|).  Every sector starts at its
+ * cheapest option; while an order is over its limit, the change of one sector's option with the largest
+ * reduction of the excess per extra cost is taken; what no single change can fix goes to FP64.  Without an
+ * estimate, each sector takes its cheapest option whose own bound is within budget times its own mean |v64| in
+ * every slot.  An option with a non-finite FP32 error is never taken; sectors with endpoint
  * exponents alpha <= -2 always take FP64.
  * Errors: QMC_ERR_ARG for a NULL required pointer, n_sample < 1, negative rel_tol/fp32_budget, or sums without
  * n_sector / n_shifts >= 1 / positive sizes.

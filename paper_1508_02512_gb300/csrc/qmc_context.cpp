@@ -138,7 +138,7 @@ struct IntegState {
     int probe_item = -1;
     std::vector<double> Tr, Ti;                 /* order_totals(): per order, summed over sectors */
     std::vector<double> probe_pr;               /* the last probe's sums, and its points per sector */
-    int64_t probe_n = 0;
+    int64_t probe_n = 0;                        /* points per sector of the last probe */
     bool prec_provisional = false;
     std::chrono::steady_clock::time_point t0;
 
@@ -187,6 +187,7 @@ struct IntegState {
         Tr.clear();
         Ti.clear();
         probe_pr.clear();
+        probe_n = 0;
         prec_provisional = false;
         const PackedSector *ps = sectors_of(packed);
         for (int pi = 0; pi < ns; ++pi) {
@@ -229,7 +230,9 @@ struct IntegState {
             const bool use32 = mixed && fl * m * (double)ladder[r].n > 1e8;
             p.precision = use32 ? QMC_PREC_MIXED : QMC_PREC_FP64;
             p.sector_precision = use32 ? prec_dev : nullptr;
-            if (use32 && probe_due && probe_item < 0) probe_item = (int)out.size();
+            /* the probe samples the largest lattice among the FP32 passes */
+            if (use32 && probe_due && (probe_item < 0 || p.lattice.n > out[probe_item].lattice.n))
+                probe_item = (int)out.size();
             masks.push_back(cnt == ns ? std::vector<int32_t>() : mk);
             out.push_back(p);
         }

@@ -67,10 +67,12 @@ bool choose_precision(const void *packed_host, const double *probe, const double
     for (int k = 0; k < K && tmax > 0.0; ++k) lim[k] = budget * std::max(std::hypot(Tr[k], Ti[k]), 1e-6 * tmax);
     const double per = 1.0 / (double)std::max<int64_t>(n_sample, 1);
     const int per_bin = QMC_ISLAND_BIN_WORDS(sl);
-    /* options: 0 = FP32, 1 + L = islands at level L, NOPT - 1 = FP64 */
+    /* options: 0 = FP32, 1 + L = islands at level L, NOPT - 1 = FP64.  Per option and slot, over its FP32 bins:
+       st = {mean |e|, |mean e|, 0, sum |e|^2 / n^2} (e = v32 - v64, n = the sample size) */
     const int NOPT = QMC_ISLAND_LEVELS + 2;
-    std::vector<double> cost((size_t)ns * NOPT), err((size_t)ns * NOPT * sl, 0.0), own((size_t)ns * sl);
+    std::vector<double> cost((size_t)ns * NOPT), st((size_t)ns * NOPT * sl * 4, 0.0), own((size_t)ns * sl);
     std::vector<char> ok((size_t)ns * NOPT, 1);
+    auto S = [&](int s, int q, int o) { return &st[(((size_t)s * NOPT + q) * sl + o) * 4]; };
     for (int s = 0; s < ns; ++s) {
         const double *bs = bins + (size_t)s * QMC_ISLAND_BINS * per_bin;
         for (int o = 0; o < sl; ++o) own[(size_t)s * sl + o] = probe[((size_t)s * sl + o) * 4] * per;
@@ -80,23 +82,24 @@ bool choose_precision(const void *packed_host, const double *probe, const double
             for (int b = top + 1; b < QMC_ISLAND_BINS; ++b) island += bs[b * per_bin] * per;
             cost[(size_t)s * NOPT + q] = flops[s] * (q == NOPT - 1 ? QMC_FP64_COST : 1.0 + QMC_FP64_COST * island);
             for (int o = 0; o < sl; ++o) {
-                /* the bias of the FP32 points' mean: |mean e| + 3 rms(e) / sqrt(n), capped by mean |e| */
-                double sa = 0.0, sr = 0.0, si = 0.0, sq = 0.0;
-                for (int b = 0; b <= top; ++b) {
-                    const double *v = &bs[b * per_bin + 1 + 4 * o];
-                    sa += v[0];
-                    sr += v[1];
-                    si += v[2];
-                    sq += v[3];
-                }
-                const double e = std::min(sa, std::hypot(sr, si) + 3.0 * std::sqrt(sq)) * per;
-                err[((size_t)s * NOPT + q) * sl + o] = e;
-                if (!std::isfinite(e) || !std::isfinite(sa)) ok[(size_t)s * NOPT + q] = 0;
+                double *e = S(s, q, o);
+                for (int b = 0; b <= top; ++b)
+                    for (int j = 0; j < 4; ++j) e[j] += bs[b * per_bin + 1 + 4 * o + j];
+                e[0] *= per;
+                e[1] = std::hypot(e[1], e[2]) * per;
+                e[2] = 0.0;
+                e[3] *= per * per;
+                for (int j = 0; j < 4; ++j)
+                    if (!std::isfinite(e[j])) ok[(size_t)s * NOPT + q] = 0;
             }
         }
         if (fp64_only[s])
             for (int q = 0; q < NOPT - 1; ++q) ok[(size_t)s * NOPT + q] = 0;
     }
+    /* the bias bound of summed statistics: the signed mean with three standard errors, capped by the mean |e| */
+    auto bound = [](double a, double r, double i, double v) {
+        return std::min(a, std::hypot(r, i) + 3.0 * std::sqrt(v));
+    };
     std::vector<int> pick(ns, NOPT - 1);
     if (tmax <= 0.0) {
         /* no estimate of the integral yet: each sector is held to budget * mean |v64| of its own, per slot */
@@ -105,8 +108,10 @@ bool choose_precision(const void *packed_host, const double *probe, const double
             for (int q = 0; q < NOPT; ++q) {
                 if (!ok[(size_t)s * NOPT + q]) continue;
                 bool fits = true;
-                for (int o = 0; o < sl && fits; ++o)
-                    fits = err[((size_t)s * NOPT + q) * sl + o] <= budget * own[(size_t)s * sl + o];
+                for (int o = 0; o < sl && fits; ++o) {
+                    const double *e = S(s, q, o);
+                    fits = bound(e[0], e[1], e[2], e[3]) <= budget * own[(size_t)s * sl + o];
+                }
                 if (fits && cost[(size_t)s * NOPT + q] < best) {
                     best = cost[(size_t)s * NOPT + q];
                     pick[s] = q;
@@ -114,10 +119,13 @@ bool choose_precision(const void *packed_host, const double *probe, const double
             }
         }
     } else {
-        /* greedy: every sector starts at its cheapest option; while an order is over its limit, take the change
-           of one sector's option with the largest reduction of the violated orders' excess (relative to their
-           limits) per unit of extra cost, among changes that push no order over its limit */
-        std::vector<double> used(K, 0.0);
+        /* per order k, the sectors' statistics add up: bound_k = min(sum mean|e|, sum |mean e| + 3 sqrt(sum var))
+           <= lim_k (the sectors' biases are added without cancelling one another; their sampling variances add).
+           Every term falls when a sector moves to FP64, so the greedy cannot stall.  Greedy: every sector
+           starts at its cheapest option; while an order is over its limit, take the change of one sector's option
+           with the largest reduction of the violated orders' excess (relative to their limits) per unit of extra
+           cost, among changes that push no order over its limit */
+        std::vector<double> tot((size_t)K * 4, 0.0);
         for (int s = 0; s < ns; ++s) {
             double best = std::numeric_limits<double>::infinity();
             for (int q = 0; q < NOPT; ++q)
@@ -125,30 +133,38 @@ bool choose_precision(const void *packed_host, const double *probe, const double
                     best = cost[(size_t)s * NOPT + q];
                     pick[s] = q;
                 }
-            for (int o = 0; o < sl; ++o) used[o - sig[s] + maxsig] += err[((size_t)s * NOPT + pick[s]) * sl + o];
+            for (int o = 0; o < sl; ++o)
+                for (int j = 0; j < 4; ++j) tot[(size_t)(o - sig[s] + maxsig) * 4 + j] += S(s, pick[s], o)[j];
         }
+        auto bound_k = [&](int k) { const double *t = &tot[(size_t)k * 4]; return bound(t[0], t[1], t[2], t[3]); };
         for (int guard = 0; guard < 4 * ns * NOPT; ++guard) {
             bool over = false;
-            for (int k = 0; k < K; ++k) over |= used[k] > lim[k];
+            for (int k = 0; k < K; ++k) over |= bound_k(k) > lim[k];
             if (!over) break;
             int bs = -1, bq = -1;
             double bratio = -1.0;
             for (int s = 0; s < ns; ++s) {
-                const double *e0 = &err[((size_t)s * NOPT + pick[s]) * sl];
                 const double c0 = cost[(size_t)s * NOPT + pick[s]];
                 for (int q = 0; q < NOPT; ++q) {
                     if (q == pick[s] || !ok[(size_t)s * NOPT + q]) continue;
-                    const double *e1 = &err[((size_t)s * NOPT + q) * sl];
                     double gain = 0.0;
-                    bool worse = false;
+                    bool worse = false, moved = false;
                     for (int o = 0; o < sl && !worse; ++o) {
+                        const double *e0 = S(s, pick[s], o), *e1 = S(s, q, o);
+                        if (e0[0] == e1[0] && e0[1] == e1[1] && e0[2] == e1[2] && e0[3] == e1[3]) continue;
+                        moved = true;
                         const int k = o - sig[s] + maxsig;
-                        const double d = e1[o] - e0[o]; /* the change itself: no rounding of used - e0 + e1 */
-                        if (d > 0.0) worse = used[k] + d > lim[k];
-                        else if (d < 0.0 && used[k] > lim[k])
-                            gain += std::min(-d, used[k] - lim[k]) / std::max(lim[k], 1e-300);
+                        const double *t = &tot[(size_t)k * 4];
+                        const double before = bound(t[0], t[1], t[2], t[3]);
+                        const double after = bound(t[0] - e0[0] + e1[0], t[1] - e0[1] + e1[1], t[2] - e0[2] + e1[2],
+                                                   std::max(t[3] - e0[3] + e1[3], 0.0));
+                        /* relative slack: the updated sums round differently from the ones they replace */
+                        const double slack = 1e-12 * (t[0] + e1[0]);
+                        if (after > std::max(before, lim[k]) + slack) worse = true;
+                        else if (before > lim[k] && after < before - slack)
+                            gain += (before - std::max(after, lim[k])) / std::max(lim[k], 1e-300);
                     }
-                    if (worse || gain <= 0.0) continue;
+                    if (worse || !moved || gain <= 0.0) continue;
                     const double dc = cost[(size_t)s * NOPT + q] - c0;
                     const double ratio = dc <= 0.0 ? std::numeric_limits<double>::infinity() : gain / dc;
                     if (ratio > bratio) {
@@ -161,17 +177,18 @@ bool choose_precision(const void *packed_host, const double *probe, const double
             if (bs < 0) break; /* no single change helps: the step below settles it */
             for (int o = 0; o < sl; ++o) {
                 const int k = o - sig[bs] + maxsig;
-                used[k] += err[((size_t)bs * NOPT + bq) * sl + o] - err[((size_t)bs * NOPT + pick[bs]) * sl + o];
+                for (int j = 0; j < 4; ++j) tot[(size_t)k * 4 + j] += S(bs, bq, o)[j] - S(bs, pick[bs], o)[j];
+                tot[(size_t)k * 4 + 3] = std::max(tot[(size_t)k * 4 + 3], 0.0);
             }
             pick[bs] = bq;
         }
         /* still over a limit (no single change helped, or the step bound ran out): the sectors with error in such
            an order take FP64 */
         std::vector<char> over(K, 0);
-        for (int k = 0; k < K; ++k) over[k] = used[k] > lim[k];
+        for (int k = 0; k < K; ++k) over[k] = bound_k(k) > lim[k];
         for (int s = 0; s < ns; ++s)
             for (int o = 0; o < sl; ++o)
-                if (over[o - sig[s] + maxsig] && err[((size_t)s * NOPT + pick[s]) * sl + o] > 0.0) pick[s] = NOPT - 1;
+                if (over[o - sig[s] + maxsig] && S(s, pick[s], o)[0] > 0.0) pick[s] = NOPT - 1;
     }
     int32_t f64 = 0, isl = 0;
     for (int s = 0; s < ns; ++s) {
