@@ -44,6 +44,7 @@ extern "C" {
 #define QMC_ERR_NO_DEVICE (-11)   /* no usable CUDA device */
 #define QMC_ERR_NOT_CONVERGED (-12) /* lattice ladder exhausted before the requested accuracy */
 #define QMC_ERR_CODEGEN (-13)     /* run-time compilation of a generated evaluator failed (NVRTC) */
+#define QMC_ERR_NONFINITE (-14)   /* a sector's FP64 sums are not finite (overflow or a singular point) */
 
 #define QMC_MAX_DIM 6             /* sector dimension (7 propagators) */
 #define QMC_MAX_SLOTS 5           /* series slots per sector */
@@ -417,7 +418,9 @@ typedef struct {
     int32_t passes, lambda_halvings, fp64_reruns, sign_failures;
     double queued_seconds;            /* serving: time between qmc_submit and admission */
     int32_t island_sectors;           /* mixed: sectors in FP32 with FP64 islands (fp64_reruns: sectors in FP64) */
-    int32_t reserved;
+    int32_t nonfinite_sectors;        /* sectors whose sums came out NaN or infinite: a mixed integration runs them
+                                         again in FP64 (counted in fp64_reruns too); in FP64 the integration stops
+                                         with QMC_ERR_NONFINITE */
 } qmc_result;
 
 typedef struct {

@@ -26,6 +26,7 @@ QMC_ERR_NOT_FOUND = -10
 QMC_ERR_NO_DEVICE = -11
 QMC_ERR_NOT_CONVERGED = -12
 QMC_ERR_CODEGEN = -13
+QMC_ERR_NONFINITE = -14
 
 QMC_MAX_DIM = 6
 QMC_MAX_SLOTS = 5
@@ -87,7 +88,7 @@ class qmc_result(ctypes.Structure):
                 ("n_final", c_int64), ("evals", c_int64), ("seconds", c_double), ("kernel_ms", c_double),
                 ("passes", c_int32), ("lambda_halvings", c_int32), ("fp64_reruns", c_int32),
                 ("sign_failures", c_int32), ("queued_seconds", c_double), ("island_sectors", c_int32),
-                ("reserved", c_int32)]
+                ("nonfinite_sectors", c_int32)]
 
 
 class qmc_serving_stats(ctypes.Structure):

@@ -140,6 +140,8 @@ struct IntegState {
     std::vector<double> probe_pr;               /* the last probe's sums, and its points per sector */
     int64_t probe_n = 0;                        /* points per sector of the last probe */
     bool prec_provisional = false;
+    bool prec_changed = false;                  /* prec changed outside set_precision: copy it to the device */
+    std::vector<char> forced64;                 /* sectors whose FP32 sums came out non-finite: FP64 from then on */
     std::chrono::steady_clock::time_point t0;
 
     int init(const unsigned char *packed_host, const qmc_options &o, std::chrono::steady_clock::time_point start,
@@ -189,6 +191,8 @@ struct IntegState {
         probe_pr.clear();
         probe_n = 0;
         prec_provisional = false;
+        prec_changed = false;
+        forced64.assign(ns, 0);
         const PackedSector *ps = sectors_of(packed);
         for (int pi = 0; pi < ns; ++pi) {
             flops[ps[pi].orig_index] = std::max(ps[pi].flops, 1.0);
@@ -254,21 +258,38 @@ struct IntegState {
     void set_precision(const std::vector<double> &pr, int64_t n_samp, qmc_result &res) {
         const double budget = (opt.fp32_budget > 0 ? opt.fp32_budget : 0.1) * opt.rel_tol;
         const bool totals = qmci::choose_precision(packed, pr.data(), pr.data() + (size_t)ns * h->n_slots * 4, n_samp,
-                                                   Tr, Ti, budget, prec.data(), &res.fp64_reruns, &res.island_sectors);
+                                                   Tr, Ti, budget, prec.data(), nullptr, nullptr);
+        for (int s = 0; s < ns; ++s)
+            if (forced64[s]) prec[s] = 0;
+        count_precision(res);
         probe_due = false;
         prec_provisional = !totals;
         if (&pr != &probe_pr) probe_pr = pr;
         probe_n = n_samp;
     }
 
-    /* true when the precision was taken again (the caller copies prec to the device before the next pass) */
+    void count_precision(qmc_result &res) const {
+        res.fp64_reruns = res.island_sectors = 0;
+        for (int s = 0; s < ns; ++s) {
+            res.fp64_reruns += prec[s] == 0;
+            res.island_sectors += prec[s] >= 2;
+        }
+    }
+
+    /* true when the precision was taken again or a sector was moved to FP64 (the caller copies prec to the device
+       before the next pass) */
     bool revisit_precision(qmc_result &res) {
-        if (!prec_provisional || probe_pr.empty()) return false;
-        double tmax = 0.0;
-        for (size_t k = 0; k < Tr.size(); ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
-        if (tmax <= 0.0) return false;
-        set_precision(probe_pr, probe_n, res);
-        return true;
+        const bool changed = prec_changed;
+        prec_changed = false;
+        if (prec_provisional && !probe_pr.empty()) {
+            double tmax = 0.0;
+            for (size_t k = 0; k < Tr.size(); ++k) tmax = std::max(tmax, std::hypot(Tr[k], Ti[k]));
+            if (tmax > 0.0) {
+                set_precision(probe_pr, probe_n, res);
+                return true;
+            }
+        }
+        return changed;
     }
 
     void count(const std::vector<qmc_pass> &ps, qmc_result &res) const {
@@ -282,6 +303,27 @@ struct IntegState {
 
     /* after an evaluation: returns QMC_PENDING to continue, or the final status */
     int step(qmc_result &res) {
+        /* non-finite sums of a sector just evaluated (an FP32 overflow at points the probe did not sample, or a
+           singular point): in a mixed integration the sector runs in FP64 from now on and this step is evaluated
+           again; in FP64 the integration stops */
+        bool redo = false;
+        const size_t per_sector = (size_t)m * h->n_slots * 2;
+        for (int s = 0; s < ns; ++s) {
+            if (!active[s]) continue;
+            bool finite = true;
+            for (size_t q = 0; q < per_sector && finite; ++q) finite = std::isfinite(sums[(size_t)s * per_sector + q]);
+            if (finite) continue;
+            res.nonfinite_sectors += 1;
+            if (!mixed || prec[s] == 0) return QMC_ERR_NONFINITE;
+            forced64[s] = 1;
+            prec[s] = 0;
+            prec_changed = true;
+            redo = true;
+        }
+        if (redo) {
+            count_precision(res);
+            return QMC_PENDING;
+        }
         /* sign check of Eq. (14) on the sectors just evaluated */
         bool again = false;
         for (int s = 0; s < ns; ++s) {

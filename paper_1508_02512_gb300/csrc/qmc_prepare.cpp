@@ -621,6 +621,7 @@ const char *qmc_strerror(int s) {
         case QMC_ERR_NO_DEVICE: return "no CUDA device";
         case QMC_ERR_NOT_CONVERGED: return "lattice ladder exhausted before the requested accuracy";
         case QMC_ERR_CODEGEN: return "run-time compilation of the generated evaluator failed";
+        case QMC_ERR_NONFINITE: return "a sector's FP64 sums are not finite";
         default: return "unknown status";
     }
 }

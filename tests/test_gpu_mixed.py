@@ -129,6 +129,43 @@ def test_mixed_integrate_massless_box_to_closed_form():
     ctx.close()
 
 
+def test_fp32_overflow_missed_by_the_probe_reruns_the_sector_in_fp64():
+    """The Euclidean massless box with s = -3e-20, t = -2: in the sectors where s multiplies the constant term of
+    F, F is O(1e-20) near the faces where the t term vanishes, and F^-2 overflows FP32 there (largest float
+    ~3.4e38) while FP64 holds it.  A probe of one point per sector misses those points, so FP32 sums come out
+    non-finite; the integration moves those sectors to FP64 and evaluates the step again.  Its results stay finite
+    and agree with the FP64 integration on the same lattices (both capped at n = 65521; this kinematics needs far
+    larger lattices to converge).  With s and t scaled by 1e-160, F^-2 overflows FP64 as well and the integration
+    stops with QMC_ERR_NONFINITE."""
+    cfg = W.CONFIG0
+    topo = cfg.topology
+    blob = T.compile_integral(topo, T.zero_invariants_of(topo, cfg.point))
+
+    def run(point, precision, **kw):
+        ctx = api.Context()
+        try:
+            iid = ctx.load_sectors(blob)
+            ctx.set_kinematics(iid, W.kinematics(topo, **point), -2, 0)
+            return ctx.integrate(iid, rel_tol=1e-3, n_shifts=8, seed=3, precision=precision, max_n=65536, **kw)
+        finally:
+            ctx.close()
+
+    pt = dict(s=-3e-20, t=-2.0)
+    r64 = run(pt, N.QMC_PREC_FP64)
+    r32 = run(pt, N.QMC_PREC_MIXED, probe_samples=1)
+    assert r64.status in (0, N.QMC_ERR_NOT_CONVERGED) and r32.status == r64.status
+    assert r64.nonfinite_sectors == 0 and r32.nonfinite_sectors > 0 and r32.fp64_reruns >= r32.nonfinite_sectors
+    v64, e64 = api.result_arrays(r64)
+    v32, e32 = api.result_arrays(r32)
+    e = np.hypot(np.hypot(e64[:, 0], e64[:, 1]), np.hypot(e32[:, 0], e32[:, 1]))
+    print(f"s = -3e-20: {r32.nonfinite_sectors} sectors came out non-finite in FP32 and ran again in FP64; "
+          f"mixed {v32} vs FP64 {v64} (+- {e})")
+    assert np.all(np.isfinite(v32)) and np.all(np.abs(v32 - v64) <= 5 * e + 1e-12 * np.abs(v64))
+    with pytest.raises(N.QMCError) as info:
+        run(dict(s=-3e-160, t=-2e-160), N.QMC_PREC_FP64)
+    assert info.value.status == N.QMC_ERR_NONFINITE
+
+
 def test_mixed_integrate_massive_box_matches_fp64():
     cfg = W.CONFIG1
     blob, prep, dev = setup(cfg)
