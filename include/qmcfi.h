@@ -123,6 +123,10 @@ typedef struct {
     const double *lambda_dev;  /* one per sector */
     double *sums_dev;          /* outputs as in qmc_eval_sums */
     int64_t *fails_dev;
+    const volatile int32_t *abort_flag; /* NULL, or a device-visible int32 (e.g. mapped pinned host memory) that the
+                                           kernels read at every work item: once nonzero, the pass's remaining
+                                           items are skipped (their partials become zero) and its sums are
+                                           meaningless.  Stops a long pass early (cancellation, time limits). */
 } qmc_batch_item;
 
 /* Text for a status code (static storage). */

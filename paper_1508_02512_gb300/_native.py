@@ -70,7 +70,8 @@ class qmc_pass(ctypes.Structure):
 
 class qmc_batch_item(ctypes.Structure):
     _fields_ = [("packed_host", c_void_p), ("packed_dev", c_void_p), ("pass_", qmc_pass), ("shifts_dev", c_void_p),
-                ("lambda_dev", c_void_p), ("sums_dev", c_void_p), ("fails_dev", c_void_p)]
+                ("lambda_dev", c_void_p), ("sums_dev", c_void_p), ("fails_dev", c_void_p),
+                ("abort_flag", c_void_p)]
 
 
 class qmc_options(ctypes.Structure):

@@ -670,12 +670,25 @@ struct Request {
     double sec_used = 0.0;         /* loop seconds charged to it so far: its share of each round's time */
     bool cancelled = false;
     int state = REQ_QUEUED;
+    int abort_slot = -1;           /* its abort flag in Serving::abort_host while it runs, or -1 */
 };
 
 }  // namespace
 
+/* abort flags of running requests: mapped pinned host memory, read by the kernels at every work item */
+#define QMC_ABORT_SLOTS 1024
+
 struct Serving {
     std::thread th;
+    volatile int32_t *abort_host = nullptr; /* QMC_ABORT_SLOTS flags; a running request owns one */
+    int32_t *abort_dev = nullptr;           /* the same flags as the device sees them */
+    std::vector<char> slot_used;
+    /* watchdog: sets the abort flag of a running request whose time limit passes during a round */
+    std::thread wd;
+    std::mutex wmu;
+    std::condition_variable wcv;
+    bool wstop = false;
+    std::vector<std::pair<std::chrono::steady_clock::time_point, int>> armed; /* (deadline, slot) */
     cudaStream_t stream = nullptr; /* the loop's own stream: rounds never wait for, or block, other context calls */
     DevBuf scratch;                /* the loop's own scratch (counted in the context's budget) */
     std::mutex mu;
@@ -700,6 +713,14 @@ void release_request(qmc_ctx *c, Request &r) {
 
 void finish(Serving *S, qmc_ctx *c, Request &r, int status) {
     release_request(c, r);
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (r.abort_slot >= 0) {
+            S->abort_host[r.abort_slot] = 0;
+            S->slot_used[r.abort_slot] = 0;
+            r.abort_slot = -1;
+        }
+    }
     if (status != QMC_OK && r.res.n_final == 0 && !r.st.ladder.empty()) r.res.n_final = r.st.ladder[0].n;
     r.res.status = status;
     r.res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
@@ -779,6 +800,30 @@ int probe(Serving *S, Request &r) {
     r.st.set_precision(pr, std::min<int64_t>(r.st.probe_samples(), r.passes[r.st.probe_item].lattice.n), r.res);
     return cuda_status(cudaMemcpyAsync(r.dprec.p, r.st.prec.data(), r.st.ns * sizeof(int32_t), cudaMemcpyHostToDevice,
                                        S->stream));
+}
+
+/* sets the abort flag of each armed slot when its deadline passes (the serving loop arms the running round's
+   requests that have a time limit, and disarms them when the round is over) */
+void watchdog(Serving *S) {
+    std::unique_lock<std::mutex> lk(S->wmu);
+    while (!S->wstop) {
+        if (S->armed.empty()) {
+            S->wcv.wait(lk);
+            continue;
+        }
+        auto next = S->armed.front().first;
+        for (const auto &a : S->armed) next = std::min(next, a.first);
+        S->wcv.wait_until(lk, next);
+        const auto now = std::chrono::steady_clock::now();
+        for (auto it = S->armed.begin(); it != S->armed.end();) {
+            if (it->first <= now) {
+                S->abort_host[it->second] = 1;
+                it = S->armed.erase(it);
+            } else {
+                ++it;
+            }
+        }
+    }
 }
 
 void serve_loop(qmc_ctx *c) {
@@ -918,6 +963,13 @@ void serve_loop(qmc_ctx *c) {
             }
             std::lock_guard<std::mutex> g2(S->mu);
             r->state = REQ_ACTIVE;
+            /* its abort flag (none when all slots are taken: it then stops at round boundaries only) */
+            for (int k = 0; k < QMC_ABORT_SLOTS && r->abort_slot < 0; ++k)
+                if (!S->slot_used[k]) {
+                    S->slot_used[k] = 1;
+                    S->abort_host[k] = r->cancelled ? 1 : 0;
+                    r->abort_slot = k;
+                }
             S->active.push_back(r);
             S->stats.peak_active = std::max<int64_t>(S->stats.peak_active, (int64_t)S->active.size());
         }
@@ -954,6 +1006,7 @@ void serve_loop(qmc_ctx *c) {
                 b.lambda_dev = (const double *)r.dlambda.p;
                 b.sums_dev = (double *)r.dsums.p;
                 b.fails_dev = (int64_t *)r.dfails.p;
+                b.abort_flag = r.abort_slot >= 0 ? S->abort_dev + r.abort_slot : nullptr;
                 items.push_back(b);
             }
             first[i + 1] = items.size();
@@ -970,6 +1023,18 @@ void serve_loop(qmc_ctx *c) {
             }
             rc = dev_reserve(c, S->scratch, need);
         }
+        /* time limits of the round's requests: past one, the watchdog stops that request's remaining work items
+           (armed before the launch: the copies back below go to pageable memory and block until the round ends) */
+        {
+            std::lock_guard<std::mutex> gw(S->wmu);
+            S->armed.clear();
+            for (auto &r : batch)
+                if (r->opt.max_seconds > 0 && r->abort_slot >= 0)
+                    S->armed.push_back({r->t_submit + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                                          std::chrono::duration<double>(r->opt.max_seconds)),
+                                        r->abort_slot});
+        }
+        S->wcv.notify_all();
         if (!rc) rc = qmc_eval_batch(items.data(), (int32_t)items.size(), S->scratch.p, S->scratch.bytes, S->stream);
         for (size_t i = 0; i < batch.size() && !rc; ++i) {
             IntegState &st = batch[i]->st;
@@ -980,6 +1045,10 @@ void serve_loop(qmc_ctx *c) {
                                                  cudaMemcpyDeviceToHost, S->stream));
         }
         if (!rc) rc = cuda_status(cudaStreamSynchronize(S->stream));
+        {
+            std::lock_guard<std::mutex> gw(S->wmu);
+            S->armed.clear();
+        }
         /* the round's time (the whole iteration: admission, preparation, probes, the batch, the copies back) is
            charged to its requests in proportion to their evaluations' algorithmic flop, FP64 evaluations
            weighted by QMC_FP64_COST */
@@ -1017,6 +1086,17 @@ void serve_loop(qmc_ctx *c) {
                     continue;
                 }
                 r.st.count(r.passes, r.res);
+                /* stopped within the round (cancelled, or its time limit passed): its sums are incomplete */
+                if (r.abort_slot >= 0 && S->abort_host[r.abort_slot]) {
+                    bool cancelled;
+                    {
+                        std::lock_guard<std::mutex> g3(S->mu);
+                        cancelled = r.cancelled;
+                    }
+                    finish(S, c, r, cancelled ? QMC_ERR_CANCELLED : QMC_ERR_TIMEOUT);
+                    done.push_back(rp);
+                    continue;
+                }
                 const int st = r.st.step(r.res);
                 if (st != QMC_PENDING) {
                     finish(S, c, r, st);
@@ -1039,11 +1119,18 @@ void serving_shutdown(qmc_ctx *c) {
     }
     c->serving->cv.notify_all();
     if (c->serving->th.joinable()) c->serving->th.join();
+    {
+        std::lock_guard<std::mutex> g(c->serving->wmu);
+        c->serving->wstop = true;
+    }
+    c->serving->wcv.notify_all();
+    if (c->serving->wd.joinable()) c->serving->wd.join();
     cudaSetDevice(c->device);
     if (c->serving->stream) cudaStreamSynchronize(c->serving->stream);
     for (auto &kv : c->serving->all) release_request(c, *kv.second);
     dev_release(c, c->serving->scratch);
     if (c->serving->stream) cudaStreamDestroy(c->serving->stream);
+    if (c->serving->abort_host) cudaFreeHost((void *)c->serving->abort_host);
     delete c->serving;
     c->serving = nullptr;
 }
@@ -1088,7 +1175,19 @@ int qmc_submit(qmc_ctx *c, int32_t integral_id, const double *invariants, int32_
                 delete S;
                 return QMC_ERR_CUDA;
             }
+            void *flags = nullptr;
+            if (cudaHostAlloc(&flags, QMC_ABORT_SLOTS * sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess ||
+                cudaHostGetDevicePointer((void **)&S->abort_dev, flags, 0) != cudaSuccess) {
+                if (flags) cudaFreeHost(flags);
+                cudaStreamDestroy(S->stream);
+                delete S;
+                return QMC_ERR_CUDA;
+            }
+            S->abort_host = static_cast<volatile int32_t *>(flags);
+            for (int k = 0; k < QMC_ABORT_SLOTS; ++k) S->abort_host[k] = 0;
+            S->slot_used.assign(QMC_ABORT_SLOTS, 0);
             c->serving = S;
+            S->wd = std::thread(watchdog, S);
             S->th = std::thread(serve_loop, c);
         }
     }
@@ -1124,6 +1223,8 @@ int qmc_cancel(qmc_ctx *c, int64_t request_id) {
     auto it = S->all.find(request_id);
     if (it == S->all.end()) return QMC_ERR_NOT_FOUND;
     it->second->cancelled = true;
+    /* a running request stops within the round: the kernels skip its remaining work items */
+    if (it->second->abort_slot >= 0) S->abort_host[it->second->abort_slot] = 1;
     S->cv.notify_all();
     return QMC_OK;
 }

@@ -583,6 +583,9 @@ DEV int find_job(const JobTable &jt, long long item) {
     return lo;
 }
 
+/* nonzero once the job's abort flag (device-visible, e.g. mapped pinned host memory) is set */
+DEV int job_aborted(const Job &J) { return J.abort ? *J.abort : 0; }
+
 /* ------------------------------------------------------------------ K1: persistent FP64 evaluation */
 template <int S, int MAXM>
 __device__ __noinline__ void point_integrand_taylor(const PackedSector &s, const PackedTerm *T, const double *x, int r,
@@ -593,7 +596,7 @@ template <int S, bool DEF, int MAXM, class Pol, bool TAYLOR = false>
 DEV void eval_f64_body(const JobTable &jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
-    __shared__ int s_job;
+    __shared__ int s_job, s_abort;
     __shared__ double s_red[16][2 * (MAXM + 1)];
     __shared__ uint32_t s_fail[16];
     /* per warp: lattice residues r_j of the points gathered for evaluation (at most 63 wait between batches) */
@@ -609,6 +612,7 @@ DEV void eval_f64_body(const JobTable &jt) {
             const long long it = (long long)atomicAdd(jt.counter, 1ull);
             s_item = it;
             s_job = it < jt.total_items ? find_job(jt, it) : 0;
+            s_abort = it < jt.total_items ? job_aborted(jt.jobs[s_job]) : 0;
         }
         __syncthreads();
         const long long item = s_item;
@@ -616,6 +620,12 @@ DEV void eval_f64_body(const JobTable &jt) {
         const int jb = s_job;
         const Job &J = jt.jobs[jb];
         const long long local = item - J.item_begin;
+        if (s_abort) { /* the pass was stopped: its remaining items contribute nothing */
+            if ((int)threadIdx.x < J.n_slots * 2) J.partials[local * J.n_slots * 2 + threadIdx.x] = 0.0;
+            if (threadIdx.x == 0) J.part_fails[local] = 0;
+            __syncthreads();
+            continue;
+        }
         const long long per_sector = (long long)J.m * J.chunks;
         const int ls = (int)(local / per_sector);
         const long long rem = local - (long long)ls * per_sector;
@@ -1456,7 +1466,7 @@ template <int S, bool DEF, int MAXM, class Pol>
 DEV void eval_f32_body(const JobTable &jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
-    __shared__ int s_job;
+    __shared__ int s_job, s_abort;
     __shared__ double s_red[16][2 * (MAXM + 1)];
     __shared__ uint32_t s_fail[16];
     const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
@@ -1468,6 +1478,7 @@ DEV void eval_f32_body(const JobTable &jt) {
             const long long it = (long long)atomicAdd(jt.counter, 1ull);
             s_item = it;
             s_job = it < jt.total_items ? find_job(jt, it) : 0;
+            s_abort = it < jt.total_items ? job_aborted(jt.jobs[s_job]) : 0;
         }
         __syncthreads();
         const long long item = s_item;
@@ -1475,6 +1486,12 @@ DEV void eval_f32_body(const JobTable &jt) {
         const int jb = s_job;
         const Job &J = jt.jobs[jb];
         const long long local = item - J.item_begin;
+        if (s_abort) { /* the pass was stopped: its remaining items contribute nothing */
+            if ((int)threadIdx.x < J.n_slots * 2) J.partials[local * J.n_slots * 2 + threadIdx.x] = 0.0;
+            if (threadIdx.x == 0) J.part_fails[local] = 0;
+            __syncthreads();
+            continue;
+        }
         const long long per_sector = (long long)J.m * J.chunks;
         const int ls = (int)(local / per_sector);
         const long long rem = local - (long long)ls * per_sector;
@@ -1936,7 +1953,7 @@ template <int S, bool DEF, int MAXM, class Pol>
 DEV void eval_f32x2_body(const JobTable &jt) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_item;
-    __shared__ int s_job;
+    __shared__ int s_job, s_abort;
     __shared__ double s_red[16][2 * (MAXM + 1)];
     __shared__ uint32_t s_fail[16];
     const PackedSector &sec = *reinterpret_cast<const PackedSector *>(smem);
@@ -1948,6 +1965,7 @@ DEV void eval_f32x2_body(const JobTable &jt) {
             const long long it = (long long)atomicAdd(jt.counter, 1ull);
             s_item = it;
             s_job = it < jt.total_items ? find_job(jt, it) : 0;
+            s_abort = it < jt.total_items ? job_aborted(jt.jobs[s_job]) : 0;
         }
         __syncthreads();
         const long long item = s_item;
@@ -1955,6 +1973,12 @@ DEV void eval_f32x2_body(const JobTable &jt) {
         const int jb = s_job;
         const Job &J = jt.jobs[jb];
         const long long local = item - J.item_begin;
+        if (s_abort) { /* the pass was stopped: its remaining items contribute nothing */
+            if ((int)threadIdx.x < J.n_slots * 2) J.partials[local * J.n_slots * 2 + threadIdx.x] = 0.0;
+            if (threadIdx.x == 0) J.part_fails[local] = 0;
+            __syncthreads();
+            continue;
+        }
         const long long per_sector = (long long)J.m * J.chunks;
         const int ls = (int)(local / per_sector);
         const long long rem = local - (long long)ls * per_sector;

@@ -104,7 +104,7 @@ struct Job {
     uint32_t zstep[QMC_MAX_DIM];  /* (blockDim * z_j) mod n */
     int32_t sector_begin, n_sect, m, n_slots;
     int32_t eU0, eU1, eF0, eF1;
-    int32_t pad[3];
+    const volatile int32_t *abort; /* null, or nonzero once the pass is stopped: its remaining items are skipped */
 };
 
 #define QMC_MAX_JOBS 96

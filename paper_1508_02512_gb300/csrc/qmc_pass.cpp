@@ -231,6 +231,7 @@ int run_eval(const qmc_batch_item *items, int n, const BatchLayout &L, unsigned 
                 J.n_sect = run.n_sect;
                 J.m = b.pass.n_shifts;
                 J.n_slots = h->n_slots;
+                J.abort = b.abort_flag;
                 J.eU0 = h->eU0;
                 J.eU1 = h->eU1;
                 J.eF0 = h->eF0;

@@ -207,3 +207,33 @@ def test_overload_sheds_requests_that_cannot_meet_their_deadline():
     assert len(ok) > 0
     # turned away early, not when their limit passed
     assert min(r.seconds for r in shed) < limit
+
+
+def test_cancel_and_time_limit_stop_a_running_round():
+    """A request with long rounds (the massive box in FP64 from a lattice of 33554393 points, 16 shifts: ~0.8 s for
+    its one round) stops within that round when it is cancelled or its time limit passes: the kernels read its
+    abort flag (mapped pinned host memory) at every work item and skip the rest.  Without the flag it would end
+    only at the round boundary, a whole round later."""
+    cfg = W.CONFIG1
+    ctx = api.Context(0, 8 << 30)
+    iid = ctx.load_sectors(table(cfg))
+    fp64 = dict(n_shifts=16, lam=0.5, precision=N.QMC_PREC_FP64)
+    # compiles the family's generated FP64 evaluator, which an admitted request would otherwise wait for
+    assert ctx.wait(ctx.submit(iid, point(cfg), 0, 0, seed=1, rel_tol=1e-3, **fp64)).status == 0
+    big = dict(rel_tol=1e-12, ladder_start=15, max_n=33554393, **fp64)
+    full = ctx.wait(ctx.submit(iid, point(cfg), 0, 0, seed=2, **big))
+    assert full.status in (0, N.QMC_ERR_NOT_CONVERGED) and full.seconds > 0.4  # one long round, whatever its end
+    rid = ctx.submit(iid, point(cfg), 0, 0, seed=3, **big)
+    time.sleep(0.1)
+    ctx.cancel(rid)
+    cancelled = ctx.wait(rid)
+    # the same table under a new id has no cost history, so the loop admits it (for this id it would be shed)
+    fresh = ctx.load_sectors(table(cfg))
+    limited = ctx.wait(ctx.submit(fresh, point(cfg), 0, 0, seed=4, max_seconds=0.15, **big))
+    st = ctx.serving_stats()
+    ctx.close()
+    print(f"one round {full.seconds:.3f} s; cancelled after 0.1 s: done at {cancelled.seconds:.3f} s; "
+          f"time limit 0.15 s: done at {limited.seconds:.3f} s; {st.rounds} rounds")
+    assert cancelled.status == N.QMC_ERR_CANCELLED and cancelled.seconds < 0.5 * full.seconds
+    assert limited.status == N.QMC_ERR_TIMEOUT and 0.14 < limited.seconds < 0.5 * full.seconds
+    assert limited.evals > 0  # it ran (stopped by the watchdog within its round, not shed before it)
