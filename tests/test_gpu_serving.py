@@ -32,7 +32,7 @@ def point(cfg, **kw):
     return W.kinematics(cfg.topology, **{**cfg.point, **kw})
 
 
-def test_batch_equals_alone():
+def test_batch_equals_alone_and_abort_flags_stop_their_passes():
     lat = dict(api.builtin_lattices())
     specs = [(W.CONFIG0, point(W.CONFIG0), -2, 0, 4093, 0.0, N.QMC_PREC_FP64),
              (W.CONFIG1, point(W.CONFIG1), 0, 0, 8191, 0.5, N.QMC_PREC_FP64),
@@ -79,6 +79,22 @@ def test_batch_equals_alone():
     torch.cuda.synchronize()
     for (s_a, f_a), (sums, fails) in zip(alone, outs):
         assert torch.equal(s_a, sums) and torch.equal(f_a, fails)
+    # the same batch with an FP64 and a mixed pass stopped before they start (qmc_batch_item.abort_flag, here in
+    # device memory): every item of theirs is skipped, so their sums are zero; the other passes are unchanged
+    stop = torch.ones(1, dtype=torch.int32, device="cuda")
+    for i in (1, 3):
+        items[i].abort_flag = stop.data_ptr()
+    for sums, fails in outs:
+        sums.fill_(7.0)
+        fails.fill_(7)
+    rc = N.lib().qmc_eval_batch(items, len(specs), base, need, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, N.strerror(rc)
+    torch.cuda.synchronize()
+    for i, ((s_a, f_a), (sums, fails)) in enumerate(zip(alone, outs)):
+        if i in (1, 3):
+            assert int(torch.count_nonzero(sums)) == 0 and int(torch.count_nonzero(fails)) == 0
+        else:
+            assert torch.equal(s_a, sums) and torch.equal(f_a, fails)
 
 
 def req_opts(prec, seed):
