@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64", help="precision of --profile-pass")
     ap.add_argument("--profile-log2n", type=int, default=0,
                     help="lattice size of --profile-pass (default 2^20 one-loop, 2^16 two-loop)")
+    ap.add_argument("--profile-islands", type=int, default=-1,
+                    help="run one mixed pass of the paper's Table 2 point (legs -1,0,0,-1) at n = 32749 with every "
+                         "sector at this FP64-island level and exit (the case for ncu captures of the island mode)")
     ap.add_argument("--serving", type=int, default=0,
                     help="run only the serving workload with this many requests and print its JSON line")
     ap.add_argument("--paper-ia-scan", type=int, default=0,
@@ -911,6 +914,32 @@ def profile_pass(precision="fp64", integral="massive_box", log2n=0):
     print("profile pass ok", int(fails.sum().item()))
 
 
+def profile_islands(level):
+    """One mixed pass of the paper's Table 2 integral (massless planar double box, legs -1,0,0,-1, geometric
+    decomposition, 143 sectors) at n = 32749 with 16 shifts, every sector at precision code 2 + level (FP32 with
+    FP64 islands): the FP64 kernel evaluates the island points, the FP32 kernel the rest."""
+    import torch
+    from paper_1508_02512_gb300 import _native as N
+    from paper_1508_02512_gb300 import api
+    from paper_1508_02512_gb300 import tables as T
+    topo = W.double_box_planar(False)
+    pt = W.PAPER_IB_POINTS["-1,0,0,-1"]
+    blob = T.compile_integral(topo, T.zero_invariants_of(topo, pt), strategy="geometric")
+    prep = api.prepare(blob, W.kinematics(topo, **pt), -4, 0)
+    dev = api.DeviceIntegral(prep)
+    ns = prep.info.n_sectors
+    n = 32749
+    p = api.make_pass(n, dict(api.builtin_lattices())[n], N_SHIFTS, 3, precision=N.QMC_PREC_MIXED)
+    codes = torch.full((ns,), 2 + level, dtype=torch.int32, device="cuda")
+    p.sector_precision = codes.data_ptr()
+    sh = torch.tensor(W.shifts(7, N_SHIFTS), dtype=torch.float64, device="cuda")
+    lam = torch.zeros(ns, dtype=torch.float64, device="cuda")
+    sums, fails = dev.outputs(p)
+    dev.eval_sums(p, sh, lam, sums, fails)
+    torch.cuda.synchronize()
+    print("island pass ok", float(sums.abs().sum()))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.serving:
@@ -921,6 +950,8 @@ if __name__ == "__main__":
         print(json.dumps(paper_table2()))
     elif a.profile_pass:
         profile_pass(a.precision, a.integral, a.profile_log2n)
+    elif a.profile_islands >= 0:
+        profile_islands(a.profile_islands)
     elif a.impl == "reference":
         main_reference(a)
     else:
