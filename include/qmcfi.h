@@ -206,8 +206,9 @@ int qmc_reduce_partials(const void *packed_host, const void *packed_dev, const q
  *   out[(s * n_slots + slot) * 4 + {0,1,2,3}] = sum |v64|, sum |v32 - v64|, sum (v32 - v64) re, im.
  * The FP32 values come from the table evaluator whatever pass->evaluator says (the generated evaluator performs
  * the same products and FMAs, summed in another order).
- * The paper evaluates in one precision; the split into an FP32 path with FP64 re-runs of sectors whose FP32
- * error exceeds a budget is this library's (Sec. II, after Eq. 12, motivates FP64 where cancellation is large).
+ * The paper evaluates in one precision; the split into an FP32 path, FP64 islands near the singular faces and
+ * FP64 sectors under an error budget is this library's (Sec. II, after Eq. 12, motivates FP64 where cancellation
+ * is large).
  */
 int qmc_probe_precision(const void *packed_host, const void *packed_dev, const qmc_pass *pass, const double *shift_dev,
                         const double *lambda_dev, int64_t n_sample, double *out_dev, void *stream);
@@ -250,12 +251,11 @@ int qmc_probe_islands(const void *packed_host, const void *packed_dev, const qmc
  * statistics add up over the sectors whose slot falls in that order, and the order's FP32 bias bound
  * min(sum mean |e|, sum |mean e| + 3 sqrt(sum |e|^2 / n^2)) -- each sector's signed mean (no cancellation
  * between sectors) with three standard errors, capped by the mean |e| -- may not exceed budget * |T_k|
- * (floor 1e-6 max_k |T_k|).  Every sector starts at its
- * cheapest option; while an order is over its limit, the change of one sector's option with the largest
- * reduction of the excess per extra cost is taken; what no single change can fix goes to FP64.  Without an
- * estimate, each sector takes its cheapest option whose own bound is within budget times its own mean |v64| in
- * every slot.  An option with a non-finite FP32 error is never taken; sectors with endpoint
- * exponents alpha <= -2 always take FP64.
+ * (floor 1e-6 max_k |T_k|).  Every sector starts at its cheapest option; while an order is over its limit, the
+ * change of one sector's option with the largest reduction of the excess per extra cost is taken; what no single
+ * change can fix goes to FP64.  Without an estimate, each sector takes its cheapest option whose own bound is
+ * within budget times its own mean |v64| in every slot.  An option with a non-finite FP32 error is never taken;
+ * sectors with endpoint exponents alpha <= -2 always take FP64.
  * Errors: QMC_ERR_ARG for a NULL required pointer, n_sample < 1, negative rel_tol/fp32_budget, or sums without
  * n_sector / n_shifts >= 1 / positive sizes.
  */
