@@ -392,7 +392,8 @@ typedef struct {
     const qmc_lattice *lattices;
     const double *shifts;    /* optional n_shifts x 6 host array overriding the seed */
     int64_t max_n;           /* stop the ladder above this lattice size (0 = no limit) */
-    double max_seconds;      /* 0 = no limit */
+    double max_seconds;      /* 0 = no limit; else the time limit (QMC_ERR_TIMEOUT), which also stops a running
+                                pass: the kernels skip its remaining work items once a timer sets an abort flag */
     int32_t block, points_per_thread; /* launch shape (0 = default) */
     int64_t probe_samples;   /* QMC_PREC_MIXED: points per sector of the FP32/FP64 probe (0 = 4096) */
     double fp32_budget;      /* QMC_PREC_MIXED (0 = 0.1): the FP32 error budget is fp32_budget * rel_tol of the

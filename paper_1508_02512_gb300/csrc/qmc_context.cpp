@@ -72,6 +72,9 @@ struct qmc_ctx {
     int32_t next_id = 1;
     DevBuf scratch, sums, fails, shifts, lambda, hpacked, prec, probe;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    /* qmc_integrate's abort flag (mapped pinned host memory, allocated on first use): set at the time limit */
+    volatile int32_t *abort_host = nullptr;
+    int32_t *abort_dev = nullptr;
     std::mutex mu;
     Serving *serving = nullptr;
 };
@@ -471,6 +474,7 @@ int qmc_destroy(qmc_ctx *c) {
     dev_release(c, c->probe);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
+    if (c->abort_host) cudaFreeHost((void *)c->abort_host);
     delete c;
     return QMC_OK;
 }
@@ -511,6 +515,32 @@ int qmc_set_kinematics(qmc_ctx *c, int32_t id, const double *inv, int32_t n_inv,
     return QMC_OK;
 }
 
+namespace {
+
+/* sets *flag at `deadline` unless disarmed first (destruction disarms and joins) */
+struct DeadlineTimer {
+    std::mutex mu;
+    std::condition_variable cv;
+    bool done = false;
+    std::thread th;
+    DeadlineTimer(volatile int32_t *flag, std::chrono::steady_clock::time_point deadline) {
+        th = std::thread([this, flag, deadline] {
+            std::unique_lock<std::mutex> lk(mu);
+            if (!cv.wait_until(lk, deadline, [this] { return done; })) *flag = 1;
+        });
+    }
+    ~DeadlineTimer() {
+        {
+            std::lock_guard<std::mutex> g(mu);
+            done = true;
+        }
+        cv.notify_all();
+        th.join();
+    }
+};
+
+}  // namespace
+
 int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *res) {
     if (!c || !opt || !res) return QMC_ERR_ARG;
     std::memset(res, 0, sizeof(*res));
@@ -537,6 +567,24 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
     const size_t bin_words = (size_t)ns * QMC_ISLAND_BINS * QMC_ISLAND_BIN_WORDS(h->n_slots);
     if (!rc && st.mixed) rc = dev_reserve(c, c->probe, (probe_words + bin_words) * sizeof(double));
     if (rc) return res->status = rc;
+    /* a time limit stops a running pass: the kernels read the abort flag at every work item */
+    std::unique_ptr<DeadlineTimer> timer;
+    if (opt->max_seconds > 0) {
+        if (!c->abort_host) {
+            void *f = nullptr;
+            if (cudaHostAlloc(&f, sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess ||
+                cudaHostGetDevicePointer((void **)&c->abort_dev, f, 0) != cudaSuccess) {
+                if (f) cudaFreeHost(f);
+                c->abort_dev = nullptr;
+                return res->status = QMC_ERR_CUDA;
+            }
+            c->abort_host = static_cast<volatile int32_t *>(f);
+        }
+        *c->abort_host = 0;
+        const auto limit = std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+            std::chrono::duration<double>(opt->max_seconds));
+        timer.reset(new DeadlineTimer(c->abort_host, t0 + limit));
+    }
     float kernel_ms_total = 0.f;
     std::vector<qmc_pass> passes;
     std::vector<qmc_batch_item> items;
@@ -575,6 +623,7 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
             items[k].lambda_dev = (const double *)c->lambda.p;
             items[k].sums_dev = (double *)c->sums.p;
             items[k].fails_dev = (int64_t *)c->fails.p;
+            items[k].abort_flag = timer ? c->abort_dev : nullptr;
         }
         const size_t need = qmc_batch_scratch_bytes(items.data(), (int32_t)items.size());
         if (!need) return res->status = QMC_ERR_ARG;
@@ -594,6 +643,10 @@ int qmc_integrate(qmc_ctx *c, int32_t id, const qmc_options *opt, qmc_result *re
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
         kernel_ms_total += ms;
         st.count(passes, *res);
+        if (timer && *c->abort_host) { /* the pass was stopped at the time limit: its sums are incomplete */
+            status = QMC_ERR_TIMEOUT;
+            break;
+        }
         status = st.step(*res);
     }
     res->kernel_ms = kernel_ms_total;

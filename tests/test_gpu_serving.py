@@ -253,3 +253,26 @@ def test_cancel_and_time_limit_stop_a_running_round():
     assert cancelled.status == N.QMC_ERR_CANCELLED and cancelled.seconds < 0.5 * full.seconds
     assert limited.status == N.QMC_ERR_TIMEOUT and 0.14 < limited.seconds < 0.5 * full.seconds
     assert limited.evals > 0  # it ran (stopped by the watchdog within its round, not shed before it)
+
+
+def test_time_limit_stops_a_running_pass_of_qmc_integrate():
+    """The blocking qmc_integrate with a time limit inside one long pass (the massive box in FP64 on 33554393
+    points, 16 shifts: ~0.8 s): a timer sets the context's abort flag at the limit, the kernels skip the rest of
+    the pass, and the call returns QMC_ERR_TIMEOUT well before the pass would have ended."""
+    cfg = W.CONFIG1
+    ctx = api.Context()
+    iid = ctx.load_sectors(table(cfg))
+    ctx.set_kinematics(iid, point(cfg), 0, 0)
+    fp64 = dict(n_shifts=16, lam=0.5, precision=N.QMC_PREC_FP64)
+    assert ctx.integrate(iid, rel_tol=1e-3, **fp64).status == 0  # compiles the generated evaluator
+    big = dict(rel_tol=1e-12, ladder_start=15, max_n=33554393, **fp64)
+    full = ctx.integrate(iid, seed=2, **big)
+    t0 = time.perf_counter()
+    limited = ctx.integrate(iid, seed=3, max_seconds=0.15, **big)
+    wall = time.perf_counter() - t0
+    again = ctx.integrate(iid, seed=2, **big)  # the flag is cleared for the next call
+    ctx.close()
+    print(f"one pass {full.seconds:.3f} s; time limit 0.15 s: returned after {wall:.3f} s")
+    assert full.seconds > 0.4 and full.status in (0, N.QMC_ERR_NOT_CONVERGED)
+    assert limited.status == N.QMC_ERR_TIMEOUT and wall < 0.5 * full.seconds
+    assert again.status == full.status and np.array_equal(api.result_arrays(again)[0], api.result_arrays(full)[0])
